@@ -1,0 +1,234 @@
+/*
+ * dobfs — direction-optimized breadth-first search on one GPU (C ABI).
+ *
+ * The method is the per-level step of direction-optimized BFS (Sec. 2.2 and
+ * Algorithm 1 of Sallinen, Gharaibeh & Ripeanu, "Accelerating Direction-
+ * Optimized Breadth First Search on Hybrid Architectures"): a level is
+ * expanded either top-down (every frontier vertex marks its unvisited
+ * neighbours, Algorithm 1 top-down branch) or bottom-up (every unvisited
+ * vertex looks for a neighbour in the frontier and stops at the first one,
+ * Algorithm 1 bottom-up branch), and the direction switches between the two
+ * from frontier vertex and edge counts (Sec. 3.3). Here the whole graph lives
+ * in one GPU's memory; every step runs in this library's CUDA kernels and
+ * the direction is chosen on the device, so a level needs no host round trip.
+ *
+ * Conventions
+ *  - Every function returns a dobfs_status; nothing throws or aborts across
+ *    this boundary. dobfs_last_error() describes the last failure of the
+ *    calling thread.
+ *  - Vertex IDs at this boundary are the caller's IDs ("original IDs"),
+ *    int32 in [0, n_vertices). A graph built with DOBFS_GRAPH_REINDEX
+ *    renumbers vertices internally; outputs are always in original IDs.
+ *  - Output conventions (the paper states none): an unreached vertex has
+ *    level -1 and parent -1; level[root] = 0 and parent[root] = root.
+ *  - Pointers are host or device pointers; the library tells them apart with
+ *    cudaPointerGetAttributes unless a flag says otherwise. Caller memory is
+ *    never freed by the library. Input arrays are copied; output arrays must
+ *    stay valid until the call (or, for the server, the poll) has completed.
+ *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream). Calls on one graph are serialised by the
+ *    library: a run on another stream first waits for the previous run.
+ */
+#ifndef DOBFS_H
+#define DOBFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DOBFS_OK = 0,
+  DOBFS_PENDING = 1,          /* server query not finished yet */
+  DOBFS_ERR_INVALID = -1,     /* bad argument (NULL handle, root out of range, size < 0, ...) */
+  DOBFS_ERR_OOM = -2,         /* device allocation failed */
+  DOBFS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  DOBFS_ERR_BAD_GRAPH = -4,   /* column out of range, or asymmetric input under VALIDATE */
+  DOBFS_ERR_TIMEOUT = -5,     /* a bounded device or host wait ran out */
+  DOBFS_ERR_BUSY = -6         /* admission refused: no free slot or not enough free memory */
+} dobfs_status;
+
+typedef struct dobfs_graph dobfs_graph;
+
+/* ------------------------------------------------------------------ memory */
+
+/* Device allocator hook. Every device buffer the library owns (graph CSR,
+ * per-graph BFS workspace, build scratch) comes from `alloc` and goes back
+ * through `free`. `alloc` returns NULL on failure (the call then fails with
+ * DOBFS_ERR_OOM). Passing NULLs restores the default (cudaMalloc/cudaFree).
+ * Process-wide; set it before creating graphs. The Python binding installs
+ * PyTorch's caching allocator here. */
+typedef void* (*dobfs_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*dobfs_free_fn)(void* ptr, void* stream, void* ctx);
+int dobfs_set_allocator(dobfs_alloc_fn alloc, dobfs_free_fn free_fn, void* ctx);
+
+/* Thread-local text of the last failure ("" if none). */
+const char* dobfs_last_error(void);
+
+/* ------------------------------------------------------------------ graphs */
+
+/* Graph build flags. */
+#define DOBFS_GRAPH_SYMMETRIZE 0x1u   /* add v->u for every stored u->v */
+#define DOBFS_GRAPH_REINDEX 0x2u      /* degree-sorted renumbering (Sec. 3.4) */
+#define DOBFS_GRAPH_DEVICE_PTRS 0x4u  /* inputs are device pointers (skip detection) */
+#define DOBFS_GRAPH_VALIDATE 0x8u     /* reject input that is not symmetric */
+#define DOBFS_GRAPH_OFFSETS64 0x10u   /* store int64 row offsets even if int32 would do */
+
+/*
+ * Builds a graph from CSR arrays: row_offsets[n_vertices+1] (int32, or int64
+ * if offsets_are_int64) and col_indices[n_entries] (int32). The stored graph
+ * is undirected CSR with each undirected edge held as two directed edges
+ * (Sec. 4, "Methodology"): self-loops and duplicate entries are dropped and
+ * each row is sorted. With DOBFS_GRAPH_SYMMETRIZE the reverse of every entry
+ * is added first; without it the input must already be symmetric, which
+ * DOBFS_GRAPH_VALIDATE checks (DOBFS_ERR_BAD_GRAPH otherwise).
+ * With DOBFS_GRAPH_REINDEX vertices are renumbered by decreasing degree (ties
+ * by increasing original ID) and every row is sorted by the new IDs, which
+ * puts the highest-degree neighbour first (Sec. 3.4).
+ * Row offsets are stored as int32 when the entry count fits, else int64.
+ * Errors: DOBFS_ERR_INVALID (n_vertices < 1 or > 2^31-1, negative sizes,
+ * NULL pointers with n_entries > 0), DOBFS_ERR_BAD_GRAPH (column or offset
+ * out of range), DOBFS_ERR_OOM, DOBFS_ERR_CUDA. On success *out owns all
+ * device memory of the graph; release it with dobfs_graph_destroy.
+ * The build runs on `stream`; the call returns once the graph is ready.
+ */
+int dobfs_graph_create(const void* row_offsets, int offsets_are_int64, const int32_t* col_indices,
+                       int64_t n_vertices, int64_t n_entries, uint32_t flags, void* stream,
+                       dobfs_graph** out);
+
+/*
+ * Builds a graph from n_pairs undirected pairs (src[i], dst[i]) (int32 IDs in
+ * [0, n_vertices)): every pair u != v is stored both ways, self-loops and
+ * duplicates dropped. Flags as for dobfs_graph_create (SYMMETRIZE is implied).
+ */
+int dobfs_graph_create_from_pairs(const int32_t* src, const int32_t* dst, int64_t n_pairs,
+                                  int64_t n_vertices, uint32_t flags, void* stream, dobfs_graph** out);
+
+/*
+ * Builds the R-MAT graph of `scale` (2^scale vertices, n_pairs undirected
+ * pairs) drawn on the device by the seeded counter-based generator of
+ * dobfs_inputs/gen.h, the stand-in for the Graph500 generator of Sec. 4
+ * ("Workloads"): quadrant cut points t_a <= t_ab <= t_abc on a 32-bit uniform
+ * draw (floor(2^32 * A), floor(2^32 * (A+B)), floor(2^32 * (A+B+C))),
+ * endpoints relabelled by the seeded bijection. scale in [1, 31].
+ */
+int dobfs_graph_create_rmat(int scale, int64_t n_pairs, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
+                            uint64_t seed, uint32_t flags, void* stream, dobfs_graph** out);
+
+/*
+ * Builds a Chung-Lu graph on n_vertices vertices from n_pairs pairs whose
+ * endpoints are drawn with probability proportional to the integer weights
+ * given as the inclusive cumulative table cdf[n_vertices] (host memory,
+ * non-decreasing, cdf[n-1] > 0), relabelled by the seeded bijection.
+ */
+int dobfs_graph_create_chunglu(const uint64_t* cdf, int64_t n_vertices, int64_t n_pairs, uint64_t seed,
+                               uint32_t flags, void* stream, dobfs_graph** out);
+
+int dobfs_graph_destroy(dobfs_graph* g);
+
+typedef struct {
+  int64_t n_vertices;
+  int64_t n_entries;        /* stored directed entries (2 x undirected edges) */
+  int64_t n_nonisolated;    /* vertices with degree >= 1 */
+  int64_t max_degree;
+  int32_t offsets_int64;    /* 1 if row offsets are stored as int64 */
+  int32_t reindexed;        /* 1 if DOBFS_GRAPH_REINDEX was applied */
+  int64_t device_bytes;     /* graph + BFS workspace held on the device */
+  float build_ms;           /* device time of the build */
+} dobfs_graph_info;
+
+int dobfs_graph_get_info(const dobfs_graph* g, dobfs_graph_info* info);
+
+/*
+ * Copies the stored CSR out in the internal vertex order: offsets_out[n+1]
+ * (int64), cols_out[n_entries] (int32), new2orig_out[n] (int32; internal ID
+ * -> original ID, identity when not reindexed). Any of the three may be NULL.
+ * Host or device pointers.
+ */
+int dobfs_graph_export(const dobfs_graph* g, int64_t* offsets_out, int32_t* cols_out, int32_t* new2orig_out,
+                       void* stream);
+
+/* Degree of every vertex, indexed by original ID: deg_out[n] (int32, host or device). */
+int dobfs_graph_degrees(const dobfs_graph* g, int32_t* deg_out, void* stream);
+
+/* ------------------------------------------------------------------ single-source runs */
+
+/* Direction policy for a level. */
+#define DOBFS_DIR_AUTO 0        /* alpha/beta heuristic on the device (default) */
+#define DOBFS_DIR_TOPDOWN 1     /* every level top-down */
+#define DOBFS_DIR_BOTTOMUP 2    /* every level bottom-up */
+#define DOBFS_DIR_RANDOM 3      /* seeded coin per level (exercises every switch; testing) */
+#define DOBFS_DIR_STATIC 4      /* the paper's policy (Sec. 3.3): the next frontier is
+                                   estimated as static_pct percent of the edges out of the
+                                   current one; top-down until that estimate exceeds n/beta,
+                                   then bottom-up for bu_steps levels, then top-down */
+
+/* Run flags. */
+#define DOBFS_RUN_CANONICAL_PARENT 0x1u /* parent = smallest original-ID neighbour one level up */
+#define DOBFS_RUN_HOST_LOOP 0x2u        /* drive levels from the host and time every kernel
+                                           (diagnostics; adds one host round trip per level) */
+#define DOBFS_RUN_SYNC_STATS 0x4u       /* wait for completion and fill *stats */
+
+typedef struct {
+  int32_t direction;        /* DOBFS_DIR_* */
+  int32_t alpha;            /* top-down -> bottom-up when m_f * alpha > m_u (default 14) */
+  int32_t beta;             /* bottom-up -> top-down when n_f * beta < n and shrinking (default 24) */
+  int32_t static_pct;       /* DOBFS_DIR_STATIC: percent of frontier out-edges (default 10) */
+  int32_t bu_steps;         /* DOBFS_DIR_STATIC: bottom-up levels before returning (default 3) */
+  uint32_t flags;           /* DOBFS_RUN_* */
+  uint64_t schedule_seed;   /* DOBFS_DIR_RANDOM */
+  void* stream;             /* cudaStream_t (NULL: the graph's creation stream) */
+} dobfs_run_opts;
+
+typedef struct {
+  float device_ms;          /* CUDA-event time from status init to outputs written */
+  int32_t levels;           /* number of BFS levels (max level + 1) */
+  int32_t td_levels;        /* levels expanded top-down */
+  int32_t bu_levels;        /* levels expanded bottom-up */
+  int64_t reached;          /* vertices reached */
+  int64_t teps_edges;       /* undirected edges in the root's component */
+  int64_t edges_examined;   /* adjacency entries read by the level kernels */
+  int64_t alg_bytes;        /* algorithmic DRAM bytes of the run (see DESIGN notes) */
+} dobfs_run_stats;
+
+/* Fills *opts with the defaults. */
+int dobfs_run_opts_init(dobfs_run_opts* opts);
+
+/*
+ * One BFS from `root` (original ID). level_out[n] and parent_out[n] (int32,
+ * indexed by original ID; parent_out may be NULL) receive the BFS level and
+ * a BFS parent (any frontier neighbour one level up, or the canonical one
+ * with DOBFS_RUN_CANONICAL_PARENT). Host or device pointers. Asynchronous on
+ * the run's stream unless stats are requested (DOBFS_RUN_SYNC_STATS or a
+ * non-NULL stats) or the outputs are host memory.
+ * Errors: DOBFS_ERR_INVALID (NULL graph/level_out, root out of range, bad
+ * opts), DOBFS_ERR_CUDA, DOBFS_ERR_OOM (host-output staging).
+ */
+int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_out,
+              const dobfs_run_opts* opts, dobfs_run_stats* stats);
+
+/* Per-level record of the last run on a graph (ready after that run completed). */
+typedef struct {
+  int32_t level;            /* level L being expanded (frontier = vertices at level L) */
+  int32_t direction;        /* 0 top-down, 1 bottom-up */
+  int64_t n_frontier;       /* n_f: vertices at level L */
+  int64_t m_frontier;       /* m_f: sum of their degrees */
+  int64_t m_unvisited;      /* m_u: sum of degrees of unvisited vertices before the step */
+  int64_t n_next;           /* vertices discovered (level L+1) */
+  int64_t edges_examined;
+  int64_t vertices_scanned; /* bottom-up: unvisited vertices scanned */
+  int64_t alg_bytes;
+  float ms;                 /* host-loop runs only: device time of the level's kernels, else 0 */
+  float ms_main;            /* host-loop runs only: time of the main expand kernel */
+} dobfs_level_trace;
+
+/* Copies up to max_levels records of the last run; *n_out = records written. */
+int dobfs_last_trace(const dobfs_graph* g, dobfs_level_trace* out, int32_t max_levels, int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOBFS_H */

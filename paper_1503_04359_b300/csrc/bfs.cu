@@ -1,0 +1,860 @@
+// Direction-optimized BFS on one GPU: the per-level step of Algorithm 1 with
+// the direction switch of Sec. 3.3, all on the device.
+//
+// State in HBM (internal vertex IDs):
+//   visited  bitmap, one bit per vertex (the isVisited flag of Algorithm 1)
+//   fbm[2]   frontier bitmaps, level parity selects current / next
+//   q[2]     frontier queues (int32), level parity selects current / next
+//   lp       int2 per vertex: (level, parent), written once when discovered
+//   ctl      BfsCtl: frontier counts n_f, m_f, unvisited edge count m_u, ...
+//
+// One level = one "step":
+//   top-down  (Algorithm 1, top-down branch): every frontier vertex reads its
+//             row and claims unvisited neighbours with atomicOr on the visited
+//             bitmap; the winner writes (level, parent) and appends the vertex
+//             to the next queue. Rows of up to kTdSmall entries are expanded
+//             by one thread in the binning kernel; longer rows are cut into
+//             kChunk-entry records expanded one warp each with 16-byte loads.
+//   bottom-up (Algorithm 1, bottom-up branch): a warp owns one visited-bitmap
+//             word (32 consecutive vertices); each unvisited vertex scans its
+//             row in order and stops at the first neighbour whose frontier
+//             bit is set. The warp writes the next-frontier word and the
+//             visited word with one store each (ballot), no atomics. Rows
+//             with no hit among their first kBuT entries continue in a
+//             warp-per-row kernel (16-byte loads, ballot for the first hit).
+//   switch    (Sec. 3.3): a one-thread kernel folds the step's counters into
+//             n_f, m_f, m_u and picks the next direction: top-down -> bottom-up
+//             when m_f * alpha > m_u, bottom-up -> top-down when the frontier
+//             shrinks below n / beta (the alpha/beta rule of the direction-
+//             optimizing BFS the paper builds on), or the paper's own static
+//             policy. Conversions (queue -> bitmap, bitmap -> queue) run only
+//             when the direction changes.
+// The level loop is a CUDA graph: a while node whose body is the switch
+// kernel followed by a switch node over the four step kinds, so the host
+// launches one graph per BFS and never waits between levels.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../dobfs_inputs/gen.h"
+#include "common.cuh"
+#include "graph.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dobfs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTdSmall = 16;   // top-down rows up to this length: one thread
+constexpr int kChunk = 512;    // top-down chunk record length (entries)
+constexpr int kBuT = 32;       // bottom-up entries scanned per thread before deferring
+constexpr int kCaseNone = 7;   // switch value with no body: loop ends
+
+template <class OffT>
+struct BfsArgs {
+  const OffT* off;
+  const int32_t* cols;
+  const uint32_t* iso;
+  const int32_t* o2n;  // NULL when not reindexed
+  uint32_t* visited;
+  uint32_t* fbm0;
+  uint32_t* fbm1;
+  int2* lp;
+  int32_t* q0;
+  int32_t* q1;
+  int2* rec;
+  int32_t* def;
+  BfsCtl* ctl;
+  LevelRec* trace;
+  int64_t n, nnz, words, cand_words, rec_cap;
+};
+
+__device__ __forceinline__ bool test_bit(const uint32_t* __restrict__ bm, int32_t v) {
+  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Appends v to q at an index taken from *tail, one atomic per group of
+// converged threads.
+__device__ __forceinline__ void enqueue(unsigned int* tail, int32_t* q, int32_t v) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
+  base = g.shfl(base, 0);
+  q[base + g.thread_rank()] = v;
+}
+
+// Top-down claim of neighbour v by frontier vertex u (Algorithm 1, top-down
+// branch): the first thread to set v's visited bit writes level and parent
+// and enqueues v; its degree goes into the next frontier's edge count m_f.
+template <class OffT>
+__device__ __forceinline__ void td_claim(const BfsArgs<OffT>& A, int32_t v, int32_t u, int32_t next_level,
+                                         int32_t* nq, unsigned long long& m_new) {
+  const uint32_t bit = 1u << (v & 31);
+  uint32_t* w = A.visited + (v >> 5);
+  if (__ldcg(w) & bit) return;
+  if (atomicOr(w, bit) & bit) return;
+  A.lp[v] = make_int2(next_level, u);
+  m_new += (unsigned long long)((int64_t)A.off[v + 1] - (int64_t)A.off[v]);
+  enqueue(&A.ctl->q_tail, nq, v);
+}
+
+template <class OffT>
+__global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t alpha, int32_t beta,
+                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int32_t r = A.o2n ? A.o2n[root_orig] : root_orig;
+  const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
+  BfsCtl* c = A.ctl;
+  c->level = 0;
+  c->dir = 0;
+  c->fmt = 0;
+  c->step_case = 0;
+  c->fresh = 1;
+  c->done = 0;
+  c->bu_run = 0;
+  c->n_levels = 0;
+  c->n_f = 1;
+  c->m_f = d;
+  c->n_f_prev = 0;
+  c->m_u = A.nnz - d;
+  c->nx_n = c->nx_m = c->nx_examined = c->nx_scanned = 0;
+  c->q_tail = c->n_rec = c->n_def = c->conv_tail = 0;
+  c->reached = 1;
+  c->teps2 = d;
+  c->examined = 0;
+  c->alg_bytes = 0;
+  c->n_td = c->n_bu = 0;
+  c->overflow = 0;
+  c->mode = mode;
+  c->alpha = alpha;
+  c->beta = beta;
+  c->static_pct = static_pct;
+  c->bu_steps = bu_steps;
+  c->sched_seed = sched_seed;
+  A.q0[0] = r;
+  A.visited[r >> 5] |= 1u << (r & 31);
+  A.lp[r] = make_int2(0, r);
+}
+
+// The direction switch: closes the step that just ran, then picks the next.
+template <class OffT>
+__global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
+                         int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  BfsCtl* c = A.ctl;
+  if (!c->fresh) {
+    const int32_t L = c->level;
+    const int64_t n_new = (c->dir == 0) ? (int64_t)c->q_tail : (int64_t)c->nx_n;
+    const int64_t m_new = (int64_t)c->nx_m;
+    const int64_t ex = (int64_t)c->nx_examined, sc = (int64_t)c->nx_scanned;
+    int64_t bytes;
+    if (c->dir == 0)  // queue read 4, row bounds 16, columns 4 each, level+parent 8 and enqueue 4 per new vertex
+      bytes = 20 * c->n_f + 4 * c->m_f + 12 * n_new + (c->step_case == 2 ? 4 * c->n_f : 0);
+    else  // row bounds 8 per scanned vertex, columns 4 each read, level+parent 8 per new vertex
+      bytes = 8 * sc + 4 * ex + 8 * n_new + (c->step_case == 3 ? 4 * c->n_f : 0);
+    if (L < kMaxTrace) {
+      LevelRec& t = A.trace[L];
+      t.level = L;
+      t.dir = c->dir;
+      t.n_f = c->n_f;
+      t.m_f = c->m_f;
+      t.m_u = c->m_u;
+      t.n_next = n_new;
+      t.examined = ex;
+      t.scanned = sc;
+      t.bytes = bytes;
+    }
+    c->alg_bytes += bytes;
+    c->examined += ex;
+    if (c->dir == 0) c->n_td += 1; else c->n_bu += 1;
+    c->m_u -= m_new;
+    c->teps2 += m_new;
+    c->reached += n_new;
+    c->n_f_prev = c->n_f;
+    c->n_f = n_new;
+    c->m_f = m_new;
+    c->level = L + 1;
+    c->fmt = c->dir;  // top-down leaves a queue, bottom-up a bitmap
+    c->bu_run = (c->dir == 1) ? c->bu_run + 1 : 0;
+    c->nx_n = c->nx_m = c->nx_examined = c->nx_scanned = 0;
+    c->q_tail = c->n_rec = c->n_def = c->conv_tail = 0;
+  }
+  const int prev_dir = c->fresh ? 0 : c->dir;
+  c->fresh = 0;
+  if (c->n_f == 0) {
+    c->done = 1;
+    c->n_levels = c->level;
+    if (in_graph) {
+      cudaGraphSetConditional(h_case, kCaseNone);
+      cudaGraphSetConditional(h_while, 0);
+    }
+    return;
+  }
+  int dir = 0;
+  switch (c->mode) {
+    case DOBFS_DIR_TOPDOWN: dir = 0; break;
+    case DOBFS_DIR_BOTTOMUP: dir = 1; break;
+    case DOBFS_DIR_RANDOM: dir = (int)(gen_mix64(c->sched_seed ^ (uint64_t)c->level) & 1ull); break;
+    case DOBFS_DIR_STATIC:
+      if (prev_dir == 0) {
+        // next frontier estimated as static_pct percent of the frontier's out-edges
+        const int64_t est = c->m_f * (int64_t)c->static_pct / 100;
+        dir = (est * (int64_t)c->beta > A.n) ? 1 : 0;
+      } else {
+        dir = (c->bu_run >= c->bu_steps) ? 0 : 1;
+      }
+      break;
+    default:  // alpha/beta
+      if (prev_dir == 0)
+        dir = (c->m_f * (int64_t)c->alpha > c->m_u) ? 1 : 0;
+      else
+        dir = (c->n_f * (int64_t)c->beta < A.n && c->n_f < c->n_f_prev) ? 0 : 1;
+      break;
+  }
+  const int kase = (dir == 0) ? (c->fmt == 0 ? 0 : 2) : (c->fmt == 1 ? 1 : 3);
+  c->dir = dir;
+  c->step_case = kase;
+  if (in_graph) cudaGraphSetConditional(h_case, (unsigned)kase);
+}
+
+// Top-down, part 1: short rows expanded in place, long rows cut into
+// chunk records.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const BfsCtl* c = A.ctl;
+  const int32_t L = c->level;
+  const int64_t nf = c->n_f;
+  const int32_t* cur = (L & 1) ? A.q1 : A.q0;
+  int32_t* nxt = (L & 1) ? A.q0 : A.q1;
+  unsigned long long m_new = 0, ex = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = cur[i];
+    const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+    ex += (unsigned long long)(e - s);
+    if (e - s <= kTdSmall) {
+      for (int64_t j = s; j < e; ++j) td_claim(A, A.cols[j], u, L + 1, nxt, m_new);
+    } else {
+      const int64_t a = s & ~3ll;
+      const unsigned nch = (unsigned)ceil_div(e - a, kChunk);
+      const unsigned base = atomicAdd(&A.ctl->n_rec, nch);
+      if ((int64_t)base + nch > A.rec_cap) {
+        A.ctl->overflow = 1;
+        continue;
+      }
+      for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2(u, (int)k);
+    }
+  }
+  m_new = block_sum_u64(m_new, sh);
+  ex = block_sum_u64(ex, sh);
+  if (threadIdx.x == 0) {
+    if (m_new) atomicAdd(&A.ctl->nx_m, m_new);
+    if (ex) atomicAdd(&A.ctl->nx_examined, ex);
+  }
+}
+
+// Top-down, part 2: one warp per chunk record, 16-byte column loads.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const BfsCtl* c = A.ctl;
+  const int32_t L = c->level;
+  const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
+  int32_t* nxt = (L & 1) ? A.q0 : A.q1;
+  unsigned long long m_new = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const unsigned lane = lane_id();
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
+    const int2 rc = A.rec[r];
+    const int32_t u = rc.x;
+    const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+    const int64_t lo = (s & ~3ll) + (int64_t)rc.y * kChunk;
+    const int64_t hi = min(e, lo + kChunk);
+    const int64_t lo_ok = max(s, lo);
+    for (int64_t p = lo + 4 * (int64_t)lane; p < hi; p += 128) {
+      const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
+      const int32_t vs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t idx = p + t;
+        if (idx >= lo_ok && idx < hi) td_claim(A, vs[t], u, L + 1, nxt, m_new);
+      }
+    }
+  }
+  m_new = block_sum_u64(m_new, sh);
+  if (threadIdx.x == 0 && m_new) atomicAdd(&A.ctl->nx_m, m_new);
+}
+
+// Frontier bitmap of level L -> queue of level L (after a bottom-up level,
+// before a top-down one). A warp converts 32 consecutive words.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_bitmap_to_queue(BfsArgs<OffT> A) {
+  const int32_t L = A.ctl->level;
+  const uint32_t* bm = (L & 1) ? A.fbm1 : A.fbm0;
+  int32_t* q = (L & 1) ? A.q1 : A.q0;
+  const unsigned lane = lane_id();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; w0 < A.cand_words; w0 += stride) {
+    const int64_t w = w0 + lane;
+    uint32_t x = (w < A.cand_words) ? bm[w] : 0u;
+    const unsigned cnt = (unsigned)__popc(x);
+    unsigned inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(&A.ctl->conv_tail, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + inc - cnt;
+    while (x) {
+      const int b = __ffs(x) - 1;
+      x &= x - 1;
+      q[pos++] = (int32_t)(w * 32 + b);
+    }
+  }
+}
+
+// Queue of level L -> frontier bitmap of level L (after a top-down level,
+// before a bottom-up one). Both bitmaps were cleared just before.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
+  const int32_t L = A.ctl->level;
+  const int64_t nf = A.ctl->n_f;
+  uint32_t* bm = (L & 1) ? A.fbm1 : A.fbm0;
+  const int32_t* q = (L & 1) ? A.q1 : A.q0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = q[i];
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+  }
+}
+
+// Bottom-up, part 1 (Algorithm 1, bottom-up branch): one warp per visited
+// word; every unvisited vertex scans its first kBuT neighbours in row order
+// and stops at the first one in the frontier.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_bu(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const BfsCtl* c = A.ctl;
+  const int32_t L = c->level;
+  const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
+  uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
+  const unsigned lane = lane_id();
+  unsigned long long n_new = 0, m_new = 0, ex = 0, sc = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < A.cand_words; w += warps) {
+    const uint32_t vis = A.visited[w];
+    const uint32_t skip = vis | A.iso[w];
+    const bool cand = !((skip >> lane) & 1u);
+    bool found = false;
+    int32_t parent = -1;
+    int64_t deg = 0;
+    if (cand) {
+      const int32_t v = (int32_t)(w * 32 + lane);
+      const int64_t s = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      deg = e - s;
+      const int64_t lim = min(e, s + kBuT);
+      int64_t j = s;
+      for (; j < lim; ++j) {
+        const int32_t u = A.cols[j];
+        if (test_bit(front, u)) {
+          found = true;
+          parent = u;
+          break;
+        }
+      }
+      ex += (unsigned long long)(found ? j - s + 1 : lim - s);
+      if (!found && e > lim) enqueue(&A.ctl->n_def, A.def, v);
+      if (found) A.lp[v] = make_int2(L + 1, parent);
+    }
+    const unsigned fm = __ballot_sync(0xffffffffu, found);
+    const unsigned cm = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) {
+      next[w] = fm;
+      if (fm) A.visited[w] = vis | fm;
+      n_new += (unsigned)__popc(fm);
+      sc += (unsigned)__popc(cm);
+    }
+    if (found) m_new += (unsigned long long)deg;
+  }
+  n_new = block_sum_u64(n_new, sh);
+  m_new = block_sum_u64(m_new, sh);
+  ex = block_sum_u64(ex, sh);
+  sc = block_sum_u64(sc, sh);
+  if (threadIdx.x == 0) {
+    if (n_new) atomicAdd(&A.ctl->nx_n, n_new);
+    if (m_new) atomicAdd(&A.ctl->nx_m, m_new);
+    if (ex) atomicAdd(&A.ctl->nx_examined, ex);
+    if (sc) atomicAdd(&A.ctl->nx_scanned, sc);
+  }
+}
+
+// Bottom-up, part 2: rows with no frontier neighbour among their first kBuT
+// entries; one warp per row, 16-byte loads, the ballot picks the first hit
+// in row order.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const BfsCtl* c = A.ctl;
+  const int32_t L = c->level;
+  const int64_t nd = c->n_def;
+  const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
+  uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
+  const unsigned lane = lane_id();
+  unsigned long long n_new = 0, m_new = 0, ex = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
+    const int32_t v = A.def[i];
+    const int64_t s0 = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    const int64_t s = s0 + kBuT;
+    int32_t parent = -1;
+    for (int64_t base = s & ~3ll; base < e; base += 128) {
+      const int64_t p = base + 4 * (int64_t)lane;
+      int32_t hit = -1;
+      if (p < e) {
+        const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
+        const int32_t us[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t idx = p + t;
+          if (hit < 0 && idx >= s && idx < e && test_bit(front, us[t])) hit = us[t];
+        }
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, hit >= 0);
+      { const int64_t span = min(e, base + 128) - max(s, base); ex += (unsigned long long)(span > 0 ? span : 0); }
+      if (b) {
+        parent = __shfl_sync(0xffffffffu, hit, __ffs(b) - 1);
+        break;
+      }
+    }
+    if (parent >= 0 && lane == 0) {
+      atomicOr(next + (v >> 5), 1u << (v & 31));
+      atomicOr(A.visited + (v >> 5), 1u << (v & 31));
+      A.lp[v] = make_int2(L + 1, parent);
+      n_new += 1;
+      m_new += (unsigned long long)(e - s0);
+    }
+  }
+  if (lane != 0) ex = 0;
+  n_new = block_sum_u64(n_new, sh);
+  m_new = block_sum_u64(m_new, sh);
+  ex = block_sum_u64(ex, sh);
+  if (threadIdx.x == 0) {
+    if (n_new) atomicAdd(&A.ctl->nx_n, n_new);
+    if (m_new) atomicAdd(&A.ctl->nx_m, m_new);
+    if (ex) atomicAdd(&A.ctl->nx_examined, ex);
+  }
+}
+
+// Results in original IDs: level_out[o], parent_out[o] for every vertex.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
+                                                     int32_t* __restrict__ level_out,
+                                                     int32_t* __restrict__ parent_out) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = A.o2n ? A.o2n[o] : (int32_t)o;
+    int32_t lev = -1, par = -1;
+    if ((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u) {
+      const int2 x = A.lp[v];
+      lev = x.x;
+      par = n2o ? n2o[x.y] : x.y;
+    }
+    level_out[o] = lev;
+    if (parent_out) parent_out[o] = par;
+  }
+}
+
+// Canonical parent: smallest original-ID neighbour one level up. One warp
+// per vertex, over the full row.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_canonical_parent(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
+                                                               int32_t* __restrict__ parent_out) {
+  const unsigned lane = lane_id();
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < A.n; v += warps) {
+    if (!((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u)) continue;
+    const int32_t lev = A.lp[v].x;
+    if (lev <= 0) continue;
+    const int64_t s = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    int32_t best = INT32_MAX;
+    for (int64_t j = s + lane; j < e; j += 32) {
+      const int32_t u = A.cols[j];
+      if (((__ldg(A.visited + (u >> 5)) >> (u & 31)) & 1u) && A.lp[u].x == lev - 1) {
+        const int32_t o = n2o ? n2o[u] : u;
+        best = min(best, o);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
+    if (lane == 0) parent_out[n2o ? n2o[v] : v] = best;
+  }
+}
+
+int grid_cap(int per_sm) { return sm_count() * per_sm; }
+
+template <class OffT>
+BfsArgs<OffT> make_args(dobfs_graph* g) {
+  BfsArgs<OffT> A;
+  A.off = g->off.as<OffT>();
+  A.cols = g->cols.as<int32_t>();
+  A.iso = g->isolated.as<uint32_t>();
+  A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
+  A.visited = g->visited.as<uint32_t>();
+  A.fbm0 = g->fbm0.as<uint32_t>();
+  A.fbm1 = g->fbm1.as<uint32_t>();
+  A.lp = g->lp.as<int2>();
+  A.q0 = g->q0.as<int32_t>();
+  A.q1 = g->q1.as<int32_t>();
+  A.rec = g->rec.as<int2>();
+  A.def = g->deferred.as<int32_t>();
+  A.ctl = g->ctl.as<BfsCtl>();
+  A.trace = g->trace.as<LevelRec>();
+  A.n = g->n;
+  A.nnz = g->nnz;
+  A.words = g->words;
+  // vertices past the last one with an edge are never candidates; with
+  // degree-sorted IDs these are all isolated vertices
+  A.cand_words = g->reindexed ? ceil_div(std::max<int64_t>(g->n_nonisolated, 1), 32) : g->words;
+  A.rec_cap = g->rec_cap;
+  return A;
+}
+
+// Grid sizes of the level kernels (fixed: the work sizes live on the device).
+struct Grids {
+  int td_bin, td_chunks, conv, bu, bu_long;
+};
+Grids grids() {
+  Grids G;
+  G.td_bin = grid_cap(8);
+  G.td_chunks = grid_cap(8);
+  G.conv = grid_cap(8);
+  G.bu = grid_cap(8);
+  G.bu_long = grid_cap(8);
+  return G;
+}
+
+// Enqueues the kernels of step kind `kase` on s (used both for graph capture
+// and for host-driven levels).
+template <class OffT>
+int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t main_begin,
+                cudaEvent_t main_end) {
+  const Grids G = grids();
+  const size_t bm_bytes = sizeof(uint32_t) * (size_t)g->words;
+  switch (kase) {
+    case 0:
+    case 2:
+      if (kase == 2) k_bitmap_to_queue<OffT><<<G.conv, kThreads, 0, s>>>(A);
+      if (main_begin) cudaEventRecord(main_begin, s);
+      k_td_bin<OffT><<<G.td_bin, kThreads, 0, s>>>(A);
+      k_td_chunks<OffT><<<G.td_chunks, kThreads, 0, s>>>(A);
+      if (main_end) cudaEventRecord(main_end, s);
+      break;
+    case 1:
+    case 3:
+      if (kase == 3) {
+        DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm0.ptr, 0, bm_bytes, s));
+        DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm1.ptr, 0, bm_bytes, s));
+        k_queue_to_bitmap<OffT><<<G.conv, kThreads, 0, s>>>(A);
+      }
+      if (main_begin) cudaEventRecord(main_begin, s);
+      k_bu<OffT><<<G.bu, kThreads, 0, s>>>(A);
+      k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
+      if (main_end) cudaEventRecord(main_end, s);
+      break;
+    default:
+      break;
+  }
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int build_level_graph(dobfs_graph* g) {
+  const BfsArgs<OffT> A = make_args<OffT>(g);
+  cudaStream_t cs = nullptr;
+  DOBFS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  auto fail = [&](int rc) {
+    cudaStreamDestroy(cs);
+    if (g->cg) cudaGraphDestroy(g->cg);
+    g->cg = nullptr;
+    return rc;
+  };
+  if (cudaGraphCreate(&g->cg, 0) != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "cudaGraphCreate failed"));
+  cudaGraphConditionalHandle h_while, h_case;
+  if (cudaGraphConditionalHandleCreate(&h_while, g->cg, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "conditional handle (while) failed"));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_while;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (cudaGraphAddNode(&wnode, g->cg, nullptr, nullptr, 0, &wp) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "while node failed: %s", cudaGetErrorString(cudaGetLastError())));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  if (cudaGraphConditionalHandleCreate(&h_case, body, 0, 0) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "conditional handle (switch) failed"));
+  // body: the switch kernel ...
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "capture to body failed"));
+  k_switch<OffT><<<1, 32, 0, cs>>>(A, h_while, h_case, 1);
+  cudaGraph_t captured = nullptr;
+  if (cudaStreamEndCapture(cs, &captured) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "end capture (body) failed"));
+  size_t nn = 0;
+  cudaGraphGetNodes(body, nullptr, &nn);
+  if (nn != 1) return fail(set_error(DOBFS_ERR_CUDA, "unexpected body node count %zu", nn));
+  cudaGraphNode_t heur;
+  cudaGraphGetNodes(body, &heur, &nn);
+  // ... then a switch over the four step kinds
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = h_case;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = 4;
+  cudaGraphNode_t snode;
+  if (cudaGraphAddNode(&snode, body, &heur, nullptr, 1, &sp) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "switch node failed: %s", cudaGetErrorString(cudaGetLastError())));
+  for (int k = 0; k < 4; ++k) {
+    if (cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return fail(set_error(DOBFS_ERR_CUDA, "capture to case %d failed", k));
+    int rc = launch_case<OffT>(g, A, k, cs, nullptr, nullptr);
+    cudaGraph_t cap = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &cap);
+    if (rc != DOBFS_OK) return fail(rc);
+    if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture case %d: %s", k, cudaGetErrorString(e)));
+  }
+  cudaError_t e = cudaGraphInstantiate(&g->cg_exec, g->cg, 0);
+  if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)));
+  cudaStreamDestroy(cs);
+  return DOBFS_OK;
+}
+
+// Host-driven levels: same kernels, one round trip per level, every level's
+// kernels timed with events (diagnostics).
+template <class OffT>
+int host_loop(dobfs_graph* g, const BfsArgs<OffT>& A, cudaStream_t s) {
+  g->host_level_ms.clear();
+  g->host_level_main_ms.clear();
+  cudaEvent_t e0, e1, m0, m1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&m0);
+  cudaEventCreate(&m1);
+  int rc = DOBFS_OK;
+  for (int64_t it = 0; it <= g->n + 1; ++it) {
+    k_switch<OffT><<<1, 32, 0, s>>>(A, 0, 0, 0);
+    int32_t hdr[8];
+    if (cudaMemcpyAsync(hdr, g->ctl.ptr, sizeof(hdr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = set_error(DOBFS_ERR_CUDA, "host loop: control read failed");
+      break;
+    }
+    const int done = hdr[5], kase = hdr[3];
+    if (done) break;
+    cudaEventRecord(e0, s);
+    rc = launch_case<OffT>(g, A, kase, s, m0, m1);
+    cudaEventRecord(e1, s);
+    if (rc != DOBFS_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f, mm = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&mm, m0, m1);
+    g->host_level_ms.push_back(ms);
+    g->host_level_main_ms.push_back(mm);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(m0);
+  cudaEventDestroy(m1);
+  return rc;
+}
+
+template <class OffT>
+int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_out, const dobfs_run_opts& o,
+             dobfs_run_stats* stats) {
+  cudaStream_t s = (cudaStream_t)o.stream;
+  if (!s) s = g->stream;
+  const bool host_loop_mode = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
+  const bool want_stats = stats || (o.flags & DOBFS_RUN_SYNC_STATS);
+  const bool dev_level = is_device_ptr(level_out);
+  const bool dev_parent = parent_out == nullptr || is_device_ptr(parent_out);
+  if (dev_level != dev_parent)
+    return set_error(DOBFS_ERR_INVALID, "level_out and parent_out must both be host or both be device memory");
+  if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g));
+  const BfsArgs<OffT> A = make_args<OffT>(g);
+  int32_t* lv = level_out;
+  int32_t* pa = parent_out;
+  if (!dev_level) {
+    if (!g->out_stage.ptr) DOBFS_TRY(g->out_stage.alloc(sizeof(int32_t) * 2 * (size_t)g->n, g->stream));
+    lv = g->out_stage.as<int32_t>();
+    pa = parent_out ? lv + g->n : nullptr;
+  }
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
+  k_init<OffT><<<1, 32, 0, s>>>(A, root, o.direction, o.alpha, o.beta, o.static_pct, o.bu_steps, o.schedule_seed);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  if (host_loop_mode) {
+    DOBFS_TRY(host_loop<OffT>(g, A, s));
+  } else {
+    DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
+  }
+  const int out_grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
+  const int32_t* n2o = g->reindexed ? g->new2orig.as<int32_t>() : nullptr;
+  k_output<OffT><<<out_grid, kThreads, 0, s>>>(A, n2o, lv, pa);
+  if (pa && (o.flags & DOBFS_RUN_CANONICAL_PARENT))
+    k_canonical_parent<OffT><<<grid_cap(8), kThreads, 0, s>>>(A, n2o, pa);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  if (!dev_level) {
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(level_out, lv, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+    if (parent_out)
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(parent_out, pa, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  }
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t1, s));
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_done, s));
+  g->last_stream = s;
+  g->last_host_loop = host_loop_mode;
+  if (!dev_level) DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (want_stats) {
+    DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_t1));
+    BfsCtl c;
+    DOBFS_CUDA_TRY(cudaMemcpy(&c, g->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.overflow) return set_error(DOBFS_ERR_CUDA, "internal: top-down record buffer overflow");
+    if (stats) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, g->ev_t0, g->ev_t1);
+      stats->device_ms = ms;
+      stats->levels = c.n_levels;
+      stats->td_levels = c.n_td;
+      stats->bu_levels = c.n_bu;
+      stats->reached = c.reached;
+      stats->teps_edges = c.teps2 / 2;
+      stats->edges_examined = c.examined;
+      // output pass: 8 bytes written per vertex, the map read when renumbered,
+      // and the (level, parent) pair of every reached vertex
+      stats->alg_bytes = c.alg_bytes + 8 * g->n + (g->reindexed ? 4 * g->n : 0) + 8 * c.reached;
+    }
+  }
+  return DOBFS_OK;
+}
+
+}  // namespace
+
+int graph_alloc_workspace(dobfs_graph* g) {
+  cudaStream_t s = g->stream;
+  const size_t wb = sizeof(uint32_t) * (size_t)g->words;
+  DOBFS_TRY(g->visited.alloc(wb, s));
+  DOBFS_TRY(g->fbm0.alloc(wb, s));
+  DOBFS_TRY(g->fbm1.alloc(wb, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm0.ptr, 0, wb, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm1.ptr, 0, wb, s));
+  DOBFS_TRY(g->lp.alloc(sizeof(int2) * (size_t)g->n, s));
+  DOBFS_TRY(g->q0.alloc(sizeof(int32_t) * (size_t)g->n, s));
+  DOBFS_TRY(g->q1.alloc(sizeof(int32_t) * (size_t)g->n, s));
+  g->rec_cap = std::min<int64_t>(g->n, g->nnz / (kTdSmall + 1)) + g->nnz / kChunk + 64;
+  DOBFS_TRY(g->rec.alloc(sizeof(int2) * (size_t)g->rec_cap, s));
+  DOBFS_TRY(g->deferred.alloc(sizeof(int32_t) * (size_t)g->n, s));
+  DOBFS_TRY(g->ctl.alloc(sizeof(BfsCtl), s));
+  DOBFS_TRY(g->trace.alloc(sizeof(LevelRec) * kMaxTrace, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->ctl.ptr, 0, sizeof(BfsCtl), s));
+  DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_done));
+  DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_t0));
+  DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_t1));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  g->ws_ready = true;
+  return DOBFS_OK;
+}
+
+void graph_release(dobfs_graph* g) {
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
+  if (g->cg) cudaGraphDestroy(g->cg);
+  g->cg_exec = nullptr;
+  g->cg = nullptr;
+  if (g->ev_done) cudaEventDestroy(g->ev_done);
+  if (g->ev_t0) cudaEventDestroy(g->ev_t0);
+  if (g->ev_t1) cudaEventDestroy(g->ev_t1);
+  g->ev_done = g->ev_t0 = g->ev_t1 = nullptr;
+}
+
+}  // namespace dobfs
+
+using namespace dobfs;
+
+extern "C" {
+
+int dobfs_run_opts_init(dobfs_run_opts* o) {
+  if (!o) return set_error(DOBFS_ERR_INVALID, "opts is NULL");
+  o->direction = DOBFS_DIR_AUTO;
+  o->alpha = 14;
+  o->beta = 24;
+  o->static_pct = 10;
+  o->bu_steps = 3;
+  o->flags = 0;
+  o->schedule_seed = 0;
+  o->stream = nullptr;
+  return DOBFS_OK;
+}
+
+int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_out, const dobfs_run_opts* opts,
+              dobfs_run_stats* stats) {
+  clear_error();
+  if (!g || !level_out) return set_error(DOBFS_ERR_INVALID, "graph and level_out are required");
+  if (root < 0 || (int64_t)root >= g->n)
+    return set_error(DOBFS_ERR_INVALID, "root %d out of range [0, %lld)", root, (long long)g->n);
+  dobfs_run_opts o;
+  dobfs_run_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.direction < 0 || o.direction > DOBFS_DIR_STATIC || o.alpha < 1 || o.beta < 1 || o.static_pct < 0 ||
+      o.bu_steps < 1)
+    return set_error(DOBFS_ERR_INVALID, "bad run options");
+  std::lock_guard<std::mutex> lk(g->mu);
+  return g->off64 ? run_impl<int64_t>(g, root, level_out, parent_out, o, stats)
+                  : run_impl<int32_t>(g, root, level_out, parent_out, o, stats);
+}
+
+int dobfs_last_trace(const dobfs_graph* gc, dobfs_level_trace* out, int32_t max_levels, int32_t* n_out) {
+  if (!gc || !out || !n_out || max_levels < 0) return set_error(DOBFS_ERR_INVALID, "bad trace arguments");
+  dobfs_graph* g = const_cast<dobfs_graph*>(gc);
+  std::lock_guard<std::mutex> lk(g->mu);
+  DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
+  BfsCtl c;
+  DOBFS_CUDA_TRY(cudaMemcpy(&c, g->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost));
+  const int32_t n = std::min<int32_t>(std::min<int32_t>(c.n_levels, kMaxTrace), max_levels);
+  std::vector<LevelRec> rec((size_t)std::max(n, 0));
+  if (n > 0) DOBFS_CUDA_TRY(cudaMemcpy(rec.data(), g->trace.ptr, sizeof(LevelRec) * (size_t)n, cudaMemcpyDeviceToHost));
+  for (int32_t i = 0; i < n; ++i) {
+    out[i].level = rec[i].level;
+    out[i].direction = rec[i].dir;
+    out[i].n_frontier = rec[i].n_f;
+    out[i].m_frontier = rec[i].m_f;
+    out[i].m_unvisited = rec[i].m_u;
+    out[i].n_next = rec[i].n_next;
+    out[i].edges_examined = rec[i].examined;
+    out[i].vertices_scanned = rec[i].scanned;
+    out[i].alg_bytes = rec[i].bytes;
+    const bool timed = g->last_host_loop && (size_t)i < g->host_level_ms.size();
+    out[i].ms = timed ? g->host_level_ms[i] : 0.f;
+    out[i].ms_main = timed ? g->host_level_main_ms[i] : 0.f;
+  }
+  *n_out = n;
+  return DOBFS_OK;
+}
+
+int dobfs_graph_destroy(dobfs_graph* g) {
+  if (!g) return DOBFS_OK;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    graph_release(g);
+  }
+  delete g;
+  return DOBFS_OK;
+}
+
+}  // extern "C"

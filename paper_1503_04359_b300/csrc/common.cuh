@@ -1,0 +1,105 @@
+// Shared internals of libdobfs: status/error plumbing, the device allocator
+// hook, launch geometry and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/dobfs.h"
+
+namespace dobfs {
+
+// ------------------------------------------------------------------ errors
+// Thread-local last-error text plus a status code; every C entry point
+// returns the code of the first failure it met.
+int set_error(int status, const char* fmt, ...);
+void clear_error();
+
+#define DOBFS_CUDA_TRY(expr)                                                                   \
+  do {                                                                                          \
+    cudaError_t _e = (expr);                                                                    \
+    if (_e != cudaSuccess) {                                                                    \
+      return ::dobfs::set_error(DOBFS_ERR_CUDA, "%s failed at %s:%d: %s", #expr, __FILE__,      \
+                                __LINE__, cudaGetErrorString(_e));                              \
+    }                                                                                           \
+  } while (0)
+
+#define DOBFS_TRY(expr)        \
+  do {                         \
+    int _s = (expr);           \
+    if (_s != DOBFS_OK) {      \
+      return _s;               \
+    }                          \
+  } while (0)
+
+// ------------------------------------------------------------------ memory
+// All library-owned device memory goes through the process-wide allocator
+// hook (default cudaMalloc/cudaFree).
+void* dev_alloc(size_t bytes, cudaStream_t stream);
+void dev_free(void* p, cudaStream_t stream);
+
+// Owning device buffer; frees through the allocator hook.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), bytes(o.bytes), stream(o.stream) { o.ptr = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      reset();
+      ptr = o.ptr; bytes = o.bytes; stream = o.stream;
+      o.ptr = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { reset(); }
+  int alloc(size_t n_bytes, cudaStream_t s);   // DOBFS_OK or DOBFS_ERR_OOM
+  void reset();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// true if p is device (or managed) memory reachable by kernels as a device pointer
+bool is_device_ptr(const void* p);
+
+// ------------------------------------------------------------------ geometry
+int sm_count();
+constexpr int kWarp = 32;
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int bits_for(int64_t n) {  // smallest b with 2^b >= n (n >= 1)
+  int b = 0;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide sum of a 64-bit value, result valid in thread 0. `sh` needs
+// blockDim/32 slots.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) sh[w] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  __syncthreads();
+  return t;
+}
+
+}  // namespace dobfs

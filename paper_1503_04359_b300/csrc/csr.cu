@@ -1,0 +1,737 @@
+// Graph construction on the device.
+//
+// Every input (pairs, CSR arrays, or the R-MAT / Chung-Lu generators of
+// dobfs_inputs/gen.h) is turned into 64-bit edge keys row<<b | col (b bits
+// per vertex ID), with self-loops mapped to a sentinel that sorts last. One
+// LSD radix sort over 2b bits orders the keys by (row, col); a partitioned
+// compaction drops duplicates and writes the columns and row offsets. The
+// CSR stores each undirected edge as two directed entries (Sec. 4,
+// "Methodology").
+//
+// Degree-sorted reindexing (Sec. 3.4): vertices are renumbered by decreasing
+// degree (ties by increasing original ID) and every key is relabelled and
+// sorted again, so rows come in new-ID order and each row lists its
+// neighbours by increasing new ID, i.e. by decreasing degree — the highest-
+// degree neighbour first, which shortens bottom-up scans.
+#include <algorithm>
+#include <vector>
+
+#include "../../dobfs_inputs/gen.h"
+#include "common.cuh"
+#include "graph.cuh"
+#include "sort.cuh"
+
+namespace dobfs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t part_lo(int64_t n, int p, int P) {
+  return (int64_t)(((unsigned __int128)n * (unsigned)p) / (unsigned)P);
+}
+
+__device__ __forceinline__ uint64_t edge_key(uint32_t u, uint32_t v, int b) {
+  return u == v ? kSentinelKey : (((uint64_t)u << b) | (uint64_t)v);
+}
+
+__global__ void k_keys_pairs(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                             int64_t n, int b, uint64_t* __restrict__ keys, int* __restrict__ err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = src[i], v = dst[i];
+    if (u < 0 || v < 0 || u >= n || v >= n) {
+      atomicExch(err, 1);
+      keys[2 * i] = kSentinelKey;
+      keys[2 * i + 1] = kSentinelKey;
+      continue;
+    }
+    keys[2 * i] = edge_key((uint32_t)u, (uint32_t)v, b);
+    keys[2 * i + 1] = edge_key((uint32_t)v, (uint32_t)u, b);
+  }
+}
+
+__global__ void k_keys_rmat(int64_t m, int scale, uint32_t ta, uint32_t tab, uint32_t tabc, uint64_t kp,
+                            uint64_t kq, int b, uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t u, v;
+    gen_rmat_pair((uint64_t)i, scale, ta, tab, tabc, kp, kq, &u, &v);
+    keys[2 * i] = edge_key(u, v, b);
+    keys[2 * i + 1] = edge_key(v, u, b);
+  }
+}
+
+__global__ void k_keys_chunglu(const uint64_t* __restrict__ cdf, uint32_t n, int64_t m, uint64_t kp,
+                               uint64_t kq, int b, uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t u, v;
+    gen_chunglu_pair((uint64_t)i, cdf, n, kp, kq, &u, &v);
+    keys[2 * i] = edge_key(u, v, b);
+    keys[2 * i + 1] = edge_key(v, u, b);
+  }
+}
+
+// One warp per row; with `sym` the reverse entry goes to keys[nnz + j].
+template <class OffT>
+__global__ void k_keys_csr(const OffT* __restrict__ off, const int32_t* __restrict__ cols, int64_t n,
+                           int64_t nnz, int b, int sym, uint64_t* __restrict__ keys, int* __restrict__ err) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t s = (int64_t)off[u], e = (int64_t)off[u + 1];
+    if (s < 0 || e < s || e > nnz) {
+      if (lane_id() == 0) atomicExch(err, 2);
+      continue;
+    }
+    for (int64_t j = s + lane_id(); j < e; j += 32) {
+      const int32_t v = cols[j];
+      if (v < 0 || v >= n) {
+        atomicExch(err, 1);
+        keys[j] = kSentinelKey;
+        if (sym) keys[nnz + j] = kSentinelKey;
+        continue;
+      }
+      keys[j] = edge_key((uint32_t)u, (uint32_t)v, b);
+      if (sym) keys[nnz + j] = edge_key((uint32_t)v, (uint32_t)u, b);
+    }
+  }
+}
+
+__device__ __forceinline__ bool key_kept(const uint64_t* __restrict__ keys, int64_t i, uint64_t* k_out,
+                                         uint64_t* kprev_out) {
+  const uint64_t k = keys[i];
+  *k_out = k;
+  if (k == kSentinelKey) return false;
+  if (i == 0) return true;
+  const uint64_t kp = keys[i - 1];
+  *kprev_out = kp;
+  return k != kp;
+}
+
+// Kept (non-sentinel, non-duplicate) keys per partition.
+__global__ void __launch_bounds__(kThreads) k_count_kept(const uint64_t* __restrict__ keys, int64_t m, int P,
+                                                         unsigned long long* __restrict__ counts) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const int64_t lo = part_lo(m, blockIdx.x, P), hi = part_lo(m, blockIdx.x + 1, P);
+  unsigned long long c = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    uint64_t k, kp;
+    c += key_kept(keys, i, &k, &kp) ? 1 : 0;
+  }
+  c = block_sum_u64(c, sh);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of P counts in place; total into counts[P].
+__global__ void k_scan_small(unsigned long long* counts, int P) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long run = 0;
+  for (int i = 0; i < P; ++i) {
+    const unsigned long long c = counts[i];
+    counts[i] = run;
+    run += c;
+  }
+  counts[P] = run;
+}
+
+// Writes the kept keys' columns (if cols) and the row offsets up to the last
+// non-empty row. Each such offset is written exactly once: by the first kept
+// key of the row, which also fills the offsets of the empty rows before it.
+// k_fill_tail writes the offsets after the last non-empty row.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_extract(const uint64_t* __restrict__ keys, int64_t m, int b, int P,
+                                                      const unsigned long long* __restrict__ base,
+                                                      OffT* __restrict__ off, int32_t* __restrict__ cols,
+                                                      int64_t n) {
+  __shared__ unsigned warp_cnt[kThreads / 32];
+  __shared__ unsigned long long running;
+  const int64_t lo = part_lo(m, blockIdx.x, P), hi = part_lo(m, blockIdx.x + 1, P);
+  if (threadIdx.x == 0) running = base[blockIdx.x];
+  __syncthreads();
+  const uint64_t cmask = (1ull << b) - 1ull;
+  const int w = threadIdx.x >> 5;
+  for (int64_t t = lo; t < hi; t += blockDim.x) {
+    const int64_t i = t + threadIdx.x;
+    uint64_t k = 0, kp = 0;
+    const bool kept = (i < hi) && key_kept(keys, i, &k, &kp);
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    if (lane_id() == 0) warp_cnt[w] = (unsigned)__popc(bal);
+    __syncthreads();
+    unsigned wpre = 0, tot = 0;
+    for (int j = 0; j < kThreads / 32; ++j) {
+      wpre += (j < w) ? warp_cnt[j] : 0u;
+      tot += warp_cnt[j];
+    }
+    const unsigned long long pos = running + wpre + (unsigned)__popc(bal & lanemask_lt());
+    if (kept) {
+      if (cols) cols[pos] = (int32_t)(k & cmask);
+      const int64_t r = (int64_t)(k >> b);
+      const int64_t rp = (i == 0) ? -1 : (int64_t)(kp >> b);
+      for (int64_t rr = rp + 1; rr <= r; ++rr) off[rr] = (OffT)pos;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) running += tot;
+    __syncthreads();
+  }
+}
+
+// off[r] = total for every row after the last non-empty one. The last kept
+// key is the one before the first sentinel of the sorted array.
+template <class OffT>
+__global__ void k_fill_tail(const uint64_t* __restrict__ keys, int64_t m, int b, OffT* __restrict__ off, int64_t n,
+                            int64_t total) {
+  int64_t lo = 0, hi = m;  // first index holding the sentinel
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (keys[mid] == kSentinelKey) hi = mid; else lo = mid + 1;
+  }
+  if (lo == 0) return;  // no kept key: offsets stay 0
+  const int64_t r_last = (int64_t)(keys[lo - 1] >> b);
+  for (int64_t r = r_last + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    off[r] = (OffT)total;
+}
+
+// Symmetry check on sorted keys: every kept key's reverse must be present.
+__global__ void k_check_sym(const uint64_t* __restrict__ keys, int64_t m, int b, int* __restrict__ err) {
+  const uint64_t cmask = (1ull << b) - 1ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k, kp;
+    if (!key_kept(keys, i, &k, &kp)) continue;
+    const uint64_t want = ((k & cmask) << b) | (k >> b);
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (keys[mid] < want) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= m || keys[lo] != want) atomicExch(err, 3);
+  }
+}
+
+// Bitmap of degree-0 vertices (and of the padding bits >= n), the count of
+// vertices with an edge, and the maximum degree. One thread per vertex; a
+// warp covers one bitmap word.
+template <class OffT>
+__global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t words, uint32_t* __restrict__ iso,
+                            unsigned long long* __restrict__ stats) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  unsigned long long nonzero = 0, mx = 0;
+  const int64_t total = words * 32;
+  for (int64_t v0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; v0 < total;
+       v0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = v0 + lane_id();
+    bool isolated = true;
+    if (v < n) {
+      const int64_t d = (int64_t)off[v + 1] - (int64_t)off[v];
+      isolated = (d == 0);
+      nonzero += isolated ? 0 : 1;
+      mx = max(mx, (unsigned long long)d);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, isolated);
+    if (lane_id() == 0) iso[v0 >> 5] = bal;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if (lane_id() == 0) atomicMax(&stats[1], mx);
+  nonzero = block_sum_u64(nonzero, sh);
+  if (threadIdx.x == 0) atomicAdd(&stats[0], nonzero);
+}
+
+// Vertex keys for the degree-sorted order: (2^b-1 - degree) << b | id, so an
+// ascending sort gives decreasing degree, ties by increasing original ID.
+__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b, uint64_t* __restrict__ keys) {
+  const uint64_t dmax = (1ull << b) - 1ull;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t d = (uint64_t)(off[u + 1] - off[u]);
+    keys[u] = ((dmax - d) << b) | (uint64_t)u;
+  }
+}
+
+__global__ void k_maps(const uint64_t* __restrict__ sorted, int64_t n, int b, int32_t* __restrict__ new2orig,
+                       int32_t* __restrict__ orig2new) {
+  const uint64_t mask = (1ull << b) - 1ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = (int32_t)(sorted[i] & mask);
+    new2orig[i] = o;
+    orig2new[o] = (int32_t)i;
+  }
+}
+
+// Relabels the kept keys of a sorted array into `out`; dropped keys become
+// the sentinel.
+__global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t m, int b, const int32_t* __restrict__ o2n,
+                          uint64_t* __restrict__ out) {
+  const uint64_t mask = (1ull << b) - 1ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k, kp;
+    if (!key_kept(keys, i, &k, &kp)) {
+      out[i] = kSentinelKey;
+      continue;
+    }
+    const uint32_t u = (uint32_t)o2n[k >> b], v = (uint32_t)o2n[k & mask];
+    out[i] = ((uint64_t)u << b) | (uint64_t)v;
+  }
+}
+
+__global__ void k_widen(const int32_t* __restrict__ a, int64_t n, int64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i];
+}
+
+__global__ void k_iota(int32_t* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)i;
+}
+
+template <class OffT>
+__global__ void k_degrees(const OffT* __restrict__ off, const int32_t* __restrict__ o2n, int64_t n,
+                          int32_t* __restrict__ deg) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = o2n ? o2n[o] : o;
+    deg[o] = (int32_t)((int64_t)off[v + 1] - (int64_t)off[v]);
+  }
+}
+
+int grid_for(int64_t work, int threads = kThreads) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), (int64_t)sm_count() * 16));
+}
+
+// Counts kept keys per partition and scans: base[P] exclusive, base[P] = total.
+int kept_bases(const uint64_t* keys, int64_t m, int P, DevBuf& base, cudaStream_t s, int64_t* total) {
+  DOBFS_TRY(base.alloc(sizeof(unsigned long long) * (P + 1), s));
+  k_count_kept<<<P, kThreads, 0, s>>>(keys, m, P, base.as<unsigned long long>());
+  k_scan_small<<<1, 1, 0, s>>>(base.as<unsigned long long>(), P);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  unsigned long long t = 0;
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(&t, base.as<unsigned long long>() + P, sizeof(t), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  *total = (int64_t)t;
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int extract(const uint64_t* keys, int64_t m, int b, int64_t n, OffT* off, int32_t* cols, cudaStream_t s,
+            int64_t* nnz_out) {
+  const int P = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 4, ceil_div(m, 4096)));
+  DevBuf base;
+  int64_t total = 0;
+  DOBFS_TRY(kept_bases(keys, m, P, base, s, &total));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(OffT) * (size_t)(n + 1), s));
+  if (m > 0) {
+    k_extract<OffT><<<P, kThreads, 0, s>>>(keys, m, b, P, base.as<unsigned long long>(), off, cols, n);
+    k_fill_tail<OffT><<<grid_for(n + 1), kThreads, 0, s>>>(keys, m, b, off, n, total);
+  }
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  *nnz_out = total;
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int finish_stats(dobfs_graph* g, cudaStream_t s) {
+  g->words = ceil_div(g->n, 32);
+  DOBFS_TRY(g->isolated.alloc(sizeof(uint32_t) * (size_t)g->words, s));
+  DevBuf st;
+  DOBFS_TRY(st.alloc(sizeof(unsigned long long) * 2, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(st.ptr, 0, sizeof(unsigned long long) * 2, s));
+  k_deg_stats<OffT><<<grid_for(g->words * 32), kThreads, 0, s>>>(g->off.as<OffT>(), g->n, g->words,
+                                                                  g->isolated.as<uint32_t>(),
+                                                                  st.as<unsigned long long>());
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  unsigned long long h[2];
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(h, st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  g->n_nonisolated = (int64_t)h[0];
+  g->max_degree = (int64_t)h[1];
+  return DOBFS_OK;
+}
+
+}  // namespace
+
+int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t m, uint32_t flags, cudaStream_t s) {
+  const int b = g->bits;
+  const int nbits = 2 * b;
+  DevBuf tmp;
+  DOBFS_TRY(tmp.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
+  uint64_t* sorted = nullptr;
+  DOBFS_TRY(radix_sort_u64(keys.as<uint64_t>(), tmp.as<uint64_t>(), m, nbits, s, &sorted));
+  uint64_t* other = (sorted == keys.as<uint64_t>()) ? tmp.as<uint64_t>() : keys.as<uint64_t>();
+
+  if ((flags & DOBFS_GRAPH_VALIDATE) && !(flags & DOBFS_GRAPH_SYMMETRIZE) && m > 0) {
+    DevBuf err;
+    DOBFS_TRY(err.alloc(sizeof(int), s));
+    DOBFS_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+    k_check_sym<<<grid_for(m), kThreads, 0, s>>>(sorted, m, b, err.as<int>());
+    int h = 0;
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&h, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return set_error(DOBFS_ERR_BAD_GRAPH, "input graph is not symmetric (VALIDATE)");
+  }
+
+  const int64_t n = g->n;
+  if (flags & DOBFS_GRAPH_REINDEX) {
+    // degrees in original IDs
+    DevBuf off0;
+    DOBFS_TRY(off0.alloc(sizeof(int64_t) * (size_t)(n + 1), s));
+    int64_t nnz0 = 0;
+    DOBFS_TRY(extract<int64_t>(sorted, m, b, n, off0.as<int64_t>(), nullptr, s, &nnz0));
+    // degree-sorted order
+    DevBuf vk, vt;
+    DOBFS_TRY(vk.alloc(sizeof(uint64_t) * (size_t)n, s));
+    DOBFS_TRY(vt.alloc(sizeof(uint64_t) * (size_t)n, s));
+    k_vertex_keys<<<grid_for(n), kThreads, 0, s>>>(off0.as<int64_t>(), n, b, vk.as<uint64_t>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    uint64_t* vsorted = nullptr;
+    DOBFS_TRY(radix_sort_u64(vk.as<uint64_t>(), vt.as<uint64_t>(), n, 2 * b, s, &vsorted));
+    DOBFS_TRY(g->new2orig.alloc(sizeof(int32_t) * (size_t)n, s));
+    DOBFS_TRY(g->orig2new.alloc(sizeof(int32_t) * (size_t)n, s));
+    k_maps<<<grid_for(n), kThreads, 0, s>>>(vsorted, n, b, g->new2orig.as<int32_t>(), g->orig2new.as<int32_t>());
+    k_relabel<<<grid_for(m), kThreads, 0, s>>>(sorted, m, b, g->orig2new.as<int32_t>(), other);
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    vk.reset();
+    vt.reset();
+    off0.reset();
+    uint64_t* a = other;
+    uint64_t* bb = sorted;
+    DOBFS_TRY(radix_sort_u64(a, bb, m, nbits, s, &sorted));
+    g->reindexed = true;
+  }
+
+  // final CSR
+  int64_t nnz = 0;
+  {
+    DevBuf base;
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 4, ceil_div(m, 4096)));
+    DOBFS_TRY(kept_bases(sorted, m, P, base, s, &nnz));
+  }
+  g->nnz = nnz;
+  g->off64 = (flags & DOBFS_GRAPH_OFFSETS64) || nnz > (int64_t)INT32_MAX;
+  // the other key buffer is free now: release it before allocating the columns
+  if (sorted == keys.as<uint64_t>()) tmp.reset(); else { keys.reset(); }
+  DOBFS_TRY(g->cols.alloc(sizeof(int32_t) * (size_t)(nnz + 4), s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->cols.as<int32_t>() + nnz, 0, sizeof(int32_t) * 4, s));
+  DOBFS_TRY(g->off.alloc((g->off64 ? 8 : 4) * (size_t)(n + 1), s));
+  int64_t nnz2 = 0;
+  if (g->off64) {
+    DOBFS_TRY(extract<int64_t>(sorted, m, b, n, g->off.as<int64_t>(), g->cols.as<int32_t>(), s, &nnz2));
+    DOBFS_TRY(finish_stats<int64_t>(g, s));
+  } else {
+    DOBFS_TRY(extract<int32_t>(sorted, m, b, n, g->off.as<int32_t>(), g->cols.as<int32_t>(), s, &nnz2));
+    DOBFS_TRY(finish_stats<int32_t>(g, s));
+  }
+  if (nnz2 != nnz) return set_error(DOBFS_ERR_CUDA, "internal: entry count changed between passes");
+  return DOBFS_OK;
+}
+
+namespace {
+
+int new_graph(int64_t n, cudaStream_t s, dobfs_graph** out) {
+  if (!out) return set_error(DOBFS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > (int64_t)INT32_MAX)
+    return set_error(DOBFS_ERR_INVALID, "n_vertices must be in [1, 2^31-1], got %lld", (long long)n);
+  dobfs_graph* g = new (std::nothrow) dobfs_graph();
+  if (!g) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  g->n = n;
+  g->bits = std::max(1, bits_for(n));
+  g->stream = s;
+  *out = g;
+  return DOBFS_OK;
+}
+
+// Finishes a build: workspace, timing; on failure frees the graph.
+int finish(dobfs_graph* g, int rc, cudaEvent_t e0, cudaEvent_t e1, dobfs_graph** out) {
+  if (rc == DOBFS_OK) rc = graph_alloc_workspace(g);
+  if (rc == DOBFS_OK && e0 && e1) {
+    cudaEventRecord(e1, g->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&g->build_ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != DOBFS_OK) {
+    graph_release(g);
+    delete g;
+    *out = nullptr;
+    return rc;
+  }
+  *out = g;
+  return DOBFS_OK;
+}
+
+int start_timer(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  DOBFS_CUDA_TRY(cudaEventCreate(e0));
+  DOBFS_CUDA_TRY(cudaEventCreate(e1));
+  DOBFS_CUDA_TRY(cudaEventRecord(*e0, s));
+  return DOBFS_OK;
+}
+
+int read_err_flag(DevBuf& err, cudaStream_t s, int* h) {
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(h, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  return DOBFS_OK;
+}
+
+// Device copy of a caller array (host or device); `dev` stays empty when the
+// caller's pointer is already device memory.
+int to_device(const void* p, size_t bytes, bool device_ptrs, DevBuf& dev, cudaStream_t s, const void** out) {
+  if (bytes == 0) {
+    *out = p;
+    return DOBFS_OK;
+  }
+  if (device_ptrs || is_device_ptr(p)) {
+    *out = p;
+    return DOBFS_OK;
+  }
+  DOBFS_TRY(dev.alloc(bytes, s));
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(dev.ptr, p, bytes, cudaMemcpyHostToDevice, s));
+  *out = dev.ptr;
+  return DOBFS_OK;
+}
+
+}  // namespace
+
+}  // namespace dobfs
+
+using namespace dobfs;
+
+extern "C" {
+
+int dobfs_graph_create_from_pairs(const int32_t* src, const int32_t* dst, int64_t n_pairs, int64_t n_vertices,
+                                  uint32_t flags, void* stream, dobfs_graph** out) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs < 0 || (n_pairs > 0 && (!src || !dst)))
+    return set_error(DOBFS_ERR_INVALID, "bad pair arrays");
+  dobfs_graph* g = nullptr;
+  DOBFS_TRY(new_graph(n_vertices, s, &g));
+  cudaEvent_t e0, e1;
+  int rc = start_timer(s, &e0, &e1);
+  if (rc == DOBFS_OK) {
+    rc = [&]() -> int {
+      DevBuf ds, dd, keys, err;
+      const void *ps = nullptr, *pd = nullptr;
+      const bool dp = (flags & DOBFS_GRAPH_DEVICE_PTRS) != 0;
+      DOBFS_TRY(to_device(src, sizeof(int32_t) * (size_t)n_pairs, dp, ds, s, &ps));
+      DOBFS_TRY(to_device(dst, sizeof(int32_t) * (size_t)n_pairs, dp, dd, s, &pd));
+      const int64_t m = 2 * n_pairs;
+      DOBFS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
+      DOBFS_TRY(err.alloc(sizeof(int), s));
+      DOBFS_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+      if (n_pairs > 0)
+        k_keys_pairs<<<grid_for(n_pairs), kThreads, 0, s>>>((const int32_t*)ps, (const int32_t*)pd, n_pairs,
+                                                            n_vertices, g->bits, keys.as<uint64_t>(), err.as<int>());
+      DOBFS_CUDA_TRY(cudaGetLastError());
+      int h = 0;
+      DOBFS_TRY(read_err_flag(err, s, &h));
+      if (h) return set_error(DOBFS_ERR_BAD_GRAPH, "pair endpoint out of range [0, %lld)", (long long)n_vertices);
+      ds.reset();
+      dd.reset();
+      return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
+    }();
+  }
+  return finish(g, rc, e0, e1, out);
+}
+
+int dobfs_graph_create(const void* row_offsets, int offsets_are_int64, const int32_t* col_indices,
+                       int64_t n_vertices, int64_t n_entries, uint32_t flags, void* stream, dobfs_graph** out) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!row_offsets || n_entries < 0 || (n_entries > 0 && !col_indices))
+    return set_error(DOBFS_ERR_INVALID, "bad CSR arrays");
+  dobfs_graph* g = nullptr;
+  DOBFS_TRY(new_graph(n_vertices, s, &g));
+  cudaEvent_t e0, e1;
+  int rc = start_timer(s, &e0, &e1);
+  if (rc == DOBFS_OK) {
+    rc = [&]() -> int {
+      const bool dp = (flags & DOBFS_GRAPH_DEVICE_PTRS) != 0;
+      const size_t ob = (offsets_are_int64 ? 8 : 4) * (size_t)(n_vertices + 1);
+      DevBuf doff, dcol, keys, err;
+      const void *po = nullptr, *pc = nullptr;
+      DOBFS_TRY(to_device(row_offsets, ob, dp, doff, s, &po));
+      DOBFS_TRY(to_device(col_indices, sizeof(int32_t) * (size_t)n_entries, dp, dcol, s, &pc));
+      // first and last offsets must be 0 and n_entries
+      int64_t ends[2] = {0, 0};
+      if (offsets_are_int64) {
+        DOBFS_CUDA_TRY(cudaMemcpyAsync(&ends[0], po, 8, cudaMemcpyDeviceToHost, s));
+        DOBFS_CUDA_TRY(cudaMemcpyAsync(&ends[1], (const int64_t*)po + n_vertices, 8, cudaMemcpyDeviceToHost, s));
+      } else {
+        int32_t e2[2] = {0, 0};
+        DOBFS_CUDA_TRY(cudaMemcpyAsync(&e2[0], po, 4, cudaMemcpyDeviceToHost, s));
+        DOBFS_CUDA_TRY(cudaMemcpyAsync(&e2[1], (const int32_t*)po + n_vertices, 4, cudaMemcpyDeviceToHost, s));
+        DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+        ends[0] = e2[0];
+        ends[1] = e2[1];
+      }
+      DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+      if (ends[0] != 0 || ends[1] != n_entries)
+        return set_error(DOBFS_ERR_BAD_GRAPH, "row offsets must start at 0 and end at n_entries");
+      const int sym = (flags & DOBFS_GRAPH_SYMMETRIZE) ? 1 : 0;
+      const int64_t m = n_entries * (sym ? 2 : 1);
+      DOBFS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
+      DOBFS_TRY(err.alloc(sizeof(int), s));
+      DOBFS_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+      const int grid = grid_for(n_vertices * 32);
+      if (offsets_are_int64)
+        k_keys_csr<int64_t><<<grid, kThreads, 0, s>>>((const int64_t*)po, (const int32_t*)pc, n_vertices, n_entries,
+                                                      g->bits, sym, keys.as<uint64_t>(), err.as<int>());
+      else
+        k_keys_csr<int32_t><<<grid, kThreads, 0, s>>>((const int32_t*)po, (const int32_t*)pc, n_vertices, n_entries,
+                                                      g->bits, sym, keys.as<uint64_t>(), err.as<int>());
+      DOBFS_CUDA_TRY(cudaGetLastError());
+      int h = 0;
+      DOBFS_TRY(read_err_flag(err, s, &h));
+      if (h == 1) return set_error(DOBFS_ERR_BAD_GRAPH, "column index out of range [0, %lld)", (long long)n_vertices);
+      if (h) return set_error(DOBFS_ERR_BAD_GRAPH, "row offsets are not non-decreasing within [0, n_entries]");
+      doff.reset();
+      dcol.reset();
+      return build_from_keys(g, keys, m, flags, s);
+    }();
+  }
+  return finish(g, rc, e0, e1, out);
+}
+
+int dobfs_graph_create_rmat(int scale, int64_t n_pairs, uint32_t t_a, uint32_t t_ab, uint32_t t_abc, uint64_t seed,
+                            uint32_t flags, void* stream, dobfs_graph** out) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (scale < 1 || scale > 31 || n_pairs < 0 || !(t_a <= t_ab && t_ab <= t_abc))
+    return set_error(DOBFS_ERR_INVALID, "bad R-MAT parameters");
+  dobfs_graph* g = nullptr;
+  DOBFS_TRY(new_graph(int64_t(1) << scale, s, &g));
+  cudaEvent_t e0, e1;
+  int rc = start_timer(s, &e0, &e1);
+  if (rc == DOBFS_OK) {
+    rc = [&]() -> int {
+      DevBuf keys;
+      const int64_t m = 2 * n_pairs;
+      DOBFS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
+      if (n_pairs > 0)
+        k_keys_rmat<<<grid_for(n_pairs), kThreads, 0, s>>>(n_pairs, scale, t_a, t_ab, t_abc, gen_key_pairs(seed),
+                                                           gen_key_perm(seed), g->bits, keys.as<uint64_t>());
+      DOBFS_CUDA_TRY(cudaGetLastError());
+      return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
+    }();
+  }
+  return finish(g, rc, e0, e1, out);
+}
+
+int dobfs_graph_create_chunglu(const uint64_t* cdf, int64_t n_vertices, int64_t n_pairs, uint64_t seed,
+                               uint32_t flags, void* stream, dobfs_graph** out) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!cdf || n_pairs < 0) return set_error(DOBFS_ERR_INVALID, "bad Chung-Lu parameters");
+  dobfs_graph* g = nullptr;
+  DOBFS_TRY(new_graph(n_vertices, s, &g));
+  cudaEvent_t e0, e1;
+  int rc = start_timer(s, &e0, &e1);
+  if (rc == DOBFS_OK) {
+    rc = [&]() -> int {
+      if (cdf[n_vertices - 1] == 0) return set_error(DOBFS_ERR_INVALID, "weight table sums to zero");
+      DevBuf dcdf, keys;
+      DOBFS_TRY(dcdf.alloc(sizeof(uint64_t) * (size_t)n_vertices, s));
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(dcdf.ptr, cdf, sizeof(uint64_t) * (size_t)n_vertices, cudaMemcpyHostToDevice, s));
+      const int64_t m = 2 * n_pairs;
+      DOBFS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
+      if (n_pairs > 0)
+        k_keys_chunglu<<<grid_for(n_pairs), kThreads, 0, s>>>(dcdf.as<uint64_t>(), (uint32_t)n_vertices, n_pairs,
+                                                              gen_key_pairs(seed), gen_key_perm(seed), g->bits,
+                                                              keys.as<uint64_t>());
+      DOBFS_CUDA_TRY(cudaGetLastError());
+      DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+      dcdf.reset();
+      return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
+    }();
+  }
+  return finish(g, rc, e0, e1, out);
+}
+
+int dobfs_graph_export(const dobfs_graph* gc, int64_t* offsets_out, int32_t* cols_out, int32_t* new2orig_out,
+                       void* stream) {
+  clear_error();
+  if (!gc) return set_error(DOBFS_ERR_INVALID, "graph is NULL");
+  dobfs_graph* g = const_cast<dobfs_graph*>(gc);
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  if (g->last_stream) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+  DevBuf tmp;
+  if (offsets_out) {
+    const size_t ob = sizeof(int64_t) * (size_t)(g->n + 1);
+    int64_t* dst = offsets_out;
+    const bool dev = is_device_ptr(offsets_out);
+    if (!dev) {
+      DOBFS_TRY(tmp.alloc(ob, s));
+      dst = tmp.as<int64_t>();
+    }
+    if (g->off64)
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(dst, g->off.ptr, ob, cudaMemcpyDeviceToDevice, s));
+    else
+      k_widen<<<grid_for(g->n + 1), kThreads, 0, s>>>(g->off.as<int32_t>(), g->n + 1, dst);
+    if (!dev) DOBFS_CUDA_TRY(cudaMemcpyAsync(offsets_out, dst, ob, cudaMemcpyDeviceToHost, s));
+  }
+  if (cols_out && g->nnz > 0)
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(cols_out, g->cols.ptr, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
+  if (new2orig_out) {
+    if (g->reindexed) {
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(new2orig_out, g->new2orig.ptr, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDefault, s));
+    } else {
+      DevBuf id;
+      int32_t* dst = new2orig_out;
+      const bool dev = is_device_ptr(new2orig_out);
+      if (!dev) {
+        DOBFS_TRY(id.alloc(sizeof(int32_t) * (size_t)g->n, s));
+        dst = id.as<int32_t>();
+      }
+      k_iota<<<grid_for(g->n), kThreads, 0, s>>>(dst, g->n);
+      if (!dev) DOBFS_CUDA_TRY(cudaMemcpyAsync(new2orig_out, dst, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+      DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  return DOBFS_OK;
+}
+
+int dobfs_graph_degrees(const dobfs_graph* gc, int32_t* deg_out, void* stream) {
+  clear_error();
+  if (!gc || !deg_out) return set_error(DOBFS_ERR_INVALID, "NULL argument");
+  dobfs_graph* g = const_cast<dobfs_graph*>(gc);
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  if (g->last_stream) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+  DevBuf tmp;
+  int32_t* dst = deg_out;
+  const bool dev = is_device_ptr(deg_out);
+  if (!dev) {
+    DOBFS_TRY(tmp.alloc(sizeof(int32_t) * (size_t)g->n, s));
+    dst = tmp.as<int32_t>();
+  }
+  const int32_t* o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
+  if (g->off64)
+    k_degrees<int64_t><<<grid_for(g->n), kThreads, 0, s>>>(g->off.as<int64_t>(), o2n, g->n, dst);
+  else
+    k_degrees<int32_t><<<grid_for(g->n), kThreads, 0, s>>>(g->off.as<int32_t>(), o2n, g->n, dst);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  if (!dev) DOBFS_CUDA_TRY(cudaMemcpyAsync(deg_out, dst, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  return DOBFS_OK;
+}
+
+int dobfs_graph_get_info(const dobfs_graph* g, dobfs_graph_info* info) {
+  if (!g || !info) return set_error(DOBFS_ERR_INVALID, "NULL argument");
+  info->n_vertices = g->n;
+  info->n_entries = g->nnz;
+  info->n_nonisolated = g->n_nonisolated;
+  info->max_degree = g->max_degree;
+  info->offsets_int64 = g->off64 ? 1 : 0;
+  info->reindexed = g->reindexed ? 1 : 0;
+  int64_t bytes = 0;
+  const DevBuf* bufs[] = {&g->off, &g->cols, &g->new2orig, &g->orig2new, &g->isolated, &g->visited, &g->fbm0,
+                          &g->fbm1, &g->lp, &g->q0, &g->q1, &g->rec, &g->deferred, &g->ctl, &g->trace,
+                          &g->out_stage};
+  for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
+  info->device_bytes = bytes;
+  info->build_ms = g->build_ms;
+  return DOBFS_OK;
+}
+
+}  // extern "C"

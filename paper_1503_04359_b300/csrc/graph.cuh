@@ -1,0 +1,104 @@
+// The graph object behind the dobfs_graph handle: the stored CSR (device),
+// the renumbering maps, and the per-graph BFS workspace.
+#pragma once
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dobfs {
+
+// Sentinel edge key: a dropped entry (self-loop or duplicate). Sorts last.
+constexpr uint64_t kSentinelKey = ~0ull;
+
+// Device-side control block of one BFS run (one per graph). The level loop
+// reads and updates it on the device; the host reads it only after a run.
+struct BfsCtl {
+  int32_t level;        // L: the frontier holds the vertices at level L
+  int32_t dir;          // direction of the step expanding level L: 0 top-down, 1 bottom-up
+  int32_t fmt;          // frontier of level L is held as 0: queue, 1: bitmap
+  int32_t step_case;    // 0 TD from queue, 1 BU from bitmap, 2 TD after bitmap->queue, 3 BU after queue->bitmap
+  int32_t fresh;        // set by init: the loop has not run a step yet
+  int32_t done;
+  int32_t bu_run;       // consecutive bottom-up levels so far (static policy)
+  int32_t n_levels;
+  int64_t n_f, m_f;     // size and degree sum of the level-L frontier
+  int64_t n_f_prev;
+  int64_t m_u;          // degree sum of vertices not yet visited
+  // accumulators of the running step, reset by the heuristic kernel
+  unsigned long long nx_n, nx_m, nx_examined, nx_scanned;
+  unsigned int q_tail;  // next-queue tail (top-down) / bitmap->queue tail
+  unsigned int n_rec;   // top-down chunk records
+  unsigned int n_def;   // bottom-up deferred (long) rows
+  unsigned int conv_tail;  // bitmap->queue conversion tail
+  // run totals
+  int64_t reached, teps2, examined, alg_bytes;
+  int32_t n_td, n_bu;
+  int32_t overflow;     // top-down record buffer overflow (never expected)
+  int32_t pad2;
+  // parameters
+  int32_t mode, alpha, beta, static_pct, bu_steps, pad1;
+  uint64_t sched_seed;
+};
+
+// Per-level trace record on the device (mirrors dobfs_level_trace).
+struct LevelRec {
+  int32_t level, dir;
+  int64_t n_f, m_f, m_u, n_next, examined, scanned, bytes;
+};
+constexpr int kMaxTrace = 4096;
+
+}  // namespace dobfs
+
+struct dobfs_graph {
+  int64_t n = 0;            // vertices
+  int64_t nnz = 0;          // stored directed entries
+  int64_t n_nonisolated = 0;
+  int64_t max_degree = 0;
+  int bits = 0;             // bits per vertex ID in edge keys
+  bool off64 = false;
+  bool reindexed = false;
+  float build_ms = 0.f;
+  cudaStream_t stream = nullptr;
+
+  // stored CSR (internal IDs). cols carries 4 padding entries so 16-byte
+  // vector loads of a row's last aligned chunk stay inside the allocation.
+  dobfs::DevBuf off, cols;
+  dobfs::DevBuf new2orig, orig2new;  // int32[n] each, only when reindexed
+  dobfs::DevBuf isolated;            // bitmap: degree-0 vertices and bits >= n
+  int64_t words = 0;                 // bitmap words = ceil(n/32)
+
+  // BFS workspace
+  dobfs::DevBuf visited, fbm0, fbm1;  // bitmaps
+  dobfs::DevBuf lp;                   // int2[n]: (level, parent) in internal IDs
+  dobfs::DevBuf q0, q1;               // int32[n] queues
+  dobfs::DevBuf rec;                  // int2[] top-down chunk records
+  int64_t rec_cap = 0;
+  dobfs::DevBuf deferred;             // int32[n]
+  dobfs::DevBuf ctl;                  // BfsCtl
+  dobfs::DevBuf trace;                // LevelRec[kMaxTrace]
+  dobfs::DevBuf out_stage;            // int32[2n] staging for host outputs (lazy)
+  bool ws_ready = false;
+
+  // level loop as a CUDA graph with a device-driven while node
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool last_host_loop = false;
+  std::vector<float> host_level_ms, host_level_main_ms;
+
+  std::mutex mu;
+};
+
+namespace dobfs {
+
+int graph_alloc_workspace(dobfs_graph* g);
+void graph_release(dobfs_graph* g);
+
+// builds g's CSR from n_keys edge keys (row<<bits | col, or kSentinelKey),
+// consuming `keys` (n_keys entries, may be reordered/overwritten)
+int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t n_keys, uint32_t flags, cudaStream_t s);
+
+}  // namespace dobfs

@@ -1,0 +1,329 @@
+"""Python binding of libdobfs (argument marshalling only).
+
+Every function named ``dobfs_*`` here forwards to the C entry point of the
+same name in ``_lib/libdobfs.so`` (declared in ``include/dobfs.h``): it turns
+torch tensors / numpy arrays into pointers and sizes, raises ``DobfsError`` on
+a non-zero status, and does nothing else. Every step of the BFS runs in the
+library's CUDA kernels; there is no CPU path. If the library is missing,
+importing this module raises.
+
+PyTorch provides device memory and streams: ``use_torch_allocator()`` routes
+the library's device allocations through PyTorch's caching allocator, and
+``stream=None`` means PyTorch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdobfs.so")
+
+DOBFS_OK, DOBFS_PENDING = 0, 1
+DOBFS_ERR_INVALID, DOBFS_ERR_OOM, DOBFS_ERR_CUDA = -1, -2, -3
+DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY = -4, -5, -6
+
+DOBFS_GRAPH_SYMMETRIZE = 0x1
+DOBFS_GRAPH_REINDEX = 0x2
+DOBFS_GRAPH_DEVICE_PTRS = 0x4
+DOBFS_GRAPH_VALIDATE = 0x8
+DOBFS_GRAPH_OFFSETS64 = 0x10
+
+DOBFS_DIR_AUTO, DOBFS_DIR_TOPDOWN, DOBFS_DIR_BOTTOMUP, DOBFS_DIR_RANDOM, DOBFS_DIR_STATIC = 0, 1, 2, 3, 4
+DOBFS_RUN_CANONICAL_PARENT = 0x1
+DOBFS_RUN_HOST_LOOP = 0x2
+DOBFS_RUN_SYNC_STATS = 0x4
+
+
+class DobfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("dobfs status %d: %s" % (status, msg))
+        self.status = status
+
+
+class dobfs_graph_info(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_entries", ctypes.c_int64), ("n_nonisolated", ctypes.c_int64),
+                ("max_degree", ctypes.c_int64), ("offsets_int64", ctypes.c_int32), ("reindexed", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_float)]
+
+
+class dobfs_run_opts(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("static_pct", ctypes.c_int32), ("bu_steps", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("schedule_seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class dobfs_run_stats(ctypes.Structure):
+    _fields_ = [("device_ms", ctypes.c_float), ("levels", ctypes.c_int32), ("td_levels", ctypes.c_int32),
+                ("bu_levels", ctypes.c_int32), ("reached", ctypes.c_int64), ("teps_edges", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("alg_bytes", ctypes.c_int64)]
+
+
+class dobfs_level_trace(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("direction", ctypes.c_int32), ("n_frontier", ctypes.c_int64),
+                ("m_frontier", ctypes.c_int64), ("m_unvisited", ctypes.c_int64), ("n_next", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("vertices_scanned", ctypes.c_int64),
+                ("alg_bytes", ctypes.c_int64), ("ms", ctypes.c_float), ("ms_main", ctypes.c_float)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libdobfs.so; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdobfs.so not built (%s); run python -m paper_1503_04359_b300.build" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    c_int, i64, i32, u32, u64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    G = ctypes.c_void_p
+    sig = {
+        "dobfs_set_allocator": (c_int, [ALLOC_FN, FREE_FN, vp]),
+        "dobfs_last_error": (ctypes.c_char_p, []),
+        "dobfs_graph_create": (c_int, [vp, c_int, vp, i64, i64, u32, vp, ctypes.POINTER(G)]),
+        "dobfs_graph_create_from_pairs": (c_int, [vp, vp, i64, i64, u32, vp, ctypes.POINTER(G)]),
+        "dobfs_graph_create_rmat": (c_int, [c_int, i64, u32, u32, u32, u64, u32, vp, ctypes.POINTER(G)]),
+        "dobfs_graph_create_chunglu": (c_int, [vp, i64, i64, u64, u32, vp, ctypes.POINTER(G)]),
+        "dobfs_graph_destroy": (c_int, [G]),
+        "dobfs_graph_get_info": (c_int, [G, ctypes.POINTER(dobfs_graph_info)]),
+        "dobfs_graph_export": (c_int, [G, vp, vp, vp, vp]),
+        "dobfs_graph_degrees": (c_int, [G, vp, vp]),
+        "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
+        "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
+        "dobfs_last_trace": (c_int, [G, ctypes.POINTER(dobfs_level_trace), i32, ctypes.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().dobfs_last_error().decode(errors="replace")
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise DobfsError(status, last_error())
+    return status
+
+
+def _ptr(x) -> int | None:
+    """Data pointer of a torch tensor or numpy array (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------- allocator
+_alloc_keepalive = None
+
+
+def use_torch_allocator(device: int | None = None) -> None:
+    """Routes every device allocation of the library through PyTorch's caching allocator."""
+    global _alloc_keepalive
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+
+    @ALLOC_FN
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:  # OOM -> NULL -> DOBFS_ERR_OOM
+            return None
+
+    @FREE_FN
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _check(load().dobfs_set_allocator(_alloc, _free, None))
+    _alloc_keepalive = (_alloc, _free)
+
+
+def use_default_allocator() -> None:
+    global _alloc_keepalive
+    _check(load().dobfs_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _alloc_keepalive = None
+
+
+# ---------------------------------------------------------------- C entry points (same names)
+def dobfs_graph_create(row_offsets, col_indices, n_vertices: int, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    off64 = 1 if str(getattr(row_offsets, "dtype", "")).endswith("int64") else 0
+    n_entries = int(col_indices.shape[0]) if col_indices is not None else 0
+    _check(load().dobfs_graph_create(_ptr(row_offsets), off64, _ptr(col_indices), n_vertices, n_entries, flags,
+                                     _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def dobfs_graph_create_from_pairs(src, dst, n_vertices: int, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dobfs_graph_create_from_pairs(_ptr(src), _ptr(dst), int(src.shape[0]), n_vertices, flags,
+                                                _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def dobfs_graph_create_rmat(scale: int, n_pairs: int, t_a: int, t_ab: int, t_abc: int, seed: int, flags: int = 0,
+                            stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dobfs_graph_create_rmat(scale, n_pairs, t_a, t_ab, t_abc, seed, flags, _stream(stream),
+                                          ctypes.byref(h)))
+    return h.value
+
+
+def dobfs_graph_create_chunglu(cdf: np.ndarray, n_pairs: int, seed: int, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    cdf = np.ascontiguousarray(cdf, dtype=np.uint64)
+    _check(load().dobfs_graph_create_chunglu(cdf.ctypes.data, len(cdf), n_pairs, seed, flags, _stream(stream),
+                                             ctypes.byref(h)))
+    return h.value
+
+
+def dobfs_graph_destroy(g: int) -> None:
+    _check(load().dobfs_graph_destroy(g))
+
+
+def dobfs_graph_get_info(g: int) -> dobfs_graph_info:
+    info = dobfs_graph_info()
+    _check(load().dobfs_graph_get_info(g, ctypes.byref(info)))
+    return info
+
+
+def dobfs_graph_export(g: int, offsets_out=None, cols_out=None, new2orig_out=None, stream=None) -> None:
+    _check(load().dobfs_graph_export(g, _ptr(offsets_out), _ptr(cols_out), _ptr(new2orig_out), _stream(stream)))
+
+
+def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
+    _check(load().dobfs_graph_degrees(g, _ptr(deg_out), _stream(stream)))
+
+
+def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: int | None = None,
+              static_pct: int | None = None, bu_steps: int | None = None, flags: int = 0, schedule_seed: int = 0,
+              stream=None) -> dobfs_run_opts:
+    o = dobfs_run_opts()
+    _check(load().dobfs_run_opts_init(ctypes.byref(o)))
+    o.direction = direction
+    if alpha is not None:
+        o.alpha = alpha
+    if beta is not None:
+        o.beta = beta
+    if static_pct is not None:
+        o.static_pct = static_pct
+    if bu_steps is not None:
+        o.bu_steps = bu_steps
+    o.flags = flags
+    o.schedule_seed = schedule_seed
+    o.stream = _stream(stream)
+    return o
+
+
+def dobfs_run(g: int, root: int, level_out, parent_out=None, opts: dobfs_run_opts | None = None,
+              want_stats: bool = False) -> dobfs_run_stats | None:
+    if opts is None:
+        opts = make_opts()
+    st = dobfs_run_stats() if want_stats else None
+    _check(load().dobfs_run(g, int(root), _ptr(level_out), _ptr(parent_out), ctypes.byref(opts),
+                            ctypes.byref(st) if st is not None else None))
+    return st
+
+
+def dobfs_last_trace(g: int, max_levels: int = 4096) -> list[dobfs_level_trace]:
+    buf = (dobfs_level_trace * max_levels)()
+    n = ctypes.c_int32(0)
+    _check(load().dobfs_last_trace(g, buf, max_levels, ctypes.byref(n)))
+    return [buf[i] for i in range(n.value)]
+
+
+# ---------------------------------------------------------------- convenience wrapper
+@dataclass
+class Graph:
+    """Owning handle of a device graph."""
+
+    handle: int
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            try:
+                dobfs_graph_destroy(self.handle)
+            finally:
+                self.handle = 0
+
+    @property
+    def info(self) -> dobfs_graph_info:
+        return dobfs_graph_get_info(self.handle)
+
+    @property
+    def n(self) -> int:
+        return int(self.info.n_vertices)
+
+    def export(self):
+        """(offsets int64[n+1], cols int32[nnz], new2orig int32[n]) as numpy arrays."""
+        info = self.info
+        off = np.empty(info.n_vertices + 1, dtype=np.int64)
+        cols = np.empty(max(info.n_entries, 1), dtype=np.int32)
+        n2o = np.empty(info.n_vertices, dtype=np.int32)
+        dobfs_graph_export(self.handle, off, cols, n2o)
+        return off, cols[:info.n_entries], n2o
+
+    def degrees(self, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        dobfs_graph_degrees(self.handle, out)
+        return out
+
+    def run(self, root: int, level_out, parent_out=None, opts=None, want_stats: bool = False):
+        return dobfs_run(self.handle, root, level_out, parent_out, opts, want_stats)
+
+    def trace(self):
+        return dobfs_last_trace(self.handle)
+
+
+def rmat_graph(spec, flags: int = DOBFS_GRAPH_REINDEX, stream=None) -> Graph:
+    """Device graph of a dobfs_inputs.RmatSpec workload."""
+    ta, tab, tabc = spec.thresholds
+    return Graph(dobfs_graph_create_rmat(spec.scale, spec.n_pairs, ta, tab, tabc, spec.seed, flags, stream))
+
+
+def chunglu_graph(spec, cdf: np.ndarray, flags: int = DOBFS_GRAPH_REINDEX, stream=None) -> Graph:
+    return Graph(dobfs_graph_create_chunglu(cdf, spec.n_pairs, spec.seed, flags, stream))
+
+
+def pairs_graph(n_vertices: int, src, dst, flags: int = 0, stream=None) -> Graph:
+    return Graph(dobfs_graph_create_from_pairs(src, dst, n_vertices, flags, stream))
+
+
+def csr_graph(row_offsets, col_indices, n_vertices: int, flags: int = 0, stream=None) -> Graph:
+    return Graph(dobfs_graph_create(row_offsets, col_indices, n_vertices, flags, stream))

@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every declared entry point (no GPU needed).
+
+Only argument checks that return before any CUDA call are exercised here.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1503_04359_b300 import build as build_mod
+from paper_1503_04359_b300 import dobfs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|const char\*|void|int32_t|int64_t)\s+(dobfs_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return dobfs.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+        assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
+
+
+def test_python_binding_has_same_names():
+    for n in _declared():
+        if n in ("dobfs_set_allocator", "dobfs_last_error", "dobfs_run_opts_init"):
+            continue
+        assert hasattr(dobfs, n), n
+
+
+def test_argument_errors_without_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.dobfs_graph_create_rmat(0, 10, 0, 0, 0, 1, 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_INVALID
+    assert "R-MAT" in dobfs.last_error()
+    assert lib.dobfs_graph_create_rmat(10, 10, 5, 3, 9, 1, 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_create_from_pairs(None, None, -1, 10, 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_run(None, 0, None, None, None, None) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_get_info(None, None) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_destroy(None) == dobfs.DOBFS_OK
+    o = dobfs.dobfs_run_opts()
+    assert lib.dobfs_run_opts_init(ctypes.byref(o)) == 0
+    assert (o.direction, o.alpha, o.beta) == (dobfs.DOBFS_DIR_AUTO, 14, 24)
+    # allocator hook: both or neither
+    assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(lambda n, s, c: None), dobfs.FREE_FN(), None) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(), dobfs.FREE_FN(), None) == dobfs.DOBFS_OK
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(dobfs, "_lib", None)
+    monkeypatch.setattr(dobfs, "LIB_PATH", "/nonexistent/libdobfs.so")
+    with pytest.raises(ImportError):
+        dobfs.load()

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Levels must match the oracle bit-exact in every direction policy (levels are
+unique, so any top-down / bottom-up schedule of Algorithm 1 reaches the same
+array); default parents must satisfy the BFS invariants; canonical parents
+must match bit-exact.
+"""
+import numpy as np
+import pytest
+
+import dobfs_inputs as inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def d():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_04359_b300 import build, dobfs
+    build.build()
+    dobfs.load()
+    dobfs.use_torch_allocator()
+    return dobfs
+
+
+MODES = [("auto", 0, 0), ("topdown", 1, 0), ("bottomup", 2, 0), ("random1", 3, 1), ("random2", 3, 2),
+         ("random3", 3, 77), ("static", 4, 0)]
+
+
+def _run(d, g, root, mode=0, seed=0, flags=0, host=False, **kw):
+    n = g.n
+    if host:
+        lv = np.empty(n, dtype=np.int32)
+        pa = np.empty(n, dtype=np.int32)
+    else:
+        lv = torch.empty(n, dtype=torch.int32, device="cuda")
+        pa = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = g.run(root, lv, pa, d.make_opts(direction=mode, schedule_seed=seed, flags=flags, **kw), want_stats=True)
+    torch.cuda.synchronize()
+    if not host:
+        lv, pa = lv.cpu().numpy(), pa.cpu().numpy()
+    return lv, pa, st
+
+
+def _check_run(og, root, lv, pa, ref_level, ref_parent=None):
+    np.testing.assert_array_equal(lv, ref_level)
+    rule, bad = oracle.check_bfs(og, root, lv, pa)
+    assert rule == 0, (oracle.RULES[rule], bad)
+    if ref_parent is not None:
+        np.testing.assert_array_equal(pa, ref_parent)
+
+
+# ------------------------------------------------------------------ CSR build
+@pytest.mark.parametrize("scale", [6, 11, 16])
+def test_csr_build_matches_oracle_no_reindex(d, scale):
+    spec = inputs.rmat(scale)
+    og = oracle.csr_from_rmat(spec)
+    g = d.rmat_graph(spec, flags=0)
+    off, cols, n2o = g.export()
+    np.testing.assert_array_equal(off, og.off)
+    np.testing.assert_array_equal(cols, og.cols)
+    np.testing.assert_array_equal(n2o, np.arange(spec.n_vertices, dtype=np.int32))
+    info = g.info
+    deg = og.degrees()
+    assert info.n_entries == og.nnz and info.reindexed == 0
+    assert info.n_nonisolated == int((deg > 0).sum()) and info.max_degree == int(deg.max())
+    np.testing.assert_array_equal(g.degrees(), deg)
+
+
+@pytest.mark.parametrize("scale,flags", [(11, 0), (14, 0x10)])
+def test_csr_build_reindex(d, scale, flags):
+    spec = inputs.rmat(scale)
+    og = oracle.csr_from_rmat(spec)
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | flags)
+    off, cols, n2o = g.export()
+    deg = og.degrees()
+    ids = np.arange(og.n)
+    # new ID = rank by (degree descending, original ID ascending)
+    np.testing.assert_array_equal(n2o, np.lexsort((ids, -deg)).astype(np.int32))
+    o2n = np.empty_like(n2o)
+    o2n[n2o] = np.arange(og.n, dtype=np.int32)
+    for i in range(og.n):
+        row = cols[off[i]:off[i + 1]]
+        assert np.all(np.diff(row) > 0)                         # sorted by new ID
+        np.testing.assert_array_equal(np.sort(n2o[row]), og.row(int(n2o[i])))
+        if len(row) > 1:                                        # highest-degree neighbour first
+            assert np.all(np.diff(deg[n2o[row]]) <= 0)
+    assert g.info.offsets_int64 == (1 if flags else 0)
+    np.testing.assert_array_equal(g.degrees(), deg)
+
+
+def test_pairs_and_csr_inputs(d):
+    rng = np.random.default_rng(11)
+    n = 3000
+    src = rng.integers(0, n, 20000).astype(np.int32)
+    dst = rng.integers(0, n, 20000).astype(np.int32)
+    og = oracle.csr_from_pairs(n, src, dst)
+    for flags in (0, d.DOBFS_GRAPH_REINDEX):
+        g = d.pairs_graph(n, src, dst, flags=flags)
+        off, cols, n2o = g.export()
+        if not flags:
+            np.testing.assert_array_equal(off, og.off)
+            np.testing.assert_array_equal(cols, og.cols)
+        else:
+            assert g.info.n_entries == og.nnz
+    # device pointers for the pairs give the same graph
+    g2 = d.pairs_graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    np.testing.assert_array_equal(g2.export()[1], og.cols)
+    # a directed CSR made symmetric by the library
+    order = np.lexsort((dst, src))
+    s_sorted, d_sorted = src[order], dst[order]
+    doff = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(doff, s_sorted + 1, 1)
+    doff = np.cumsum(doff)
+    g3 = d.csr_graph(doff, d_sorted.copy(), n, flags=d.DOBFS_GRAPH_SYMMETRIZE)
+    off3, cols3, _ = g3.export()
+    np.testing.assert_array_equal(off3, og.off)
+    np.testing.assert_array_equal(cols3, og.cols)
+    # the symmetric CSR passes VALIDATE; the directed one does not
+    d.csr_graph(og.off, og.cols, n, flags=d.DOBFS_GRAPH_VALIDATE).close()
+    with pytest.raises(d.DobfsError) as e:
+        d.csr_graph(doff, d_sorted.copy(), n, flags=d.DOBFS_GRAPH_VALIDATE)
+    assert e.value.status == d.DOBFS_ERR_BAD_GRAPH
+    bad = og.cols.copy()
+    bad[5] = n
+    with pytest.raises(d.DobfsError) as e:
+        d.csr_graph(og.off, bad, n)
+    assert e.value.status == d.DOBFS_ERR_BAD_GRAPH
+    with pytest.raises(d.DobfsError) as e:
+        d.pairs_graph(n, src, np.full_like(dst, -1))
+    assert e.value.status == d.DOBFS_ERR_BAD_GRAPH
+
+
+# ------------------------------------------------------------------ BFS parity
+@pytest.fixture(scope="module")
+def s16(d):
+    """R-MAT scale 16, edgefactor 16, int32 offsets, relabel on, reindex off; 16 roots."""
+    spec = inputs.rmat(16)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 16, og.degrees() > 0)
+    lv, pa = oracle.bfs_many(og, roots)
+    return spec, og, roots, lv, pa
+
+
+@pytest.mark.parametrize("name,mode,seed", MODES)
+def test_levels_bit_exact_s16_no_reindex(d, s16, name, mode, seed):
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=0)
+    assert g.info.offsets_int64 == 0
+    for i, r in enumerate(roots):
+        lv, pa, st = _run(d, g, int(r), mode, seed)
+        _check_run(og, int(r), lv, pa, ref_l[i])
+        assert st.teps_edges == oracle.teps_edges(og, ref_l[i])
+        assert st.reached == int((ref_l[i] >= 0).sum())
+        assert st.levels == int(ref_l[i].max()) + 1
+        if mode == 1:
+            assert st.bu_levels == 0
+        if mode == 2:
+            assert st.td_levels == 0
+
+
+@pytest.mark.parametrize("name,mode,seed", MODES)
+def test_levels_bit_exact_s16_reindex_off64(d, s16, name, mode, seed):
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64)
+    for i, r in enumerate(roots[:6]):
+        lv, pa, st = _run(d, g, int(r), mode, seed)
+        _check_run(og, int(r), lv, pa, ref_l[i])
+
+
+def test_canonical_parent_bit_exact(d, s16):
+    spec, og, roots, ref_l, ref_p = s16
+    for flags in (0, d.DOBFS_GRAPH_REINDEX):
+        g = d.rmat_graph(spec, flags=flags)
+        for i, r in enumerate(roots[:8]):
+            lv, pa, _ = _run(d, g, int(r), 0, flags=d.DOBFS_RUN_CANONICAL_PARENT)
+            _check_run(og, int(r), lv, pa, ref_l[i], ref_p[i])
+
+
+def test_host_outputs_and_host_loop(d, s16):
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    r = int(roots[0])
+    lv, pa, st = _run(d, g, r, host=True)
+    _check_run(og, r, lv, pa, ref_l[0])
+    lv2, pa2, st2 = _run(d, g, r, flags=d.DOBFS_RUN_HOST_LOOP)
+    _check_run(og, r, lv2, pa2, ref_l[0])
+    tr = g.trace()
+    assert len(tr) == st2.levels
+    assert sum(t.n_next for t in tr) + 1 == st2.reached
+    assert all(t.ms > 0 for t in tr)
+    assert [t.level for t in tr] == list(range(len(tr)))
+    # the same schedule and counters as the graph-driven run
+    _run(d, g, r)
+    tr1 = g.trace()
+    assert [(t.direction, t.n_frontier, t.m_frontier, t.n_next) for t in tr1] == \
+           [(t.direction, t.n_frontier, t.m_frontier, t.n_next) for t in tr]
+    # direction-optimized: some level bottom-up, the first top-down
+    assert tr1[0].direction == 0 and any(t.direction == 1 for t in tr1)
+
+
+def _pairs_graph(d, n, pairs, flags=0):
+    src = np.array([p[0] for p in pairs], dtype=np.int32)
+    dst = np.array([p[1] for p in pairs], dtype=np.int32)
+    return d.pairs_graph(n, src, dst, flags=flags), oracle.csr_from_pairs(n, src, dst)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("flags", [0, 0x2])
+def test_closed_forms(d, mode, flags):
+    n = 2000  # path: 2000 levels
+    g, og = _pairs_graph(d, n, [(i, i + 1) for i in range(n - 1)], flags)
+    lv, pa, st = _run(d, g, 0, mode, seed=5)
+    assert lv.tolist() == list(range(n)) and st.levels == n
+    lv, pa, _ = _run(d, g, 700, mode, seed=5)
+    assert lv.tolist() == [abs(i - 700) for i in range(n)]
+    # star with 5000 leaves: one long row (chunked top-down, deferred bottom-up)
+    n = 5001
+    g, og = _pairs_graph(d, n, [(0, i) for i in range(1, n)], flags)
+    lv, pa, _ = _run(d, g, 0, mode, seed=5)
+    assert lv.tolist() == [0] + [1] * (n - 1) and np.all(pa[1:] == 0)
+    lv, pa, _ = _run(d, g, 4321, mode, seed=5)
+    assert lv[0] == 1 and lv[4321] == 0 and int((lv == 2).sum()) == n - 2
+    _check_run(og, 4321, lv, pa, oracle.bfs(og, 4321)[0])
+    # binary tree in heap order, plus a separate cycle and an isolated vertex
+    t = 1023
+    pairs = [((i - 1) // 2, i) for i in range(1, t)] + [(t + i, t + (i + 1) % 50) for i in range(50)]
+    n = t + 51
+    g, og = _pairs_graph(d, n, pairs, flags)
+    lv, pa, _ = _run(d, g, 0, mode, seed=5, flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    assert lv[:t].tolist() == [int(np.floor(np.log2(i + 1))) for i in range(t)]
+    assert np.all(lv[t:] == -1) and np.all(pa[t:] == -1)
+    assert pa[:t].tolist() == [0] + [(i - 1) // 2 for i in range(1, t)]
+    lv, pa, st = _run(d, g, n - 1, mode, seed=5)  # isolated root
+    assert lv.tolist() == [-1] * (n - 1) + [0] and pa[n - 1] == n - 1 and st.teps_edges == 0
+
+
+def test_root_out_of_range(d, s16):
+    spec = s16[0]
+    g = d.rmat_graph(spec, flags=0)
+    lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for r in (-1, g.n):
+        with pytest.raises(d.DobfsError) as e:
+            g.run(r, lv)
+        assert e.value.status == d.DOBFS_ERR_INVALID
+
+
+def test_chunglu_small(d):
+    spec = inputs.chunglu(13, max_weight=float(1 << 9))
+    cdf = inputs.chunglu_cdf(spec)
+    src, dst = inputs.chunglu_pairs(spec, cdf)
+    og = oracle.csr_from_pairs(spec.n_vertices, src, dst)
+    g = d.chunglu_graph(spec, cdf, flags=0)
+    off, cols, _ = g.export()
+    np.testing.assert_array_equal(off, og.off)
+    np.testing.assert_array_equal(cols, og.cols)
+    gr = d.chunglu_graph(spec, cdf)
+    roots = inputs.sample_roots(5, og.n, 4, og.degrees() > 0)
+    for r in roots:
+        ref, _, _ = oracle.bfs(og, int(r), want_parent=False)
+        for gg in (g, gr):
+            lv, pa, _ = _run(d, gg, int(r))
+            _check_run(og, int(r), lv, pa, ref)
+
+
+def test_repeated_runs_and_streams(d, s16):
+    spec, og, roots, ref_l, _ = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for i, r in enumerate(roots[:6]):
+        s = s1 if i % 2 else s2
+        lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(s):
+            g.run(int(r), lv, None, d.make_opts(stream=s))
+        outs.append((i, lv, s))
+    torch.cuda.synchronize()
+    for i, lv, s in outs:
+        np.testing.assert_array_equal(lv.cpu().numpy(), ref_l[i])
