@@ -1,0 +1,363 @@
+"""Benchmark: single-source direction-optimized BFS, GTEPS on R-MAT scale 28.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--scale S] [--impl ours|reference]
+
+One step = one BFS from one seeded root on the resident graph: status init,
+the device-driven level loop (top-down / bottom-up steps and the switch),
+and the outputs (level and parent per vertex, original IDs) written to device
+buffers. GTEPS per root = undirected edges in the root's component / device
+time (CUDA events on the launching stream); the reported value is the
+harmonic mean over the K timed roots (Graph500 convention). The graph
+(~36 GB at scale 28) is far larger than L2, so no flush is needed between
+steps. With N > 1 (torchrun) every rank runs independent replicas on its own
+GPU: BFS from a single root does not shard without a per-level exchange, so
+the job's value is the sum of the ranks' rates measured over the max time.
+
+Also reported: the roofline of the dominant kernel (the bottom-up step,
+measured per level with CUDA events in host-driven mode on the same roots),
+an end-to-end number through the C ABI with host (pinned) output buffers,
+the CPU oracle on a bounded sample, SM clocks sampled during the timed
+region, and the number of kernels launched.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS at R-MAT scale 28; batched BFS/s and p50/p99 latency vs serial BFS"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scale: int = 22, n_roots: int = 4) -> dict:
+    """The CPU oracle (serial queue BFS, 1 thread) on a bounded sample."""
+    import dobfs_inputs as inputs
+    import oracle
+
+    spec = inputs.rmat(scale)
+    g = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), g.n, n_roots, g.degrees() > 0)
+    t_sum, rates, e_sum = 0.0, [], 0
+    for r in roots:
+        t0 = time.perf_counter()
+        lv, _, _ = oracle.bfs(g, int(r), want_parent=True)
+        dt = time.perf_counter() - t0
+        e = oracle.teps_edges(g, lv)
+        t_sum += dt
+        e_sum += e
+        rates.append(e / dt / 1e9)
+    hm = len(rates) / sum(1.0 / x for x in rates)
+    return {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": "oracle serial FIFO BFS with canonical parents, %d seeded roots on R-MAT scale %d "
+                      "(edgefactor 16, same generator; CSR build excluded), harmonic mean" % (n_roots, scale),
+            "seconds": t_sum}
+
+
+def run_reference(args) -> None:
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import dobfs_inputs as inputs
+    import oracle
+
+    scale = min(args.scale, 22)
+    spec = inputs.rmat(scale)
+    g = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), g.n, args.steps + args.warmup, g.degrees() > 0)
+    for r in roots[:args.warmup]:
+        oracle.bfs(g, int(r))
+    rates, t_sum = [], 0.0
+    for r in roots[args.warmup:]:
+        t0 = time.perf_counter()
+        lv, _, _ = oracle.bfs(g, int(r))
+        dt = time.perf_counter() - t0
+        t_sum += dt
+        rates.append(oracle.teps_edges(g, lv) / dt / 1e9)
+    hm = len(rates) / sum(1.0 / x for x in rates)
+    sample = ("oracle serial FIFO BFS with canonical parents on R-MAT scale %d (same generator, edgefactor 16; "
+              "CSR build excluded), one root per step" % scale)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": hm, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_sum / max(1, len(rates)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "rmat-s%d-ef16" % scale, "scale": scale, "edgefactor": 16},
+        "cpu_baseline": {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": hm, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--scale", type=int, default=28)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-reindex", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import dobfs_inputs as inputs
+    from paper_1503_04359_b300 import build as build_mod
+    from paper_1503_04359_b300 import dobfs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build_mod.build()
+    if dist:
+        dist.barrier()
+    dobfs.load()
+    dobfs.use_torch_allocator()
+    dev = torch.cuda.current_device()
+
+    spec = inputs.rmat(args.scale)
+    flags = 0 if args.no_reindex else dobfs.DOBFS_GRAPH_REINDEX
+    t0 = time.perf_counter()
+    g = dobfs.rmat_graph(spec, flags=flags)
+    build_s = time.perf_counter() - t0
+    info = g.info
+    n = int(info.n_vertices)
+    deg = g.degrees()
+    roots_all = inputs.sample_roots(inputs.root_seed(spec.seed) + rank * 0x1000, n, args.steps + args.warmup, deg > 0)
+    warm, roots = roots_all[:args.warmup], roots_all[args.warmup:]
+
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    opts = dobfs.make_opts(stream=stream)
+
+    # untimed pass: per-root edge counts, levels and algorithmic bytes
+    teps, alg_bytes, launches, levels = [], [], [], []
+    for r in list(warm) + list(roots):
+        st = g.run(int(r), level, parent, opts, want_stats=True)
+        tr = g.trace()
+        teps.append(st.teps_edges)
+        alg_bytes.append(st.alg_bytes)
+        levels.append(st.levels)
+        # kernels: init + output + per level (switch + 2 expand kernels, + 1 conversion on a direction
+        # change) + the closing switch
+        k = 3
+        prev = 0
+        for t in tr:
+            k += 3 + (1 if t.direction != prev else 0)
+            prev = t.direction
+        launches.append(k)
+    teps, alg_bytes = teps[args.warmup:], alg_bytes[args.warmup:]
+    launches, levels = launches[args.warmup:], levels[args.warmup:]
+
+    # timed pass
+    for r in warm:
+        g.run(int(r), level, parent, opts)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(roots) + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        wall0 = time.perf_counter()
+        ev[0].record(stream)
+        for i, r in enumerate(roots):
+            g.run(int(r), level, parent, opts)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(roots))]
+    total_ms = sum(ms)
+    rates = [e / (t * 1e-3) / 1e9 for e, t in zip(teps, ms)]
+    hmean = len(rates) / sum(1.0 / x for x in rates)
+    total_edges = float(sum(teps))
+    clocks = clk.summary()
+
+    # job value over ranks: sum of per-rank rates at the slowest rank's time
+    job_value, job_ms = hmean, total_ms
+    if dist:
+        t = torch.tensor([total_ms, total_edges, hmean], dtype=torch.float64, device="cuda")
+        allt = [torch.zeros_like(t) for _ in range(ws)]
+        dist.all_gather(allt, t)
+        mx = max(float(x[0]) for x in allt)
+        job_ms = mx
+        job_value = sum(float(x[1]) for x in allt) / (mx * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: per-level events in host-driven mode on the same roots
+    peak, peak_kind = _peaks()
+    hl = dobfs.make_opts(stream=stream, flags=dobfs.DOBFS_RUN_HOST_LOOP)
+    per_kind = {0: [0.0, 0], 1: [0.0, 0]}  # direction -> [ms, bytes]
+    n_launch = {0: 0, 1: 0}
+    for r in roots[:min(len(roots), 16)]:
+        g.run(int(r), level, parent, hl)
+        torch.cuda.synchronize()
+        for t in g.trace():
+            per_kind[t.direction][0] += t.ms_main
+            per_kind[t.direction][1] += t.alg_bytes
+            n_launch[t.direction] += 1
+    dom = 1 if per_kind[1][0] >= per_kind[0][0] else 0
+    dom_ms, dom_bytes = per_kind[dom]
+    achieved = (dom_bytes / n_launch[dom]) / ((dom_ms / n_launch[dom]) * 1e-3) / 1e9 if n_launch[dom] else 0.0
+    whole_gbs = (sum(alg_bytes) / (total_ms * 1e-3)) / 1e9
+
+    # end to end through the C ABI with pinned host outputs (D2H inside the timed region)
+    hl_lv = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hl_pa = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    e2e_roots = roots[:max(1, min(args.e2e_steps, len(roots)))]
+    g.run(int(e2e_roots[0]), hl_lv.numpy(), hl_pa.numpy(), opts)
+    e2e_rates = []
+    e2e_t = 0.0
+    for i, r in enumerate(e2e_roots):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.run(int(r), hl_lv.numpy(), hl_pa.numpy(), opts)  # returns after the D2H copies completed
+        dt = time.perf_counter() - t0
+        e2e_t += dt
+        e2e_rates.append(teps[i] / dt / 1e9)
+    e2e_hm = len(e2e_rates) / sum(1.0 / x for x in e2e_rates)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank != 0:
+        return
+    result = {
+        "metric": METRIC,
+        "value": job_value,
+        "unit": "GTEPS",
+        "n_gpus": ws,
+        "steps": len(roots),
+        "warmup": args.warmup,
+        "ms_per_step": job_ms / len(roots),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex"),
+            "scale": args.scale, "edgefactor": 16, "a": spec.a, "b": spec.b, "c": spec.c, "seed": spec.seed,
+            "n_vertices": n, "n_entries": int(info.n_entries), "n_nonisolated": int(info.n_nonisolated),
+            "offsets_int64": int(info.offsets_int64), "reindexed": int(info.reindexed),
+            "roots": len(roots), "parallelism": "replicas" if ws > 1 else "single-gpu",
+            "l2": "inputs larger than L2 (graph %.1f GB resident), no flush" % (info.device_bytes / 1e9),
+            "build_s": round(build_s, 2), "device_bytes": int(info.device_bytes),
+        },
+        "per_root": {"ms_mean": total_ms / len(roots), "ms_min": min(ms), "ms_max": max(ms),
+                     "gteps_min": min(rates), "gteps_max": max(rates), "levels_mean": float(np.mean(levels)),
+                     "teps_edges_mean": total_edges / len(roots), "aggregate_gteps": total_edges / total_ms / 1e6,
+                     "wall_s": wall},
+        "roofline": {
+            "kernel": "bottom-up step (k_bu + k_bu_long)" if dom == 1 else "top-down step (k_td_bin + k_td_chunks)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "traffic": None,
+            "whole_bfs_alg_gbs": whole_gbs, "whole_bfs_frac": whole_gbs / peak,
+            "alg_bytes_per_root": float(np.mean(alg_bytes)),
+        },
+        "e2e": {"value": e2e_hm, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * n,
+                "steps": len(e2e_roots), "note": "dobfs_run with pinned host outputs; root passed by value"},
+        "gpu_launches": int(sum(launches)),
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(result))
+
+
+if __name__ == "__main__":
+    main()
