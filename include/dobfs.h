@@ -227,6 +227,43 @@ typedef struct {
 /* Copies up to max_levels records of the last run; *n_out = records written. */
 int dobfs_last_trace(const dobfs_graph* g, dobfs_level_trace* out, int32_t max_levels, int32_t* n_out);
 
+/* ------------------------------------------------------------------ allocation-free runs */
+
+/*
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory when they need a BFS: code working in
+ * a memory budget reserved up front, allocation-free real-time or serving
+ * paths, or plugins inside a framework that owns every device allocation.
+ * dobfs_run needs a graph from dobfs_graph_create, which allocates; this
+ * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).
+ *
+ * BFS from `root` on the caller's CSR: row_offsets[n_vertices+1] (int32) and
+ * col_indices[row_offsets[n_vertices]] (int32), both device pointers, the
+ * graph undirected (every edge stored both ways). level_out[n_vertices] and
+ * parent_out[n_vertices] (device pointers; parent_out may be NULL) receive
+ * the level (-1 if unreached) and a BFS parent (parent[root] = root).
+ *
+ * Working memory: one static device array of about 8.4 MB, sized for at
+ * most DOBFS_STATIC_MAX_VERTICES vertices, held by every GPU that loads the
+ * library until the process exits. n_vertices above that maximum (or below
+ * 1), a root out of range or a NULL pointer give DOBFS_ERR_INVALID before
+ * any GPU work.
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture. Every call on a device shares the array and
+ * clears what must start at zero. The library serialises calls and each
+ * call returns only when its GPU work on `stream` has finished, so calls do
+ * not overlap; GPU work that overlapped with a call (for instance the same
+ * array used from another thread bypassing this lock) would race on it.
+ * Levels are chosen by the alpha/beta rule with the defaults of
+ * dobfs_run_opts_init, one small device-to-host read per level.
+ */
+#define DOBFS_STATIC_MAX_VERTICES (1 << 20)
+int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int32_t n_vertices, int32_t root,
+                     int32_t* level_out, int32_t* parent_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

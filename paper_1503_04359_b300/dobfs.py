@@ -36,6 +36,7 @@ DOBFS_DIR_AUTO, DOBFS_DIR_TOPDOWN, DOBFS_DIR_BOTTOMUP, DOBFS_DIR_RANDOM, DOBFS_D
 DOBFS_RUN_CANONICAL_PARENT = 0x1
 DOBFS_RUN_HOST_LOOP = 0x2
 DOBFS_RUN_SYNC_STATS = 0x4
+DOBFS_STATIC_MAX_VERTICES = 1 << 20
 
 
 class DobfsError(RuntimeError):
@@ -99,6 +100,7 @@ def load() -> ctypes.CDLL:
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
         "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
         "dobfs_last_trace": (c_int, [G, ctypes.POINTER(dobfs_level_trace), i32, ctypes.POINTER(i32)]),
+        "dobfs_run_static": (c_int, [vp, vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -262,6 +264,14 @@ def dobfs_last_trace(g: int, max_levels: int = 4096) -> list[dobfs_level_trace]:
     n = ctypes.c_int32(0)
     _check(load().dobfs_last_trace(g, buf, max_levels, ctypes.byref(n)))
     return [buf[i] for i in range(n.value)]
+
+
+def dobfs_run_static(row_offsets, col_indices, n_vertices: int, root: int, level_out, parent_out=None,
+                     stream=None) -> None:
+    """BFS on a caller's device CSR (int32 offsets) with no device allocation: the
+    library's working memory is a fixed static device array (see include/dobfs.h)."""
+    _check(load().dobfs_run_static(_ptr(row_offsets), _ptr(col_indices), int(n_vertices), int(root),
+                                   _ptr(level_out), _ptr(parent_out), _stream(stream)))
 
 
 # ---------------------------------------------------------------- convenience wrapper
