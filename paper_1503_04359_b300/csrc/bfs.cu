@@ -59,6 +59,7 @@ struct BfsArgs {
   const int32_t* cols;
   const uint32_t* iso;
   const int32_t* o2n;  // NULL when not reindexed
+  const int2* firstdeg;  // (first neighbour, degree) per vertex; first = -1 for isolated vertices
   uint32_t* visited;
   uint32_t* fbm0;
   uint32_t* fbm1;
@@ -69,7 +70,7 @@ struct BfsArgs {
   int32_t* def;
   BfsCtl* ctl;
   LevelRec* trace;
-  int64_t n, nnz, words, cand_words, rec_cap;
+  int64_t n, nnz, words, cand_words, rec_cap, n_nonisolated;
 };
 
 __device__ __forceinline__ bool test_bit(const uint32_t* __restrict__ bm, int32_t v) {
@@ -86,19 +87,38 @@ __device__ __forceinline__ void enqueue(unsigned int* tail, int32_t* q, int32_t 
   q[base + g.thread_rank()] = v;
 }
 
-// Top-down claim of neighbour v by frontier vertex u (Algorithm 1, top-down
-// branch): the first thread to set v's visited bit writes level and parent
-// and enqueues v; its degree goes into the next frontier's edge count m_f.
+// Four top-down claims at once: the visited words are read first, then the
+// atomics for the still-unvisited neighbours are issued together, then the
+// winners write (level, parent) and read their degree. Keeping the four
+// chains independent overlaps their memory latencies. Returns the winners
+// as a 4-bit mask; `m_new` accumulates their degrees.
 template <class OffT>
-__device__ __forceinline__ void td_claim(const BfsArgs<OffT>& A, int32_t v, int32_t u, int32_t next_level,
-                                         int32_t* nq, unsigned long long& m_new) {
-  const uint32_t bit = 1u << (v & 31);
-  uint32_t* w = A.visited + (v >> 5);
-  if (__ldcg(w) & bit) return;
-  if (atomicOr(w, bit) & bit) return;
-  A.lp[v] = make_int2(next_level, u);
-  m_new += (unsigned long long)((int64_t)A.off[v + 1] - (int64_t)A.off[v]);
-  enqueue(&A.ctl->q_tail, nq, v);
+__device__ __forceinline__ unsigned td_claim4(const BfsArgs<OffT>& A, const int32_t (&v)[4], unsigned valid,
+                                              int32_t u, int32_t next_level, unsigned long long& m_new) {
+  uint32_t w[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) w[t] = ((valid >> t) & 1u) ? __ldcg(A.visited + (v[t] >> 5)) : ~0u;
+  unsigned cand = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (!((w[t] >> (v[t] & 31)) & 1u)) cand |= 1u << t;
+  unsigned won = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if ((cand >> t) & 1u) {
+      const uint32_t bit = 1u << (v[t] & 31);
+      if (!(atomicOr(A.visited + (v[t] >> 5), bit) & bit)) won |= 1u << t;
+    }
+  int32_t d[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if ((won >> t) & 1u) {
+      A.lp[v[t]] = make_int2(next_level, u);
+      d[t] = __ldg(&A.firstdeg[v[t]].y);
+    }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) m_new += (unsigned long long)d[t];
+  return won;
 }
 
 template <class OffT>
@@ -236,7 +256,21 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
     const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
     ex += (unsigned long long)(e - s);
     if (e - s <= kTdSmall) {
-      for (int64_t j = s; j < e; ++j) td_claim(A, A.cols[j], u, L + 1, nxt, m_new);
+      for (int64_t j = s; j < e; j += 4) {
+        int32_t v[4];
+        unsigned valid = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          v[t] = (j + t < e) ? A.cols[j + t] : 0;
+          if (j + t < e) valid |= 1u << t;
+        }
+        unsigned won = td_claim4(A, v, valid, u, L + 1, m_new);
+        while (won) {
+          const int t = __ffs(won) - 1;
+          won &= won - 1;
+          enqueue(&A.ctl->q_tail, nxt, v[t]);
+        }
+      }
     } else {
       const int64_t a = s & ~3ll;
       const unsigned nch = (unsigned)ceil_div(e - a, kChunk);
@@ -274,13 +308,37 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
     const int64_t lo = (s & ~3ll) + (int64_t)rc.y * kChunk;
     const int64_t hi = min(e, lo + kChunk);
     const int64_t lo_ok = max(s, lo);
-    for (int64_t p = lo + 4 * (int64_t)lane; p < hi; p += 128) {
-      const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
-      const int32_t vs[4] = {x.x, x.y, x.z, x.w};
+    for (int64_t pb = lo; pb < hi; pb += 128) {  // uniform trip count: the warp enqueues together
+      const int64_t p = pb + 4 * (int64_t)lane;
+      int32_t v[4] = {0, 0, 0, 0};
+      unsigned valid = 0;
+      if (p < hi) {
+        const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int64_t idx = p + t;
-        if (idx >= lo_ok && idx < hi) td_claim(A, vs[t], u, L + 1, nxt, m_new);
+        for (int t = 0; t < 4; ++t)
+          if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
+      }
+      const unsigned won = valid ? td_claim4(A, v, valid, u, L + 1, m_new) : 0u;
+      const unsigned cnt = (unsigned)__popc(won);
+      unsigned incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total) {
+        unsigned qb = 0;
+        if (lane == 31) qb = atomicAdd(&A.ctl->q_tail, total);
+        qb = __shfl_sync(0xffffffffu, qb, 31);
+        unsigned pos = qb + incl - cnt;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if ((won >> t) & 1u) nxt[pos++] = v[t];
       }
     }
   }
@@ -333,53 +391,98 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
   }
 }
 
-// Bottom-up, part 1 (Algorithm 1, bottom-up branch): one warp per visited
-// word; every unvisited vertex scans its first kBuT neighbours in row order
-// and stops at the first one in the frontier.
+// Bottom-up, part 1 (Algorithm 1, bottom-up branch). A warp takes 32
+// consecutive visited words (1024 vertices) at a time: one coalesced load of
+// the visited and isolated words gives the candidates (unvisited vertices
+// with an edge), which are compacted so that every lane holds one candidate
+// per round. A candidate first tests its first neighbour, read with its
+// degree from the packed (first, degree) array: rows are sorted with the
+// highest-degree neighbour first, so most vertices that have a frontier
+// neighbour resolve with that one 8-byte load. Otherwise the lane scans the
+// rest of its first kBuT entries, four loads at a time, and stops at the
+// first neighbour in the frontier; longer rows without a hit go to the
+// deferred list. Found vertices are collected per word in shared memory and
+// every lane writes its own next-frontier and visited word: no global atomics.
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
+  __shared__ uint32_t s_found[kThreads / 32][32];
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
   uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
   const unsigned lane = lane_id();
+  const int wid = threadIdx.x >> 5;
   unsigned long long n_new = 0, m_new = 0, ex = 0, sc = 0;
+  const int64_t groups = ceil_div(A.cand_words, 32);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < A.cand_words; w += warps) {
-    const uint32_t vis = A.visited[w];
-    const uint32_t skip = vis | A.iso[w];
-    const bool cand = !((skip >> lane) & 1u);
-    bool found = false;
-    int32_t parent = -1;
-    int64_t deg = 0;
-    if (cand) {
-      const int32_t v = (int32_t)(w * 32 + lane);
-      const int64_t s = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
-      deg = e - s;
-      const int64_t lim = min(e, s + kBuT);
-      int64_t j = s;
-      for (; j < lim; ++j) {
-        const int32_t u = A.cols[j];
-        if (test_bit(front, u)) {
-          found = true;
-          parent = u;
-          break;
-        }
+  for (int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; grp < groups; grp += warps) {
+    const int64_t w = grp * 32 + lane;
+    const bool in = w < A.cand_words;
+    const uint32_t vis = in ? A.visited[w] : ~0u;
+    const uint32_t cand = in ? ~(vis | A.iso[w]) : 0u;
+    const unsigned cnt = (unsigned)__popc(cand);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    s_found[wid][lane] = 0u;
+    __syncwarp();
+    sc += cnt;
+    for (unsigned base = 0; base < total; base += 32) {
+      const unsigned k = base + lane;
+      // word j holding candidate k: the first lane whose inclusive count exceeds k
+      unsigned j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned probe = __shfl_sync(0xffffffffu, incl, j + step - 1);
+        if (probe <= k) j += step;
       }
-      ex += (unsigned long long)(found ? j - s + 1 : lim - s);
-      if (!found && e > lim) enqueue(&A.ctl->n_def, A.def, v);
-      if (found) A.lp[v] = make_int2(L + 1, parent);
+      const uint32_t cw = __shfl_sync(0xffffffffu, cand, j);
+      const unsigned ex_j = __shfl_sync(0xffffffffu, incl - cnt, j);
+      if (k >= total) continue;
+      const unsigned bit = __fns(cw, 0, (int)(k - ex_j) + 1);
+      const int32_t v = (int32_t)((grp * 32 + j) * 32 + bit);
+      const int2 fd = __ldg(A.firstdeg + v);
+      int32_t parent = -1;
+      unsigned long long exv = 1;
+      if (test_bit(front, fd.x)) {
+        parent = fd.x;
+      } else if (fd.y > 1) {
+        const int64_t s0 = (int64_t)A.off[v];
+        const int64_t lim = s0 + min(fd.y, kBuT);
+        for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
+          int32_t u[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) u[t] = (p + t < lim) ? A.cols[p + t] : -1;
+          bool h[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
+#pragma unroll
+          for (int t = 3; t >= 0; --t)
+            if (h[t]) parent = u[t];
+          exv += (unsigned long long)min((int64_t)4, lim - p);
+        }
+        if (parent < 0 && fd.y > kBuT) enqueue(&A.ctl->n_def, A.def, v);
+      }
+      ex += exv;
+      if (parent >= 0) {
+        atomicOr(&s_found[wid][j], 1u << bit);
+        A.lp[v] = make_int2(L + 1, parent);
+        n_new += 1;
+        m_new += (unsigned long long)fd.y;
+      }
     }
-    const unsigned fm = __ballot_sync(0xffffffffu, found);
-    const unsigned cm = __ballot_sync(0xffffffffu, cand);
-    if (lane == 0) {
-      next[w] = fm;
-      if (fm) A.visited[w] = vis | fm;
-      n_new += (unsigned)__popc(fm);
-      sc += (unsigned)__popc(cm);
+    __syncwarp();
+    if (in) {
+      const uint32_t f = s_found[wid][lane];
+      next[w] = f;
+      if (f) A.visited[w] = vis | f;
     }
-    if (found) m_new += (unsigned long long)deg;
+    __syncwarp();
   }
   n_new = block_sum_u64(n_new, sh);
   m_new = block_sum_u64(m_new, sh);
@@ -451,18 +554,59 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
 }
 
 // Results in original IDs: level_out[o], parent_out[o] for every vertex.
+// Each thread handles four consecutive original IDs (16-byte map loads and
+// output stores). Vertices renumbered past the last one with an edge are
+// isolated: unreached unless they are the root, so only the root among them
+// needs the visited bit and the (level, parent) gather.
+template <class OffT>
+__device__ __forceinline__ void output_one(const BfsArgs<OffT>& A, const int32_t* __restrict__ n2o, int32_t v,
+                                           int32_t root, int32_t& lev, int32_t& par) {
+  lev = -1;
+  par = -1;
+  if (A.o2n && v >= A.n_nonisolated && v != root) return;
+  if ((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u) {
+    const int2 x = A.lp[v];
+    lev = x.x;
+    par = n2o ? __ldg(n2o + x.y) : x.y;
+  }
+}
+
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
-                                                     int32_t* __restrict__ level_out,
+                                                     int32_t root_orig, int32_t* __restrict__ level_out,
                                                      int32_t* __restrict__ parent_out) {
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = A.o2n ? A.o2n[o] : (int32_t)o;
-    int32_t lev = -1, par = -1;
-    if ((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u) {
-      const int2 x = A.lp[v];
-      lev = x.x;
-      par = n2o ? n2o[x.y] : x.y;
+  const int32_t root = A.o2n ? __ldg(A.o2n + root_orig) : root_orig;
+  const int64_t quads = A.n >> 2;
+  const bool vec = ((reinterpret_cast<uintptr_t>(level_out) | reinterpret_cast<uintptr_t>(parent_out)) & 15) == 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t q = tid; q < quads; q += stride) {
+    const int64_t o = q * 4;
+    int32_t v[4];
+    if (A.o2n) {
+      const int4 m = __ldg(reinterpret_cast<const int4*>(A.o2n) + q);
+      v[0] = m.x; v[1] = m.y; v[2] = m.z; v[3] = m.w;
+    } else {
+      v[0] = (int32_t)o; v[1] = (int32_t)o + 1; v[2] = (int32_t)o + 2; v[3] = (int32_t)o + 3;
     }
+    int32_t lev[4], par[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) output_one(A, n2o, v[t], root, lev[t], par[t]);
+    if (vec) {
+      reinterpret_cast<int4*>(level_out)[q] = make_int4(lev[0], lev[1], lev[2], lev[3]);
+      if (parent_out) reinterpret_cast<int4*>(parent_out)[q] = make_int4(par[0], par[1], par[2], par[3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        level_out[o + t] = lev[t];
+        if (parent_out) parent_out[o + t] = par[t];
+      }
+    }
+  }
+  for (int64_t o = quads * 4 + tid; o < A.n; o += stride) {  // ragged tail
+    const int32_t v = A.o2n ? __ldg(A.o2n + o) : (int32_t)o;
+    int32_t lev, par;
+    output_one(A, n2o, v, root, lev, par);
     level_out[o] = lev;
     if (parent_out) parent_out[o] = par;
   }
@@ -493,6 +637,16 @@ __global__ void __launch_bounds__(kThreads) k_canonical_parent(BfsArgs<OffT> A, 
   }
 }
 
+// (first neighbour, degree) of every vertex, for the bottom-up first test.
+template <class OffT>
+__global__ void k_firstdeg(const OffT* __restrict__ off, const int32_t* __restrict__ cols, int64_t n,
+                           int2* __restrict__ fd) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = (int64_t)off[v], e = (int64_t)off[v + 1];
+    fd[v] = make_int2(e > s ? cols[s] : -1, (int32_t)(e - s));
+  }
+}
+
 int grid_cap(int per_sm) { return sm_count() * per_sm; }
 
 template <class OffT>
@@ -502,6 +656,7 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   A.cols = g->cols.as<int32_t>();
   A.iso = g->isolated.as<uint32_t>();
   A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
+  A.firstdeg = g->firstdeg.as<int2>();
   A.visited = g->visited.as<uint32_t>();
   A.fbm0 = g->fbm0.as<uint32_t>();
   A.fbm1 = g->fbm1.as<uint32_t>();
@@ -519,6 +674,7 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   // degree-sorted IDs these are all isolated vertices
   A.cand_words = g->reindexed ? ceil_div(std::max<int64_t>(g->n_nonisolated, 1), 32) : g->words;
   A.rec_cap = g->rec_cap;
+  A.n_nonisolated = g->n_nonisolated;
   return A;
 }
 
@@ -704,9 +860,9 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   } else {
     DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
   }
-  const int out_grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
+  const int out_grid = (int)std::min<int64_t>(ceil_div(ceil_div(g->n, 4), kThreads), (int64_t)grid_cap(16));
   const int32_t* n2o = g->reindexed ? g->new2orig.as<int32_t>() : nullptr;
-  k_output<OffT><<<out_grid, kThreads, 0, s>>>(A, n2o, lv, pa);
+  k_output<OffT><<<out_grid, kThreads, 0, s>>>(A, n2o, root, lv, pa);
   if (pa && (o.flags & DOBFS_RUN_CANONICAL_PARENT))
     k_canonical_parent<OffT><<<grid_cap(8), kThreads, 0, s>>>(A, n2o, pa);
   DOBFS_CUDA_TRY(cudaGetLastError());
@@ -759,6 +915,17 @@ int graph_alloc_workspace(dobfs_graph* g) {
   g->rec_cap = std::min<int64_t>(g->n, g->nnz / (kTdSmall + 1)) + g->nnz / kChunk + 64;
   DOBFS_TRY(g->rec.alloc(sizeof(int2) * (size_t)g->rec_cap, s));
   DOBFS_TRY(g->deferred.alloc(sizeof(int32_t) * (size_t)g->n, s));
+  DOBFS_TRY(g->firstdeg.alloc(sizeof(int2) * (size_t)g->n, s));
+  {
+    const int grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
+    if (g->off64)
+      k_firstdeg<int64_t><<<grid, kThreads, 0, s>>>(g->off.as<int64_t>(), g->cols.as<int32_t>(), g->n,
+                                                   g->firstdeg.as<int2>());
+    else
+      k_firstdeg<int32_t><<<grid, kThreads, 0, s>>>(g->off.as<int32_t>(), g->cols.as<int32_t>(), g->n,
+                                                   g->firstdeg.as<int2>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+  }
   DOBFS_TRY(g->ctl.alloc(sizeof(BfsCtl), s));
   DOBFS_TRY(g->trace.alloc(sizeof(LevelRec) * kMaxTrace, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(g->ctl.ptr, 0, sizeof(BfsCtl), s));

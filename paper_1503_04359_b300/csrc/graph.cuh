@@ -76,6 +76,7 @@ struct dobfs_graph {
   dobfs::DevBuf rec;                  // int2[] top-down chunk records
   int64_t rec_cap = 0;
   dobfs::DevBuf deferred;             // int32[n]
+  dobfs::DevBuf firstdeg;             // int2[n]: (first neighbour, degree)
   dobfs::DevBuf ctl;                  // BfsCtl
   dobfs::DevBuf trace;                // LevelRec[kMaxTrace]
   dobfs::DevBuf out_stage;            // int32[2n] staging for host outputs (lazy)
