@@ -71,10 +71,11 @@ const char* dobfs_last_error(void);
 
 /* Graph build flags. */
 #define DOBFS_GRAPH_SYMMETRIZE 0x1u   /* add v->u for every stored u->v */
-#define DOBFS_GRAPH_REINDEX 0x2u      /* degree-sorted renumbering (Sec. 3.4) */
+#define DOBFS_GRAPH_REINDEX 0x2u      /* degree-sorted renumbering by degree class (Sec. 3.4) */
 #define DOBFS_GRAPH_DEVICE_PTRS 0x4u  /* inputs are device pointers (skip detection) */
 #define DOBFS_GRAPH_VALIDATE 0x8u     /* reject input that is not symmetric */
 #define DOBFS_GRAPH_OFFSETS64 0x10u   /* store int64 row offsets even if int32 would do */
+#define DOBFS_GRAPH_REINDEX_EXACT 0x20u /* degree-sorted renumbering by exact degree (Sec. 3.4) */
 
 /*
  * Builds a graph from CSR arrays: row_offsets[n_vertices+1] (int32, or int64
@@ -84,9 +85,16 @@ const char* dobfs_last_error(void);
  * each row is sorted. With DOBFS_GRAPH_SYMMETRIZE the reverse of every entry
  * is added first; without it the input must already be symmetric, which
  * DOBFS_GRAPH_VALIDATE checks (DOBFS_ERR_BAD_GRAPH otherwise).
- * With DOBFS_GRAPH_REINDEX vertices are renumbered by decreasing degree (ties
- * by increasing original ID) and every row is sorted by the new IDs, which
- * puts the highest-degree neighbour first (Sec. 3.4).
+ * With DOBFS_GRAPH_REINDEX_EXACT vertices are renumbered by decreasing
+ * degree (ties by increasing original ID) and every row is sorted by the new
+ * IDs, which puts the highest-degree neighbour first (Sec. 3.4).
+ * DOBFS_GRAPH_REINDEX renumbers by decreasing degree class instead: degrees
+ * below 8 are their own class, degrees in [8, 4096) fall into four classes
+ * per octave (the two bits after the leading one), degrees of 4096 or more
+ * keep their exact order; ties by increasing original ID. Rows then start
+ * with a neighbour of the highest class, and consecutive original IDs of a
+ * class get consecutive new IDs, which keeps the translation of the results
+ * back to original IDs close to sequential.
  * Row offsets are stored as int32 when the entry count fits, else int64.
  * Errors: DOBFS_ERR_INVALID (n_vertices < 1 or > 2^31-1, negative sizes,
  * NULL pointers with n_entries > 0), DOBFS_ERR_BAD_GRAPH (column or offset

@@ -26,6 +26,8 @@ namespace dobfs {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr uint64_t kHubDegree = 4096;   // degrees from here on keep their exact order
+constexpr uint64_t kQuantClasses = 64;  // above the largest quantised class (43)
 
 __device__ __forceinline__ int64_t part_lo(int64_t n, int p, int P) {
   return (int64_t)(((unsigned __int128)n * (unsigned)p) / (unsigned)P);
@@ -234,13 +236,28 @@ __global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t wor
   if (threadIdx.x == 0) atomicAdd(&stats[0], nonzero);
 }
 
-// Vertex keys for the degree-sorted order: (2^b-1 - degree) << b | id, so an
-// ascending sort gives decreasing degree, ties by increasing original ID.
-__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b, uint64_t* __restrict__ keys) {
-  const uint64_t dmax = (1ull << b) - 1ull;
+// Degree class used by the renumbering. Exact order (DOBFS_GRAPH_REINDEX_EXACT):
+// the degree itself. Class order (DOBFS_GRAPH_REINDEX): degrees below 8 are
+// their own class, degrees in [8, 4096) are cut into four classes per
+// octave (the two bits below the leading one), and degrees of 4096 and more
+// (the hubs) keep their exact order above every quantised class. Both are
+// non-decreasing in the degree, so the renumbering stays by decreasing
+// degree up to ties inside a class, which are broken by original ID.
+__device__ __forceinline__ uint64_t degree_class(uint64_t d, bool exact) {
+  if (exact || d >= kHubDegree) return exact ? d : kQuantClasses + d;
+  if (d < 8) return d;
+  const int e = 63 - __clzll((long long)d);  // floor(log2 d) >= 3
+  return 8 + 4 * (uint64_t)(e - 3) + ((d >> (e - 2)) & 3ull);
+}
+
+// Vertex keys for the renumbering: (cmax - class(degree)) << b | id, so an
+// ascending sort gives decreasing class, ties by increasing original ID.
+__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b, int cls_bits, int exact,
+                              uint64_t* __restrict__ keys) {
+  const uint64_t cmax = (1ull << cls_bits) - 1ull;
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t d = (uint64_t)(off[u + 1] - off[u]);
-    keys[u] = ((dmax - d) << b) | (uint64_t)u;
+    keys[u] = ((cmax - degree_class(d, exact != 0)) << b) | (uint64_t)u;
   }
 }
 
@@ -366,7 +383,7 @@ int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t m, uint32_t flags, cud
   }
 
   const int64_t n = g->n;
-  if (flags & DOBFS_GRAPH_REINDEX) {
+  if (flags & (DOBFS_GRAPH_REINDEX | DOBFS_GRAPH_REINDEX_EXACT)) {
     // degrees in original IDs
     DevBuf off0;
     DOBFS_TRY(off0.alloc(sizeof(int64_t) * (size_t)(n + 1), s));
@@ -376,10 +393,13 @@ int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t m, uint32_t flags, cud
     DevBuf vk, vt;
     DOBFS_TRY(vk.alloc(sizeof(uint64_t) * (size_t)n, s));
     DOBFS_TRY(vt.alloc(sizeof(uint64_t) * (size_t)n, s));
-    k_vertex_keys<<<grid_for(n), kThreads, 0, s>>>(off0.as<int64_t>(), n, b, vk.as<uint64_t>());
+    // class < 64 + 2^b <= 2^(max(b, 6) + 1)
+    const int cls_bits = std::max(b, 6) + 1;
+    const int exact = (flags & DOBFS_GRAPH_REINDEX_EXACT) ? 1 : 0;
+    k_vertex_keys<<<grid_for(n), kThreads, 0, s>>>(off0.as<int64_t>(), n, b, cls_bits, exact, vk.as<uint64_t>());
     DOBFS_CUDA_TRY(cudaGetLastError());
     uint64_t* vsorted = nullptr;
-    DOBFS_TRY(radix_sort_u64(vk.as<uint64_t>(), vt.as<uint64_t>(), n, 2 * b, s, &vsorted));
+    DOBFS_TRY(radix_sort_u64(vk.as<uint64_t>(), vt.as<uint64_t>(), n, b + cls_bits, s, &vsorted));
     DOBFS_TRY(g->new2orig.alloc(sizeof(int32_t) * (size_t)n, s));
     DOBFS_TRY(g->orig2new.alloc(sizeof(int32_t) * (size_t)n, s));
     k_maps<<<grid_for(n), kThreads, 0, s>>>(vsorted, n, b, g->new2orig.as<int32_t>(), g->orig2new.as<int32_t>());

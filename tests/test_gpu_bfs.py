@@ -70,26 +70,43 @@ def test_csr_build_matches_oracle_no_reindex(d, scale):
     np.testing.assert_array_equal(g.degrees(), deg)
 
 
-@pytest.mark.parametrize("scale,flags", [(11, 0), (14, 0x10)])
-def test_csr_build_reindex(d, scale, flags):
+def _degree_class(deg, exact):
+    """Renumbering class, written out from the definition in include/dobfs.h."""
+    if exact:
+        return deg.astype(np.int64)
+    out = np.empty(len(deg), dtype=np.int64)
+    for i, d in enumerate(deg.tolist()):
+        if d >= 4096:
+            out[i] = 64 + d
+        elif d < 8:
+            out[i] = d
+        else:
+            e = d.bit_length() - 1
+            out[i] = 8 + 4 * (e - 3) + ((d >> (e - 2)) & 3)
+    return out
+
+
+@pytest.mark.parametrize("scale,flags,exact", [(11, 0x20, True), (14, 0x10 | 0x20, True), (11, 0x2, False),
+                                               (14, 0x10 | 0x2, False)])
+def test_csr_build_reindex(d, scale, flags, exact):
     spec = inputs.rmat(scale)
     og = oracle.csr_from_rmat(spec)
-    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | flags)
+    g = d.rmat_graph(spec, flags=flags)
     off, cols, n2o = g.export()
     deg = og.degrees()
+    cls = _degree_class(deg, exact)
     ids = np.arange(og.n)
-    # new ID = rank by (degree descending, original ID ascending)
-    np.testing.assert_array_equal(n2o, np.lexsort((ids, -deg)).astype(np.int32))
-    o2n = np.empty_like(n2o)
-    o2n[n2o] = np.arange(og.n, dtype=np.int32)
+    # new ID = rank by (degree class descending, original ID ascending)
+    np.testing.assert_array_equal(n2o, np.lexsort((ids, -cls)).astype(np.int32))
     for i in range(og.n):
         row = cols[off[i]:off[i + 1]]
         assert np.all(np.diff(row) > 0)                         # sorted by new ID
         np.testing.assert_array_equal(np.sort(n2o[row]), og.row(int(n2o[i])))
-        if len(row) > 1:                                        # highest-degree neighbour first
-            assert np.all(np.diff(deg[n2o[row]]) <= 0)
-    assert g.info.offsets_int64 == (1 if flags else 0)
+        if len(row) > 1:                                        # highest-class neighbour first
+            assert np.all(np.diff(cls[n2o[row]]) <= 0)
+    assert g.info.offsets_int64 == (1 if flags & 0x10 else 0)
     np.testing.assert_array_equal(g.degrees(), deg)
+    assert g.info.reindexed == 1
 
 
 def test_pairs_and_csr_inputs(d):
@@ -169,6 +186,15 @@ def test_levels_bit_exact_s16_reindex_off64(d, s16, name, mode, seed):
     for i, r in enumerate(roots[:6]):
         lv, pa, st = _run(d, g, int(r), mode, seed)
         _check_run(og, int(r), lv, pa, ref_l[i])
+
+
+def test_levels_bit_exact_s16_exact_reindex(d, s16):
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX_EXACT)
+    for i, r in enumerate(roots[:6]):
+        for mode in (0, 2):
+            lv, pa, _ = _run(d, g, int(r), mode)
+            _check_run(og, int(r), lv, pa, ref_l[i])
 
 
 def test_canonical_parent_bit_exact(d, s16):
