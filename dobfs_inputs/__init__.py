@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -54,7 +54,7 @@ def _load():
             f.restype = None
             f.argtypes = [ctypes.c_int, u32, u32, u32, u64, u64, i64, i32p, i32p]
         lib.gen_c_chunglu_pairs.restype = None
-        lib.gen_c_chunglu_pairs.argtypes = [ctypes.POINTER(ctypes.c_uint64), u32, u64, u64, i64, i32p, i32p]
+        lib.gen_c_chunglu_pairs.argtypes = [ctypes.POINTER(ctypes.c_uint64), u32, u64, u64, i64, i32p, i32p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -190,7 +190,8 @@ def chunglu_cdf(spec: ChungLuSpec) -> np.ndarray:
     return np.cumsum(wi, dtype=np.uint64)
 
 
-def chunglu_pairs(spec: ChungLuSpec, cdf: np.ndarray | None = None, k0: int = 0, count: int | None = None):
+def chunglu_pairs(spec: ChungLuSpec, cdf: np.ndarray | None = None, k0: int = 0, count: int | None = None,
+                  plain_search: bool = False):
     lib = _load()
     if cdf is None:
         cdf = chunglu_cdf(spec)
@@ -200,7 +201,7 @@ def chunglu_pairs(spec: ChungLuSpec, cdf: np.ndarray | None = None, k0: int = 0,
     src = np.empty(count, dtype=np.int32)
     dst = np.empty(count, dtype=np.int32)
     lib.gen_c_chunglu_pairs(cdf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), spec.n_vertices,
-                            spec.seed, k0, count, _i32p(src), _i32p(dst))
+                            spec.seed, k0, count, _i32p(src), _i32p(dst), 1 if plain_search else 0)
     return src, dst
 
 

@@ -254,115 +254,162 @@ int64_t oracle_teps_edges(int64_t n, const int64_t* off, const int32_t* level) {
   return s / 2;
 }
 
+/* Source of the undirected pairs of a streamed graph: regenerated R-MAT
+ * pairs (gen.h), or pairs held in two arrays. */
+typedef struct {
+  int kind; /* 0: R-MAT stream, 1: arrays */
+  int scale;
+  uint32_t t_a, t_ab, t_abc;
+  uint64_t kp, kq;
+  const int32_t* src;
+  const int32_t* dst;
+} pair_source;
+
+static inline void get_pair(const pair_source* ps, int64_t i, uint32_t* u, uint32_t* v) {
+  if (ps->kind == 0) {
+    gen_rmat_pair((uint64_t)i, ps->scale, ps->t_a, ps->t_ab, ps->t_abc, ps->kp, ps->kq, u, v);
+  } else {
+    *u = (uint32_t)ps->src[i];
+    *v = (uint32_t)ps->dst[i];
+  }
+}
+
+static void note_violation(int32_t* rule_out, int64_t* bad_out, int32_t rule, int64_t where) {
+#pragma omp critical
+  {
+    if (*rule_out == 0 || where < *bad_out) {
+      *rule_out = rule;
+      *bad_out = where;
+    }
+  }
+}
+
+static void atomic_min_i32(int32_t* p, int32_t x) {
+  int32_t cur = __atomic_load_n(p, __ATOMIC_RELAXED);
+  while ((cur == -1 || x < cur) && !__atomic_compare_exchange_n(p, &cur, x, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+  }
+}
+
 /*
- * Streaming check of a BFS on the R-MAT graph of gen.h without building its
- * CSR: the pairs are regenerated, and for every pair u != v (stored both
- * ways in the graph) the edge rules 3 and 4 of oracle_check_bfs are checked;
- * a pair also confirms parent[v] == u (or parent[u] == v) as an edge. After
- * the pass every reached v != root must have a neighbour one level up
- * (rule 10) and a confirmed parent one level up, and canon[v] receives
- * min{u in N(v) : level[u] = level[v] - 1} (canon may be NULL). has_nbr
- * (may be NULL) receives 1 for every vertex with at least one neighbour.
- * Returns 0 or the rule number as above, with *bad the vertex; rule 9 =
- * the parent is not a neighbour. Rule 8 needs no union-find here: rule 4
- * makes the reached set closed under edges and rule 10 connects every
- * reached vertex to the root.
+ * Streaming check of R BFS results (roots[r], level[r*n ..], parent[r*n ..])
+ * on a graph given only by its pair stream, without building a CSR. For
+ * every pair u != v (stored both ways in the graph) the edge rules 3 and 4
+ * of oracle_check_bfs are checked; a pair also confirms parent[v] == u (or
+ * parent[u] == v) as an edge and marks a neighbour one level up. After the
+ * pass every reached v != root must have a neighbour one level up (rule 10)
+ * and a confirmed parent one level up, and canon[r*n + v] receives
+ * min{u in N(v) : level[u] = level[v] - 1} (canon may be NULL). has_nbr (may
+ * be NULL) receives 1 for every vertex with at least one neighbour.
+ * rc[r] receives 0 or the rule number as above, with bad[r] the vertex;
+ * rule 9 = the parent is not a neighbour. Rule 8 needs no union-find here:
+ * rule 4 makes the reached set closed under edges and rule 10 connects every
+ * reached vertex to the root. Returns the number of failed roots.
  */
-int32_t oracle_check_bfs_rmat_stream(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
-                                     uint64_t seed, int32_t root, const int32_t* level,
-                                     const int32_t* parent, int32_t* canon, uint8_t* has_nbr,
-                                     int32_t n_threads, int64_t* bad) {
-  const int64_t n = (int64_t)1 << scale;
-  const uint64_t kp = gen_key_pairs(seed), kq = gen_key_perm(seed);
-  uint8_t* confirmed = (uint8_t*)calloc((size_t)n, 1);
-  uint8_t* up = (uint8_t*)calloc((size_t)n, 1);
+static int32_t check_stream_core(const pair_source* ps, int64_t n, int64_t m, int32_t R, const int32_t* roots,
+                                 const int32_t* level, const int32_t* parent, int32_t* canon, uint8_t* has_nbr,
+                                 int32_t n_threads, int32_t* rc, int64_t* bad) {
+  uint8_t* confirmed = (uint8_t*)calloc((size_t)(n * R), 1);
+  uint8_t* up = (uint8_t*)calloc((size_t)(n * R), 1);
   if (canon)
-    for (int64_t v = 0; v < n; ++v) canon[v] = -1;
+    for (int64_t i = 0; i < n * R; ++i) canon[i] = -1;
   if (has_nbr) memset(has_nbr, 0, (size_t)n);
-  int64_t first_bad = -1;
-  int32_t first_rule = 0;
-  *bad = root;
-  if (root < 0 || root >= n || level[root] != 0 || (parent && parent[root] != root)) {
-    free(confirmed);
-    free(up);
-    return (root < 0 || root >= n || level[root] != 0) ? 1 : 2;
+  for (int32_t r = 0; r < R; ++r) {
+    const int32_t root = roots[r];
+    const int32_t* lv = level + (int64_t)r * n;
+    const int32_t* pa = parent ? parent + (int64_t)r * n : NULL;
+    rc[r] = 0;
+    bad[r] = root;
+    if (root < 0 || root >= n || lv[root] != 0) rc[r] = 1;
+    else if (pa && pa[root] != root) rc[r] = 2;
   }
 #pragma omp parallel for schedule(static, 1 << 16) num_threads(n_threads > 0 ? n_threads : 1)
   for (int64_t i = 0; i < m; ++i) {
     uint32_t a, b;
-    gen_rmat_pair((uint64_t)i, scale, t_a, t_ab, t_abc, kp, kq, &a, &b);
+    get_pair(ps, i, &a, &b);
     if (a == b) continue;
     const int32_t u = (int32_t)a, v = (int32_t)b;
     if (has_nbr) {
       has_nbr[u] = 1;
       has_nbr[v] = 1;
     }
-    const int32_t lu = level[u], lv = level[v];
-    int32_t rule = 0;
-    int64_t where = -1;
-    if ((lu >= 0) != (lv >= 0)) {
-      rule = 4;
-      where = lu >= 0 ? u : v;
-    } else if (lu >= 0 && (lu - lv > 1 || lv - lu > 1)) {
-      rule = 3;
-      where = u;
-    }
-    if (rule) {
-#pragma omp critical
-      {
-        if (first_rule == 0 || where < first_bad) {
-          first_rule = rule;
-          first_bad = where;
-        }
+    for (int32_t r = 0; r < R; ++r) {
+      if (rc[r] == 1 || rc[r] == 2) continue;
+      const int64_t o = (int64_t)r * n;
+      const int32_t lu = level[o + u], lv = level[o + v];
+      if ((lu >= 0) != (lv >= 0)) {
+        note_violation(&rc[r], &bad[r], 4, lu >= 0 ? u : v);
+        continue;
       }
-      continue;
-    }
-    if (lu < 0) continue;
-    if (lu == lv - 1) __atomic_store_n(&up[v], 1, __ATOMIC_RELAXED);
-    if (lv == lu - 1) __atomic_store_n(&up[u], 1, __ATOMIC_RELAXED);
-    if (parent) {
-      if (parent[v] == u) __atomic_store_n(&confirmed[v], 1, __ATOMIC_RELAXED);
-      if (parent[u] == v) __atomic_store_n(&confirmed[u], 1, __ATOMIC_RELAXED);
-    }
-    if (canon) {
-      if (lu == lv - 1) {
-        int32_t cur = __atomic_load_n(&canon[v], __ATOMIC_RELAXED);
-        while ((cur == -1 || u < cur) &&
-               !__atomic_compare_exchange_n(&canon[v], &cur, u, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
-        }
+      if (lu < 0) continue;
+      if (lu - lv > 1 || lv - lu > 1) {
+        note_violation(&rc[r], &bad[r], 3, u);
+        continue;
       }
-      if (lv == lu - 1) {
-        int32_t cur = __atomic_load_n(&canon[u], __ATOMIC_RELAXED);
-        while ((cur == -1 || v < cur) &&
-               !__atomic_compare_exchange_n(&canon[u], &cur, v, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
-        }
+      if (lu == lv - 1) __atomic_store_n(&up[o + v], 1, __ATOMIC_RELAXED);
+      if (lv == lu - 1) __atomic_store_n(&up[o + u], 1, __ATOMIC_RELAXED);
+      if (parent) {
+        if (parent[o + v] == u) __atomic_store_n(&confirmed[o + v], 1, __ATOMIC_RELAXED);
+        if (parent[o + u] == v) __atomic_store_n(&confirmed[o + u], 1, __ATOMIC_RELAXED);
+      }
+      if (canon) {
+        if (lu == lv - 1) atomic_min_i32(&canon[o + v], u);
+        if (lv == lu - 1) atomic_min_i32(&canon[o + u], v);
       }
     }
   }
-  if (first_rule) {
-    *bad = first_bad;
-    free(confirmed);
-    free(up);
-    return first_rule;
-  }
-  int32_t rc = 0;
-  for (int64_t v = 0; v < n && !rc; ++v) {
-    *bad = v;
-    if (level[v] < -1) rc = 7;
-    else if (level[v] == -1) {
-      if (parent && parent[v] != -1) rc = 7;
-    } else if (v != root) {
-      if (!up[v]) rc = 10;
-      else if (parent) {
-        const int32_t p = parent[v];
-        if (p < 0 || p >= n) rc = 5;
-        else if (!confirmed[v]) rc = 9;
-        else if (level[p] != level[v] - 1) rc = 6;
+  int32_t failed = 0;
+  for (int32_t r = 0; r < R; ++r) {
+    const int64_t o = (int64_t)r * n;
+    const int32_t root = roots[r];
+    for (int64_t v = 0; v < n && !rc[r]; ++v) {
+      const int32_t lvv = level[o + v];
+      if (lvv < -1) rc[r] = 7;
+      else if (lvv == -1) {
+        if (parent && parent[o + v] != -1) rc[r] = 7;
+      } else if (v != root) {
+        if (!up[o + v]) rc[r] = 10;
+        else if (parent) {
+          const int32_t p = parent[o + v];
+          if (p < 0 || p >= n) rc[r] = 5;
+          else if (!confirmed[o + v]) rc[r] = 9;
+          else if (level[o + p] != lvv - 1) rc[r] = 6;
+        }
       }
+      if (rc[r]) bad[r] = v;
     }
+    if (canon && !rc[r]) canon[o + root] = root;
+    failed += rc[r] ? 1 : 0;
   }
-  if (canon && !rc) canon[root] = root;
   free(confirmed);
   free(up);
+  return failed;
+}
+
+/* Streaming check of one BFS on the R-MAT graph of gen.h (see check_stream_core). */
+int32_t oracle_check_bfs_rmat_stream(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
+                                     uint64_t seed, int32_t root, const int32_t* level,
+                                     const int32_t* parent, int32_t* canon, uint8_t* has_nbr,
+                                     int32_t n_threads, int64_t* bad) {
+  const pair_source ps = {0, scale, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed), NULL, NULL};
+  int32_t rc = 0;
+  check_stream_core(&ps, (int64_t)1 << scale, m, 1, &root, level, parent, canon, has_nbr, n_threads, &rc, bad);
   return rc;
+}
+
+/* Streaming check of R BFS results on the R-MAT graph of gen.h. */
+int32_t oracle_check_bfs_rmat_stream_multi(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
+                                           uint64_t seed, int32_t R, const int32_t* roots, const int32_t* level,
+                                           const int32_t* parent, int32_t* canon, int32_t n_threads, int32_t* rc,
+                                           int64_t* bad) {
+  const pair_source ps = {0, scale, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed), NULL, NULL};
+  return check_stream_core(&ps, (int64_t)1 << scale, m, R, roots, level, parent, canon, NULL, n_threads, rc, bad);
+}
+
+/* Streaming check of R BFS results on the graph of m pairs held in src/dst. */
+int32_t oracle_check_bfs_pairs_multi(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int32_t R,
+                                     const int32_t* roots, const int32_t* level, const int32_t* parent,
+                                     int32_t* canon, uint8_t* has_nbr, int32_t n_threads, int32_t* rc,
+                                     int64_t* bad) {
+  const pair_source ps = {1, 0, 0, 0, 0, 0, 0, src, dst};
+  return check_stream_core(&ps, n, m, R, roots, level, parent, canon, has_nbr, n_threads, rc, bad);
 }

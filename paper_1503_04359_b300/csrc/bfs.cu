@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // deferred list. Found vertices are collected per word in shared memory and
 // every lane writes its own next-frontier and visited word: no global atomics.
 template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_bu(BfsArgs<OffT> A) {
+__global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ uint32_t s_found[kThreads / 32][32];
   const BfsCtl* c = A.ctl;
@@ -432,48 +432,64 @@ __global__ void __launch_bounds__(kThreads) k_bu(BfsArgs<OffT> A) {
     s_found[wid][lane] = 0u;
     __syncwarp();
     sc += cnt;
-    for (unsigned base = 0; base < total; base += 32) {
-      const unsigned k = base + lane;
-      // word j holding candidate k: the first lane whose inclusive count exceeds k
-      unsigned j = 0;
+    for (unsigned base = 0; base < total; base += 64) {
+      // two candidates per lane per round: their load chains overlap
+      unsigned jj[2], bb[2];
+      int32_t vv[2];
+      bool act[2];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const unsigned probe = __shfl_sync(0xffffffffu, incl, j + step - 1);
-        if (probe <= k) j += step;
-      }
-      const uint32_t cw = __shfl_sync(0xffffffffu, cand, j);
-      const unsigned ex_j = __shfl_sync(0xffffffffu, incl - cnt, j);
-      if (k >= total) continue;
-      const unsigned bit = __fns(cw, 0, (int)(k - ex_j) + 1);
-      const int32_t v = (int32_t)((grp * 32 + j) * 32 + bit);
-      const int2 fd = __ldg(A.firstdeg + v);
-      int32_t parent = -1;
-      unsigned long long exv = 1;
-      if (test_bit(front, fd.x)) {
-        parent = fd.x;
-      } else if (fd.y > 1) {
-        const int64_t s0 = (int64_t)A.off[v];
-        const int64_t lim = s0 + min(fd.y, kBuT);
-        for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
-          int32_t u[4];
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const unsigned k = base + 32 * c2 + lane;
+        // word j holding candidate k: the first lane whose inclusive count exceeds k
+        unsigned j = 0;
 #pragma unroll
-          for (int t = 0; t < 4; ++t) u[t] = (p + t < lim) ? A.cols[p + t] : -1;
-          bool h[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
-#pragma unroll
-          for (int t = 3; t >= 0; --t)
-            if (h[t]) parent = u[t];
-          exv += (unsigned long long)min((int64_t)4, lim - p);
+        for (int step = 16; step > 0; step >>= 1) {
+          const unsigned probe = __shfl_sync(0xffffffffu, incl, j + step - 1);
+          if (probe <= k) j += step;
         }
-        if (parent < 0 && fd.y > kBuT) enqueue(&A.ctl->n_def, A.def, v);
+        const uint32_t cw = __shfl_sync(0xffffffffu, cand, j);
+        const unsigned ex_j = __shfl_sync(0xffffffffu, incl - cnt, j);
+        act[c2] = k < total;
+        jj[c2] = j;
+        bb[c2] = act[c2] ? __fns(cw, 0, (int)(k - ex_j) + 1) : 0u;
+        vv[c2] = (int32_t)((grp * 32 + j) * 32 + bb[c2]);
       }
-      ex += exv;
-      if (parent >= 0) {
-        atomicOr(&s_found[wid][j], 1u << bit);
-        A.lp[v] = make_int2(L + 1, parent);
-        n_new += 1;
-        m_new += (unsigned long long)fd.y;
+      int2 fd[2];
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) fd[c2] = act[c2] ? __ldg(A.firstdeg + vv[c2]) : make_int2(0, 0);
+      bool hit0[2];
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) hit0[c2] = act[c2] && test_bit(front, fd[c2].x);
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) {
+        if (!act[c2]) continue;
+        const int32_t v = vv[c2];
+        int32_t parent = hit0[c2] ? fd[c2].x : -1;
+        unsigned long long exv = 1;
+        if (!hit0[c2] && fd[c2].y > 1) {
+          const int64_t s0 = (int64_t)A.off[v];
+          const int64_t lim = s0 + min(fd[c2].y, kBuT);
+          for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
+            int32_t u[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) u[t] = (p + t < lim) ? A.cols[p + t] : -1;
+            bool h[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
+#pragma unroll
+            for (int t = 3; t >= 0; --t)
+              if (h[t]) parent = u[t];
+            exv += (unsigned long long)min((int64_t)4, lim - p);
+          }
+          if (parent < 0 && fd[c2].y > kBuT) enqueue(&A.ctl->n_def, A.def, v);
+        }
+        ex += exv;
+        if (parent >= 0) {
+          atomicOr(&s_found[wid][jj[c2]], 1u << bb[c2]);
+          A.lp[v] = make_int2(L + 1, parent);
+          n_new += 1;
+          m_new += (unsigned long long)fd[c2].y;
+        }
       }
     }
     __syncwarp();
@@ -559,54 +575,80 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
 // isolated: unreached unless they are the root, so only the root among them
 // needs the visited bit and the (level, parent) gather.
 template <class OffT>
-__device__ __forceinline__ void output_one(const BfsArgs<OffT>& A, const int32_t* __restrict__ n2o, int32_t v,
-                                           int32_t root, int32_t& lev, int32_t& par) {
-  lev = -1;
-  par = -1;
-  if (A.o2n && v >= A.n_nonisolated && v != root) return;
-  if ((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u) {
-    const int2 x = A.lp[v];
-    lev = x.x;
-    par = n2o ? __ldg(n2o + x.y) : x.y;
-  }
-}
-
-template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
                                                      int32_t root_orig, int32_t* __restrict__ level_out,
                                                      int32_t* __restrict__ parent_out) {
+  constexpr int kQ = 2;  // quads per thread and step: eight independent gathers in flight
   const int32_t root = A.o2n ? __ldg(A.o2n + root_orig) : root_orig;
   const int64_t quads = A.n >> 2;
   const bool vec = ((reinterpret_cast<uintptr_t>(level_out) | reinterpret_cast<uintptr_t>(parent_out)) & 15) == 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t q = tid; q < quads; q += stride) {
-    const int64_t o = q * 4;
-    int32_t v[4];
-    if (A.o2n) {
-      const int4 m = __ldg(reinterpret_cast<const int4*>(A.o2n) + q);
-      v[0] = m.x; v[1] = m.y; v[2] = m.z; v[3] = m.w;
-    } else {
-      v[0] = (int32_t)o; v[1] = (int32_t)o + 1; v[2] = (int32_t)o + 2; v[3] = (int32_t)o + 3;
-    }
-    int32_t lev[4], par[4];
+  for (int64_t q0 = tid; q0 < quads; q0 += stride * kQ) {
+    int32_t v[kQ][4];
+    bool inq[kQ];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) output_one(A, n2o, v[t], root, lev[t], par[t]);
-    if (vec) {
-      reinterpret_cast<int4*>(level_out)[q] = make_int4(lev[0], lev[1], lev[2], lev[3]);
-      if (parent_out) reinterpret_cast<int4*>(parent_out)[q] = make_int4(par[0], par[1], par[2], par[3]);
-    } else {
+    for (int a = 0; a < kQ; ++a) {
+      const int64_t q = q0 + a * stride;
+      inq[a] = q < quads;
+      if (A.o2n) {
+        const int4 m = inq[a] ? __ldg(reinterpret_cast<const int4*>(A.o2n) + q) : make_int4(0, 0, 0, 0);
+        v[a][0] = m.x; v[a][1] = m.y; v[a][2] = m.z; v[a][3] = m.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[a][t] = (int32_t)(q * 4 + t);
+      }
+    }
+    // a vertex renumbered past the last one with an edge is isolated: only
+    // the root among them can be reached
+    bool need[kQ][4];
+    uint32_t vw[kQ][4];
+    int2 x[kQ][4];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a)
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        level_out[o + t] = lev[t];
-        if (parent_out) parent_out[o + t] = par[t];
+        const int32_t vt = v[a][t];
+        need[a][t] = inq[a] && (!A.o2n || vt < A.n_nonisolated || vt == root);
+        // the visited word and the (level, parent) pair are loaded together;
+        // the pair is used only if the vertex was visited
+        vw[a][t] = need[a][t] ? __ldg(A.visited + (vt >> 5)) : 0u;
+        x[a][t] = need[a][t] ? A.lp[vt] : make_int2(-1, -1);
+      }
+    int32_t lev[kQ][4], par[kQ][4];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const bool vis = (vw[a][t] >> (v[a][t] & 31)) & 1u;
+        lev[a][t] = vis ? x[a][t].x : -1;
+        par[a][t] = vis ? (n2o ? __ldg(n2o + x[a][t].y) : x[a][t].y) : -1;
+      }
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+      if (!inq[a]) continue;
+      const int64_t q = q0 + a * stride;
+      if (vec) {
+        reinterpret_cast<int4*>(level_out)[q] = make_int4(lev[a][0], lev[a][1], lev[a][2], lev[a][3]);
+        if (parent_out)
+          reinterpret_cast<int4*>(parent_out)[q] = make_int4(par[a][0], par[a][1], par[a][2], par[a][3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          level_out[q * 4 + t] = lev[a][t];
+          if (parent_out) parent_out[q * 4 + t] = par[a][t];
+        }
       }
     }
   }
   for (int64_t o = quads * 4 + tid; o < A.n; o += stride) {  // ragged tail
-    const int32_t v = A.o2n ? __ldg(A.o2n + o) : (int32_t)o;
-    int32_t lev, par;
-    output_one(A, n2o, v, root, lev, par);
+    const int32_t vt = A.o2n ? __ldg(A.o2n + o) : (int32_t)o;
+    int32_t lev = -1, par = -1;
+    if ((__ldg(A.visited + (vt >> 5)) >> (vt & 31)) & 1u) {
+      const int2 y = A.lp[vt];
+      lev = y.x;
+      par = n2o ? __ldg(n2o + y.y) : y.y;
+    }
     level_out[o] = lev;
     if (parent_out) parent_out[o] = par;
   }
@@ -682,13 +724,28 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
 struct Grids {
   int td_bin, td_chunks, conv, bu, bu_long;
 };
+// One full wave of resident blocks per kernel: the grid-stride loops then
+// run every block to the end of the work without a second, partial wave.
+template <class K>
+int resident_grid(K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 4;
+  }
+  return grid_cap(per_sm);
+}
+
+template <class OffT>
 Grids grids() {
-  Grids G;
-  G.td_bin = grid_cap(8);
-  G.td_chunks = grid_cap(8);
-  G.conv = grid_cap(8);
-  G.bu = grid_cap(8);
-  G.bu_long = grid_cap(8);
+  static Grids G = {0, 0, 0, 0, 0};
+  if (G.bu == 0) {
+    G.td_bin = resident_grid(k_td_bin<OffT>);
+    G.td_chunks = resident_grid(k_td_chunks<OffT>);
+    G.conv = resident_grid(k_bitmap_to_queue<OffT>);
+    G.bu = resident_grid(k_bu<OffT>);
+    G.bu_long = resident_grid(k_bu_long<OffT>);
+  }
   return G;
 }
 
@@ -697,7 +754,7 @@ Grids grids() {
 template <class OffT>
 int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t main_begin,
                 cudaEvent_t main_end) {
-  const Grids G = grids();
+  const Grids G = grids<OffT>();
   const size_t bm_bytes = sizeof(uint32_t) * (size_t)g->words;
   switch (kase) {
     case 0:

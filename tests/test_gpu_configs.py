@@ -1,0 +1,112 @@
+"""GPU parity at the full sizes of the benchmark workloads.
+
+- R-MAT scale 22 (int64 offsets, renumbered), 64 seeded roots: levels
+  bit-exact with the oracle's serial BFS on its own CSR, parents valid,
+  canonical parents bit-exact.
+- R-MAT scale 28 and Chung-Lu 2^26: the oracle cannot hold a CSR within the
+  test's time, so the GPU results are checked by the streaming invariant
+  checker over the regenerated (R-MAT) or host-generated (Chung-Lu) pairs.
+  The invariants characterise BFS levels exactly (level = distance), and the
+  checker computes the canonical parent by its definition, compared
+  bit-exact. Roots here are endpoints of seeded pairs of the input stream
+  (degree >= 1 by construction, degree-biased), so no root comes from the
+  CUDA path.
+"""
+import numpy as np
+import pytest
+
+import dobfs_inputs as inputs
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def d():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_04359_b300 import build, dobfs
+    build.build()
+    dobfs.load()
+    dobfs.use_torch_allocator()
+    return dobfs
+
+
+def _gpu_runs(d, g, roots, flags=0):
+    n = g.n
+    lv = np.empty((len(roots), n), dtype=np.int32)
+    pa = np.empty((len(roots), n), dtype=np.int32)
+    l_dev = torch.empty(n, dtype=torch.int32, device="cuda")
+    p_dev = torch.empty(n, dtype=torch.int32, device="cuda")
+    for i, r in enumerate(roots):
+        g.run(int(r), l_dev, p_dev, d.make_opts(flags=flags))
+        torch.cuda.synchronize()
+        lv[i] = l_dev.cpu().numpy()
+        pa[i] = p_dev.cpu().numpy()
+    return lv, pa
+
+
+def _pair_roots(src, dst, seed, count):
+    """Endpoints of seeded pairs that are not self-loops."""
+    out, j = [], 0
+    while len(out) < count:
+        k = inputs.mix64(inputs.mix64(seed) ^ j) % len(src)
+        j += 1
+        if src[k] != dst[k] and int(src[k]) not in out:
+            out.append(int(src[k]))
+    return np.asarray(out, dtype=np.int32)
+
+
+def test_config2_rmat22_64_roots(d):
+    spec = inputs.rmat(22)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 64, og.degrees() > 0)
+    ref_l, ref_p = oracle.bfs_many(og, roots)
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64)
+    assert g.info.offsets_int64 == 1 and g.info.n_entries == og.nnz
+    lv, pa = _gpu_runs(d, g, roots)
+    np.testing.assert_array_equal(lv, ref_l)
+    for i in range(0, 64, 8):
+        rule, bad = oracle.check_bfs(og, int(roots[i]), lv[i], pa[i])
+        assert rule == 0, (i, oracle.RULES[rule], bad)
+    lv_c, pa_c = _gpu_runs(d, g, roots[:8], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    np.testing.assert_array_equal(lv_c, ref_l[:8])
+    np.testing.assert_array_equal(pa_c, ref_p[:8])
+
+
+def test_config3a_rmat28_streaming_check(d):
+    spec = inputs.rmat(28)
+    src, dst = inputs.rmat_pairs(spec, count=1 << 20)
+    roots = _pair_roots(src, dst, inputs.root_seed(spec.seed), 4)
+    del src, dst
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    lv, pa = _gpu_runs(d, g, roots[:2])
+    lv_c, pa_c = _gpu_runs(d, g, roots[2:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    g.close()
+    torch.cuda.empty_cache()
+    levels = np.concatenate([lv, lv_c])
+    parents = np.concatenate([pa, pa_c])
+    del lv, pa, lv_c, pa_c
+    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, levels, parents, want_canon=True)
+    assert rc.tolist() == [0, 0, 0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
+    np.testing.assert_array_equal(parents[2:], canon[2:])
+    assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(4))
+
+
+def test_config3b_chunglu26_streaming_check(d):
+    spec = inputs.chunglu(26)
+    cdf = inputs.chunglu_cdf(spec)
+    g = d.chunglu_graph(spec, cdf)
+    src, dst = inputs.chunglu_pairs(spec, cdf)
+    roots = _pair_roots(src, dst, spec.seed ^ 0xB00F, 4)
+    lv, pa = _gpu_runs(d, g, roots[:2])
+    lv_c, pa_c = _gpu_runs(d, g, roots[2:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    g.close()
+    levels = np.concatenate([lv, lv_c])
+    parents = np.concatenate([pa, pa_c])
+    rc, bad, canon, _ = oracle.check_bfs_pairs_multi(spec.n_vertices, src, dst, roots, levels, parents,
+                                                     want_canon=True)
+    assert rc.tolist() == [0, 0, 0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
+    np.testing.assert_array_equal(parents[2:], canon[2:])
+    assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(4))

@@ -92,3 +92,12 @@ def test_sample_roots():
     np.testing.assert_array_equal(r, inputs.sample_roots(5, 1000, 50, deg > 0))
     with pytest.raises(ValueError):
         inputs.sample_roots(5, 10, 5, np.zeros(10, dtype=bool))
+
+
+def test_chunglu_bucketed_search_equals_plain_search():
+    spec = inputs.chunglu(16, max_weight=float(1 << 12))
+    cdf = inputs.chunglu_cdf(spec)
+    a = inputs.chunglu_pairs(spec, cdf, count=200_000)
+    b = inputs.chunglu_pairs(spec, cdf, count=200_000, plain_search=True)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])

@@ -292,3 +292,29 @@ def test_bfs_many_equals_single():
         l1, p1, _ = oracle.bfs(g, int(r))
         np.testing.assert_array_equal(lv[i], l1)
         np.testing.assert_array_equal(pa[i], p1)
+
+
+def test_stream_multi_equals_single_and_isolates_roots():
+    spec, g, root = _rmat_small()
+    roots = inputs.sample_roots(77, g.n, 3, g.degrees() > 0)
+    lv, pa = oracle.bfs_many(g, roots)
+    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, lv, pa, want_canon=True)
+    assert rc.tolist() == [0, 0, 0]
+    np.testing.assert_array_equal(canon, pa)
+    # a planted mistake in root 1 only fails root 1
+    lv2 = lv.copy()
+    v = int(np.flatnonzero(lv2[1] > 1)[0])
+    lv2[1, v] = -1
+    rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, roots, lv2, pa)
+    assert rc.tolist() == [0, 4, 0]
+    # the same check over the pairs held in arrays
+    src, dst = inputs.rmat_pairs(spec)
+    rc, bad, canon2, has_nbr = oracle.check_bfs_pairs_multi(g.n, src, dst, roots, lv, pa, want_canon=True,
+                                                            want_has_nbr=True)
+    assert rc.tolist() == [0, 0, 0]
+    np.testing.assert_array_equal(canon2, pa)
+    np.testing.assert_array_equal(has_nbr.astype(bool), g.degrees() > 0)
+    badp = pa.copy()
+    badp[2, int(np.flatnonzero(lv[2] > 0)[0])] = -5
+    rc, _, _, _ = oracle.check_bfs_pairs_multi(g.n, src, dst, roots, lv, badp)
+    assert rc.tolist() == [0, 0, 5]
