@@ -51,6 +51,7 @@ constexpr int kThreads = 256;
 constexpr int kTdSmall = 16;   // top-down rows up to this length: one thread
 constexpr int kChunk = 512;    // top-down chunk record length (entries)
 constexpr int kBuT = 32;       // bottom-up entries scanned per thread before deferring
+constexpr int kCases = 6;      // step kinds of the level loop's switch node
 constexpr int kCaseNone = 7;   // switch value with no body: loop ends
 
 template <class OffT>
@@ -121,9 +122,31 @@ __device__ __forceinline__ unsigned td_claim4(const BfsArgs<OffT>& A, const int3
   return won;
 }
 
+// Top-down marking without claims (bitmap-output top-down steps): a
+// neighbour not yet visited gets its bit in the next-frontier bitmap. The
+// visited bitmap is read-only during the marking, so it is read through the
+// read-only cache; a bit already set in the next bitmap needs no atomic.
+// Parents are recovered afterwards from the frontier bitmap (k_bu in
+// recovery mode).
+template <class OffT>
+__device__ __forceinline__ void td_mark4(const BfsArgs<OffT>& A, const int32_t (&v)[4], unsigned valid,
+                                         uint32_t* next) {
+  uint32_t w[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) w[t] = ((valid >> t) & 1u) ? __ldg(A.visited + (v[t] >> 5)) : ~0u;
+  uint32_t nw[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) nw[t] = ((w[t] >> (v[t] & 31)) & 1u) ? ~0u : __ldcg(next + (v[t] >> 5));
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const uint32_t bit = 1u << (v[t] & 31);
+    if (!(nw[t] & bit)) atomicOr(next + (v[t] >> 5), bit);
+  }
+}
+
 template <class OffT>
 __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t alpha, int32_t beta,
-                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed) {
+                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed, int32_t td_bm_div) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int32_t r = A.o2n ? A.o2n[root_orig] : root_orig;
   const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
@@ -154,6 +177,7 @@ __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t
   c->static_pct = static_pct;
   c->bu_steps = bu_steps;
   c->sched_seed = sched_seed;
+  c->td_bm_div = td_bm_div;
   A.q0[0] = r;
   A.visited[r >> 5] |= 1u << (r & 31);
   A.lp[r] = make_int2(0, r);
@@ -167,12 +191,14 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
   BfsCtl* c = A.ctl;
   if (!c->fresh) {
     const int32_t L = c->level;
-    const int64_t n_new = (c->dir == 0) ? (int64_t)c->q_tail : (int64_t)c->nx_n;
+    // top-down steps with queue output count their new vertices in the queue
+    const bool queue_out = (c->step_case == 0 || c->step_case == 2);
+    const int64_t n_new = queue_out ? (int64_t)c->q_tail : (int64_t)c->nx_n;
     const int64_t m_new = (int64_t)c->nx_m;
     const int64_t ex = (int64_t)c->nx_examined, sc = (int64_t)c->nx_scanned;
     int64_t bytes;
     if (c->dir == 0)  // queue read 4, row bounds 16, columns 4 each, level+parent 8 and enqueue 4 per new vertex
-      bytes = 20 * c->n_f + 4 * c->m_f + 12 * n_new + (c->step_case == 2 ? 4 * c->n_f : 0);
+      bytes = 20 * c->n_f + 4 * c->m_f + 12 * n_new + (c->step_case >= 2 ? 4 * c->n_f : 0);
     else  // row bounds 8 per scanned vertex, columns 4 each read, level+parent 8 per new vertex
       bytes = 8 * sc + 4 * ex + 8 * n_new + (c->step_case == 3 ? 4 * c->n_f : 0);
     if (L < kMaxTrace) {
@@ -197,7 +223,7 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
     c->n_f = n_new;
     c->m_f = m_new;
     c->level = L + 1;
-    c->fmt = c->dir;  // top-down leaves a queue, bottom-up a bitmap
+    c->fmt = queue_out ? 0 : 1;  // queue-output top-down leaves a queue, the other steps a bitmap
     c->bu_run = (c->dir == 1) ? c->bu_run + 1 : 0;
     c->nx_n = c->nx_m = c->nx_examined = c->nx_scanned = 0;
     c->q_tail = c->n_rec = c->n_def = c->conv_tail = 0;
@@ -234,7 +260,14 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
         dir = (c->n_f * (int64_t)c->beta < A.n && c->n_f < c->n_f_prev) ? 0 : 1;
       break;
   }
-  const int kase = (dir == 0) ? (c->fmt == 0 ? 0 : 2) : (c->fmt == 1 ? 1 : 3);
+  int kase;
+  if (dir == 0) {
+    // heavy top-down levels mark a bitmap and recover parents afterwards
+    const bool bm = c->td_bm_div > 0 && c->m_f * (int64_t)c->td_bm_div >= A.n;
+    kase = bm ? (c->fmt == 0 ? 4 : 5) : (c->fmt == 0 ? 0 : 2);
+  } else {
+    kase = (c->fmt == 1) ? 1 : 3;
+  }
   c->dir = dir;
   c->step_case = kase;
   if (in_graph) cudaGraphSetConditional(h_case, (unsigned)kase);
@@ -242,7 +275,7 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
 
 // Top-down, part 1: short rows expanded in place, long rows cut into
 // chunk records.
-template <class OffT>
+template <class OffT, bool BM>
 __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   const BfsCtl* c = A.ctl;
@@ -264,11 +297,15 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
           v[t] = (j + t < e) ? A.cols[j + t] : 0;
           if (j + t < e) valid |= 1u << t;
         }
-        unsigned won = td_claim4(A, v, valid, u, L + 1, m_new);
-        while (won) {
-          const int t = __ffs(won) - 1;
-          won &= won - 1;
-          enqueue(&A.ctl->q_tail, nxt, v[t]);
+        if (BM) {
+          td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
+        } else {
+          unsigned won = td_claim4(A, v, valid, u, L + 1, m_new);
+          while (won) {
+            const int t = __ffs(won) - 1;
+            won &= won - 1;
+            enqueue(&A.ctl->q_tail, nxt, v[t]);
+          }
         }
       }
     } else {
@@ -291,7 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
 }
 
 // Top-down, part 2: one warp per chunk record, 16-byte column loads.
-template <class OffT>
+template <class OffT, bool BM>
 __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   const BfsCtl* c = A.ctl;
@@ -321,6 +358,10 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
+      }
+      if (BM) {
+        if (valid) td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
+        continue;
       }
       const unsigned won = valid ? td_claim4(A, v, valid, u, L + 1, m_new) : 0u;
       const unsigned cnt = (unsigned)__popc(won);
@@ -403,7 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // first neighbour in the frontier; longer rows without a hit go to the
 // deferred list. Found vertices are collected per word in shared memory and
 // every lane writes its own next-frontier and visited word: no global atomics.
-template <class OffT>
+template <class OffT, bool RECOVER>
 __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ uint32_t s_found[kThreads / 32][32];
@@ -420,7 +461,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
     const int64_t w = grp * 32 + lane;
     const bool in = w < A.cand_words;
     const uint32_t vis = in ? A.visited[w] : ~0u;
-    const uint32_t cand = in ? ~(vis | A.iso[w]) : 0u;
+    // recovery: the candidates are the vertices the top-down marking found
+    const uint32_t cand = in ? (RECOVER ? next[w] : ~(vis | A.iso[w])) : 0u;
     const unsigned cnt = (unsigned)__popc(cand);
     unsigned incl = cnt;
 #pragma unroll
@@ -495,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
     __syncwarp();
     if (in) {
       const uint32_t f = s_found[wid][lane];
-      next[w] = f;
+      if (!RECOVER) next[w] = f;
       if (f) A.visited[w] = vis | f;
     }
     __syncwarp();
@@ -510,6 +552,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
     if (ex) atomicAdd(&A.ctl->nx_examined, ex);
     if (sc) atomicAdd(&A.ctl->nx_scanned, sc);
   }
+}
+
+// Clears the next-frontier bitmap of level L (bitmap-output top-down step
+// after a bottom-up level, when the current frontier bitmap must stay).
+template <class OffT>
+__global__ void k_clear_next(BfsArgs<OffT> A) {
+  const int32_t L = A.ctl->level;
+  uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < A.words; w += (int64_t)gridDim.x * blockDim.x)
+    next[w] = 0u;
 }
 
 // Bottom-up, part 2: rows with no frontier neighbour among their first kBuT
@@ -740,10 +792,10 @@ template <class OffT>
 Grids grids() {
   static Grids G = {0, 0, 0, 0, 0};
   if (G.bu == 0) {
-    G.td_bin = resident_grid(k_td_bin<OffT>);
-    G.td_chunks = resident_grid(k_td_chunks<OffT>);
+    G.td_bin = resident_grid(k_td_bin<OffT, false>);
+    G.td_chunks = resident_grid(k_td_chunks<OffT, false>);
     G.conv = resident_grid(k_bitmap_to_queue<OffT>);
-    G.bu = resident_grid(k_bu<OffT>);
+    G.bu = resident_grid(k_bu<OffT, false>);
     G.bu_long = resident_grid(k_bu_long<OffT>);
   }
   return G;
@@ -761,8 +813,8 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
     case 2:
       if (kase == 2) k_bitmap_to_queue<OffT><<<G.conv, kThreads, 0, s>>>(A);
       if (main_begin) cudaEventRecord(main_begin, s);
-      k_td_bin<OffT><<<G.td_bin, kThreads, 0, s>>>(A);
-      k_td_chunks<OffT><<<G.td_chunks, kThreads, 0, s>>>(A);
+      k_td_bin<OffT, false><<<G.td_bin, kThreads, 0, s>>>(A);
+      k_td_chunks<OffT, false><<<G.td_chunks, kThreads, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
       break;
     case 1:
@@ -773,7 +825,24 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
         k_queue_to_bitmap<OffT><<<G.conv, kThreads, 0, s>>>(A);
       }
       if (main_begin) cudaEventRecord(main_begin, s);
-      k_bu<OffT><<<G.bu, kThreads, 0, s>>>(A);
+      k_bu<OffT, false><<<G.bu, kThreads, 0, s>>>(A);
+      k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
+      if (main_end) cudaEventRecord(main_end, s);
+      break;
+    case 4:  // top-down with bitmap output, frontier held as a queue
+    case 5:  // the same after a bottom-up level (frontier held as a bitmap)
+      if (kase == 4) {
+        DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm0.ptr, 0, bm_bytes, s));
+        DOBFS_CUDA_TRY(cudaMemsetAsync(g->fbm1.ptr, 0, bm_bytes, s));
+        k_queue_to_bitmap<OffT><<<G.conv, kThreads, 0, s>>>(A);
+      } else {
+        k_bitmap_to_queue<OffT><<<G.conv, kThreads, 0, s>>>(A);
+        k_clear_next<OffT><<<G.conv, kThreads, 0, s>>>(A);
+      }
+      if (main_begin) cudaEventRecord(main_begin, s);
+      k_td_bin<OffT, true><<<G.td_bin, kThreads, 0, s>>>(A);
+      k_td_chunks<OffT, true><<<G.td_chunks, kThreads, 0, s>>>(A);
+      k_bu<OffT, true><<<G.bu, kThreads, 0, s>>>(A);
       k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
       break;
@@ -827,11 +896,11 @@ int build_level_graph(dobfs_graph* g) {
   sp.type = cudaGraphNodeTypeConditional;
   sp.conditional.handle = h_case;
   sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = 4;
+  sp.conditional.size = kCases;
   cudaGraphNode_t snode;
   if (cudaGraphAddNode(&snode, body, &heur, nullptr, 1, &sp) != cudaSuccess)
     return fail(set_error(DOBFS_ERR_CUDA, "switch node failed: %s", cudaGetErrorString(cudaGetLastError())));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kCases; ++k) {
     if (cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return fail(set_error(DOBFS_ERR_CUDA, "capture to case %d failed", k));
@@ -910,7 +979,8 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   }
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
-  k_init<OffT><<<1, 32, 0, s>>>(A, root, o.direction, o.alpha, o.beta, o.static_pct, o.bu_steps, o.schedule_seed);
+  k_init<OffT><<<1, 32, 0, s>>>(A, root, o.direction, o.alpha, o.beta, o.static_pct, o.bu_steps, o.schedule_seed,
+                                o.td_bitmap_div);
   DOBFS_CUDA_TRY(cudaGetLastError());
   if (host_loop_mode) {
     DOBFS_TRY(host_loop<OffT>(g, A, s));
@@ -1023,6 +1093,7 @@ int dobfs_run_opts_init(dobfs_run_opts* o) {
   o->flags = 0;
   o->schedule_seed = 0;
   o->stream = nullptr;
+  o->td_bitmap_div = 16;
   return DOBFS_OK;
 }
 
@@ -1036,7 +1107,7 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
   dobfs_run_opts_init(&o);
   if (opts) o = *opts;
   if (o.direction < 0 || o.direction > DOBFS_DIR_STATIC || o.alpha < 1 || o.beta < 1 || o.static_pct < 0 ||
-      o.bu_steps < 1)
+      o.bu_steps < 1 || o.td_bitmap_div < 0)
     return set_error(DOBFS_ERR_INVALID, "bad run options");
   std::lock_guard<std::mutex> lk(g->mu);
   return g->off64 ? run_impl<int64_t>(g, root, level_out, parent_out, o, stats)

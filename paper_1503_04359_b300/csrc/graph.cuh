@@ -18,7 +18,8 @@ struct BfsCtl {
   int32_t level;        // L: the frontier holds the vertices at level L
   int32_t dir;          // direction of the step expanding level L: 0 top-down, 1 bottom-up
   int32_t fmt;          // frontier of level L is held as 0: queue, 1: bitmap
-  int32_t step_case;    // 0 TD from queue, 1 BU from bitmap, 2 TD after bitmap->queue, 3 BU after queue->bitmap
+  int32_t step_case;    // 0 TD from queue, 1 BU from bitmap, 2 TD after bitmap->queue, 3 BU after queue->bitmap,
+                        // 4/5 TD with bitmap output (from queue / from bitmap)
   int32_t fresh;        // set by init: the loop has not run a step yet
   int32_t done;
   int32_t bu_run;       // consecutive bottom-up levels so far (static policy)
@@ -38,7 +39,7 @@ struct BfsCtl {
   int32_t overflow;     // top-down record buffer overflow (never expected)
   int32_t pad2;
   // parameters
-  int32_t mode, alpha, beta, static_pct, bu_steps, pad1;
+  int32_t mode, alpha, beta, static_pct, bu_steps, td_bm_div;
   uint64_t sched_seed;
 };
 

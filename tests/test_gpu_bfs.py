@@ -197,6 +197,22 @@ def test_levels_bit_exact_s16_exact_reindex(d, s16):
             _check_run(og, int(r), lv, pa, ref_l[i])
 
 
+@pytest.mark.parametrize("div", [0, 1 << 30])
+@pytest.mark.parametrize("mode,seed", [(0, 0), (1, 0), (3, 5), (3, 9)])
+def test_topdown_bitmap_output(d, s16, div, mode, seed):
+    """Top-down levels with bitmap output and parent recovery (div = 2^30 makes
+    every top-down level take it) against the queue form (div = 0)."""
+    spec, og, roots, ref_l, ref_p = s16
+    for flags in (0, d.DOBFS_GRAPH_REINDEX):
+        g = d.rmat_graph(spec, flags=flags)
+        for i, r in enumerate(roots[:4]):
+            lv, pa, st = _run(d, g, int(r), mode, seed, td_bitmap_div=div)
+            _check_run(og, int(r), lv, pa, ref_l[i])
+            assert st.teps_edges == oracle.teps_edges(og, ref_l[i])
+            lv, pa, _ = _run(d, g, int(r), mode, seed, flags=d.DOBFS_RUN_CANONICAL_PARENT, td_bitmap_div=div)
+            _check_run(og, int(r), lv, pa, ref_l[i], ref_p[i])
+
+
 def test_canonical_parent_bit_exact(d, s16):
     spec, og, roots, ref_l, ref_p = s16
     for flags in (0, d.DOBFS_GRAPH_REINDEX):
@@ -236,19 +252,20 @@ def _pairs_graph(d, n, pairs, flags=0):
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("flags", [0, 0x2])
-def test_closed_forms(d, mode, flags):
+@pytest.mark.parametrize("div", [16, 1 << 30])
+def test_closed_forms(d, mode, flags, div):
     n = 2000  # path: 2000 levels
     g, og = _pairs_graph(d, n, [(i, i + 1) for i in range(n - 1)], flags)
-    lv, pa, st = _run(d, g, 0, mode, seed=5)
+    lv, pa, st = _run(d, g, 0, mode, seed=5, td_bitmap_div=div)
     assert lv.tolist() == list(range(n)) and st.levels == n
-    lv, pa, _ = _run(d, g, 700, mode, seed=5)
+    lv, pa, _ = _run(d, g, 700, mode, seed=5, td_bitmap_div=div)
     assert lv.tolist() == [abs(i - 700) for i in range(n)]
     # star with 5000 leaves: one long row (chunked top-down, deferred bottom-up)
     n = 5001
     g, og = _pairs_graph(d, n, [(0, i) for i in range(1, n)], flags)
-    lv, pa, _ = _run(d, g, 0, mode, seed=5)
+    lv, pa, _ = _run(d, g, 0, mode, seed=5, td_bitmap_div=div)
     assert lv.tolist() == [0] + [1] * (n - 1) and np.all(pa[1:] == 0)
-    lv, pa, _ = _run(d, g, 4321, mode, seed=5)
+    lv, pa, _ = _run(d, g, 4321, mode, seed=5, td_bitmap_div=div)
     assert lv[0] == 1 and lv[4321] == 0 and int((lv == 2).sum()) == n - 2
     _check_run(og, 4321, lv, pa, oracle.bfs(og, 4321)[0])
     # binary tree in heap order, plus a separate cycle and an isolated vertex
@@ -256,11 +273,11 @@ def test_closed_forms(d, mode, flags):
     pairs = [((i - 1) // 2, i) for i in range(1, t)] + [(t + i, t + (i + 1) % 50) for i in range(50)]
     n = t + 51
     g, og = _pairs_graph(d, n, pairs, flags)
-    lv, pa, _ = _run(d, g, 0, mode, seed=5, flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    lv, pa, _ = _run(d, g, 0, mode, seed=5, flags=d.DOBFS_RUN_CANONICAL_PARENT, td_bitmap_div=div)
     assert lv[:t].tolist() == [int(np.floor(np.log2(i + 1))) for i in range(t)]
     assert np.all(lv[t:] == -1) and np.all(pa[t:] == -1)
     assert pa[:t].tolist() == [0] + [(i - 1) // 2 for i in range(1, t)]
-    lv, pa, st = _run(d, g, n - 1, mode, seed=5)  # isolated root
+    lv, pa, st = _run(d, g, n - 1, mode, seed=5, td_bitmap_div=div)  # isolated root
     assert lv.tolist() == [-1] * (n - 1) + [0] and pa[n - 1] == n - 1 and st.teps_edges == 0
 
 
