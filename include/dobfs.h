@@ -189,7 +189,7 @@ typedef struct {
   uint64_t schedule_seed;   /* DOBFS_DIR_RANDOM */
   void* stream;             /* cudaStream_t (NULL: the graph's creation stream) */
   int32_t td_bitmap_div;    /* a top-down level with m_f * td_bitmap_div >= n marks a next-frontier
-                               bitmap and finds parents afterwards (0: never; default 16) */
+                               bitmap and finds parents afterwards (0: never; default 2) */
 } dobfs_run_opts;
 
 typedef struct {

@@ -448,6 +448,7 @@ template <class OffT, bool RECOVER>
 __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ uint32_t s_found[kThreads / 32][32];
+  __shared__ uint16_t s_cand[kThreads / 32][1024];
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
@@ -474,6 +475,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
     s_found[wid][lane] = 0u;
     __syncwarp();
     sc += cnt;
+    // candidate list: each lane writes the positions (word << 5 | bit) of its
+    // word's candidates at its exclusive prefix
+    {
+      uint32_t x = cand;
+      unsigned pos = incl - cnt;
+      while (x) {
+        const unsigned b = (unsigned)(__ffs(x) - 1);
+        x &= x - 1;
+        s_cand[wid][pos++] = (uint16_t)((lane << 5) | b);
+      }
+    }
+    __syncwarp();
     for (unsigned base = 0; base < total; base += 64) {
       // two candidates per lane per round: their load chains overlap
       unsigned jj[2], bb[2];
@@ -482,19 +495,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2) {
         const unsigned k = base + 32 * c2 + lane;
-        // word j holding candidate k: the first lane whose inclusive count exceeds k
-        unsigned j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const unsigned probe = __shfl_sync(0xffffffffu, incl, j + step - 1);
-          if (probe <= k) j += step;
-        }
-        const uint32_t cw = __shfl_sync(0xffffffffu, cand, j);
-        const unsigned ex_j = __shfl_sync(0xffffffffu, incl - cnt, j);
         act[c2] = k < total;
-        jj[c2] = j;
-        bb[c2] = act[c2] ? __fns(cw, 0, (int)(k - ex_j) + 1) : 0u;
-        vv[c2] = (int32_t)((grp * 32 + j) * 32 + bb[c2]);
+        const unsigned loc = act[c2] ? (unsigned)s_cand[wid][k] : 0u;
+        jj[c2] = loc >> 5;
+        bb[c2] = loc & 31u;
+        vv[c2] = (int32_t)(grp * 1024 + loc);
       }
       int2 fd[2];
 #pragma unroll
@@ -1093,7 +1098,7 @@ int dobfs_run_opts_init(dobfs_run_opts* o) {
   o->flags = 0;
   o->schedule_seed = 0;
   o->stream = nullptr;
-  o->td_bitmap_div = 16;
+  o->td_bitmap_div = 2;
   return DOBFS_OK;
 }
 
