@@ -219,6 +219,23 @@ int dobfs_run_opts_init(dobfs_run_opts* opts);
 int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_out,
               const dobfs_run_opts* opts, dobfs_run_stats* stats);
 
+/*
+ * Batched BFS from n_roots roots (original IDs) with the bit-parallel
+ * multi-source traversal: roots are taken 64 at a time as the lanes of one
+ * traversal in which every vertex carries 64-bit masks (lanes that reached
+ * it, lanes for which it is in the frontier); each level runs top-down or
+ * bottom-up (Algorithm 1) for all lanes at once, the direction picked by the
+ * alpha/beta rule on the union of the lanes' frontiers. level_out[n_roots][n]
+ * (int32, row r for roots[r], original IDs) receives the levels, identical
+ * to n_roots separate dobfs_run calls. Levels only: parent_out must be NULL.
+ * roots and level_out may be host or device memory. A lane runs at most 65535
+ * levels. opts: direction auto, top-down, bottom-up or random; alpha, beta,
+ * schedule_seed, stream. stats (nullable): device_ms, levels (deepest
+ * group), edges_examined.
+ */
+int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out, int32_t* parent_out,
+                    const dobfs_run_opts* opts, dobfs_run_stats* stats);
+
 /* Per-level record of the last run on a graph (ready after that run completed). */
 typedef struct {
   int32_t level;            /* level L being expanded (frontier = vertices at level L) */

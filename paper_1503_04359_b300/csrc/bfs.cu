@@ -40,6 +40,7 @@
 #include "../../dobfs_inputs/gen.h"
 #include "common.cuh"
 #include "graph.cuh"
+#include "msbfs.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1072,6 +1073,8 @@ int graph_alloc_workspace(dobfs_graph* g) {
 void graph_release(dobfs_graph* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  ms_group_destroy(g->ms);
+  g->ms = nullptr;
   if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
   if (g->cg) cudaGraphDestroy(g->cg);
   g->cg_exec = nullptr;

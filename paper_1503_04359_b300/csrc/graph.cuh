@@ -9,6 +9,8 @@
 
 namespace dobfs {
 
+struct MsGroup;
+
 // Sentinel edge key: a dropped entry (self-loop or duplicate). Sorts last.
 constexpr uint64_t kSentinelKey = ~0ull;
 
@@ -90,6 +92,10 @@ struct dobfs_graph {
   cudaStream_t last_stream = nullptr;
   bool last_host_loop = false;
   std::vector<float> host_level_ms, host_level_main_ms;
+
+  // batched runs: one lane group and a staging buffer for host outputs
+  dobfs::MsGroup* ms = nullptr;
+  dobfs::DevBuf ms_stage;
 
   std::mutex mu;
 };

@@ -1,0 +1,727 @@
+// Bit-parallel multi-source BFS: up to 64 BFS (one per lane) over the same
+// graph in one traversal, each vertex carrying 64-bit lane masks.
+//
+//   seen[v]       lanes that have reached v
+//   front/next    lanes for which v is in the current / next frontier
+//   planes[b][v]  bit b of the iteration at which each lane reached v
+//
+// A step expands the frontier of iteration t for every lane at once, in the
+// direction of Algorithm 1 picked by the same alpha/beta rule on the union of
+// the lanes' frontiers:
+//   top-down  every frontier vertex u pushes front[u] & ~seen[v] to each
+//             neighbour v (atomicOr into next[v]);
+//   bottom-up every vertex v still missing live lanes ORs front[u] over its
+//             row and stops as soon as all the lanes it misses are found.
+// Vertices found at iteration t+1 get seen |= new and the bits of t+1 set in
+// the planes for those lanes, so each (lane, vertex) level costs no separate
+// store; the flush writes level = (iteration found - start of lane) for all
+// lanes of a vertex in one pass over original IDs, with coalesced stores per
+// lane. Iterations are kept mod 2^16, so a lane may run at most 65535 levels.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../dobfs_inputs/gen.h"
+#include "msbfs.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dobfs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMsChunk = 1024;  // top-down chunk record length
+constexpr int kMsT = 32;        // bottom-up entries per thread before a row continues warp-wide
+constexpr int kMsCases = 2;
+constexpr int kMsCaseNone = 7;
+constexpr unsigned kIterMask = (1u << kMsPlanes) - 1u;
+
+template <class OffT>
+struct MsArgs {
+  const OffT* off;
+  const int32_t* cols;
+  const int2* firstdeg;
+  const int32_t* o2n;
+  uint64_t* seen;
+  uint64_t* fb0;
+  uint64_t* fb1;
+  uint64_t* planes;
+  int2* rec;
+  int32_t* def;
+  MsCtl* ctl;
+  int64_t n, nnz, n_cand, rec_cap;
+};
+
+struct SeedArgs {
+  int32_t count;
+  int32_t lane[kMsLanes];
+  int32_t root[kMsLanes];
+};
+
+struct FlushArgs {
+  unsigned long long lanes;
+  int32_t release;
+  int32_t* out[kMsLanes];
+  int32_t start[kMsLanes];
+};
+
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
+  const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
+  const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ void enqueue_ms(unsigned int* tail, int32_t* q, int32_t v) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
+  base = g.shfl(base, 0);
+  q[base + g.thread_rank()] = v;
+}
+
+// Records the lanes `nw` found at vertex v at iteration T in the planes.
+template <class OffT>
+__device__ __forceinline__ void set_planes(const MsArgs<OffT>& A, int64_t v, unsigned long long nw, unsigned T,
+                                           int n_planes) {
+  for (int b = 0; b < n_planes; ++b)
+    if ((T >> b) & 1u) A.planes[(int64_t)b * A.n + v] |= nw;
+}
+
+template <class OffT>
+__global__ void k_ms_seed(MsArgs<OffT> A, SeedArgs S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  MsCtl* c = A.ctl;
+  const unsigned T = (unsigned)c->iter & kIterMask;
+  uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
+  for (int i = 0; i < S.count; ++i) {
+    const int32_t r = A.o2n ? A.o2n[S.root[i]] : S.root[i];
+    const unsigned long long bit = 1ull << S.lane[i];
+    const unsigned long long s_old = A.seen[r], f_old = front[r];
+    A.seen[r] = s_old | bit;
+    front[r] = f_old | bit;
+    set_planes(A, r, bit, T, c->n_planes);
+    const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
+    if (!f_old) {
+      c->n_f += 1;
+      c->m_f += d;
+    }
+    if (!s_old) c->m_u -= d;
+    c->active |= bit;
+    c->live |= bit;
+  }
+}
+
+template <class OffT>
+__global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
+                            int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  MsCtl* c = A.ctl;
+  if (!c->fresh) {
+    c->n_f_prev = c->n_f;
+    c->n_f = (int64_t)c->nx_n;
+    c->m_f = (int64_t)c->nx_m;
+    c->m_u -= (int64_t)c->nx_mu;
+    c->live = c->nx_live & c->active;
+    c->examined += (int64_t)c->nx_examined;
+    c->iter += 1;
+    c->levels_run += 1;
+    c->nx_n = c->nx_m = c->nx_mu = c->nx_live = c->nx_examined = 0;
+    c->n_rec = c->n_def = 0;
+  }
+  const int prev_dir = c->fresh ? 0 : c->dir;
+  c->fresh = 0;
+  if (c->live == 0 || c->n_f == 0) {
+    c->done = 1;
+    c->live = 0;
+    if (in_graph) {
+      cudaGraphSetConditional(h_case, kMsCaseNone);
+      cudaGraphSetConditional(h_while, 0);
+    }
+    return;
+  }
+  int dir;
+  switch (c->mode) {
+    case DOBFS_DIR_TOPDOWN: dir = 0; break;
+    case DOBFS_DIR_BOTTOMUP: dir = 1; break;
+    case DOBFS_DIR_RANDOM: dir = (int)(gen_mix64(c->sched_seed ^ (uint64_t)c->iter) & 1ull); break;
+    default:
+      if (prev_dir == 0)
+        dir = (c->m_f * (int64_t)c->alpha > c->m_u) ? 1 : 0;
+      else
+        dir = (c->n_f * (int64_t)c->beta < A.n && c->n_f < c->n_f_prev) ? 0 : 1;
+      break;
+  }
+  // the planes needed by iteration t+1 must be clean: clear the next one the
+  // first time t+1 reaches it
+  const unsigned tn = (unsigned)(c->iter + 1) & kIterMask;
+  c->clear_plane = -1;
+  if (c->n_planes < kMsPlanes && (tn >> c->n_planes) != 0u) {
+    c->clear_plane = c->n_planes;
+    c->n_planes += 1;
+  }
+  c->dir = dir;
+  c->step_case = dir;
+  c->done = 0;
+  if (in_graph) cudaGraphSetConditional(h_case, (unsigned)dir);
+}
+
+template <class OffT>
+__global__ void k_ms_clear_plane(MsArgs<OffT> A) {
+  const int b = A.ctl->clear_plane;
+  if (b < 0) return;
+  uint64_t* p = A.planes + (int64_t)b * A.n;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n; v += (int64_t)gridDim.x * blockDim.x)
+    p[v] = 0ull;
+}
+
+template <class OffT>
+__global__ void k_ms_clear_next(MsArgs<OffT> A) {
+  uint64_t* next = (A.ctl->iter & 1) ? A.fb0 : A.fb1;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x)
+    next[v] = 0ull;
+}
+
+// Top-down, part 1: chunk records for the rows of the frontier vertices.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
+  const uint64_t* front = (A.ctl->iter & 1) ? A.fb1 : A.fb0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!front[v]) continue;
+    const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
+    if (d == 0) continue;
+    const unsigned nch = (unsigned)ceil_div(d, kMsChunk);
+    const unsigned base = atomicAdd(&A.ctl->n_rec, nch);
+    if ((int64_t)base + nch > A.rec_cap) continue;  // cannot happen: one record per kMsChunk entries or vertex
+    for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2((int32_t)v, (int32_t)k);
+  }
+}
+
+// Top-down, part 2: one warp per record pushes front[u] to the unseen lanes
+// of each neighbour.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const MsCtl* c = A.ctl;
+  const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
+  uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
+  const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
+  const unsigned lane = lane_id();
+  unsigned long long ex = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
+    const int2 rc = A.rec[r];
+    const int32_t u = rc.x;
+    const unsigned long long fu = front[u];
+    const int64_t s = (int64_t)A.off[u] + (int64_t)rc.y * kMsChunk;
+    const int64_t e = min((int64_t)A.off[u + 1], s + kMsChunk);
+    if (lane == 0) ex += (unsigned long long)(e - s);
+    for (int64_t j = s + lane; j < e; j += 32) {
+      const int32_t v = A.cols[j];
+      const unsigned long long m = fu & ~__ldg(A.seen + v);
+      if (m && (m & ~__ldcg(next + v))) atomicOr(reinterpret_cast<unsigned long long*>(next + v), m);
+    }
+  }
+  ex = block_sum_u64(ex, sh);
+  if (threadIdx.x == 0 && ex) atomicAdd(&A.ctl->nx_examined, ex);
+}
+
+// Folds the lanes found at vertex v into the step's counters.
+struct MsCount {
+  unsigned long long n = 0, m = 0, mu = 0, live = 0, ex = 0;
+};
+
+// Top-down, part 3: the pushed masks become the next frontier; record them.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  MsCtl* c = A.ctl;
+  uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
+  const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
+  const int np = c->n_planes;
+  MsCount k;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long nx = next[v];
+    if (!nx) continue;
+    const unsigned long long s = A.seen[v];
+    const unsigned long long nw = nx & ~s;
+    next[v] = nw;
+    if (!nw) continue;
+    A.seen[v] = s | nw;
+    set_planes(A, v, nw, T, np);
+    const int64_t d = A.firstdeg[v].y;
+    k.n += 1;
+    k.m += (unsigned long long)d;
+    if (!s) k.mu += (unsigned long long)d;
+    k.live |= nw;
+  }
+  const unsigned long long lv = warp_or64(k.live);
+  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
+  k.n = block_sum_u64(k.n, sh);
+  k.m = block_sum_u64(k.m, sh);
+  k.mu = block_sum_u64(k.mu, sh);
+  if (threadIdx.x == 0) {
+    if (k.n) atomicAdd(&c->nx_n, k.n);
+    if (k.m) atomicAdd(&c->nx_m, k.m);
+    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
+  }
+}
+
+// Bottom-up, part 1: one vertex per thread. A vertex missing live lanes ORs
+// the frontier masks of its first kMsT neighbours and stops once every
+// missing lane is found; longer rows continue in k_ms_bu_long with the
+// partial mask kept in next[v].
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  MsCtl* c = A.ctl;
+  const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
+  uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
+  const unsigned long long live = c->live;
+  const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
+  const int np = c->n_planes;
+  MsCount k;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long s = A.seen[v];
+    const unsigned long long need = live & ~s;
+    if (!need) {
+      next[v] = 0ull;
+      continue;
+    }
+    const int2 fd = A.firstdeg[v];
+    unsigned long long acc = 0;
+    int64_t j = 0;
+    if (fd.y > 0) {
+      acc = __ldg(front + fd.x);
+      j = 1;
+      const int64_t o = (int64_t)A.off[v];
+      const int64_t lim = min((int64_t)fd.y, (int64_t)kMsT);
+      while (j < lim && (acc & need) != need) {
+        int32_t u[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) u[t] = (j + t < lim) ? A.cols[o + j + t] : -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (u[t] >= 0) acc |= __ldg(front + u[t]);
+        j = min(j + 4, lim);
+      }
+    }
+    k.ex += (unsigned long long)j;
+    const unsigned long long nw = acc & need;
+    if (nw != need && fd.y > kMsT) {
+      next[v] = nw;  // partial: k_ms_bu_long finishes the row
+      enqueue_ms(&c->n_def, A.def, (int32_t)v);
+      continue;
+    }
+    next[v] = nw;
+    if (!nw) continue;
+    A.seen[v] = s | nw;
+    set_planes(A, v, nw, T, np);
+    k.n += 1;
+    k.m += (unsigned long long)fd.y;
+    if (!s) k.mu += (unsigned long long)fd.y;
+    k.live |= nw;
+  }
+  const unsigned long long lv = warp_or64(k.live);
+  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
+  k.n = block_sum_u64(k.n, sh);
+  k.m = block_sum_u64(k.m, sh);
+  k.mu = block_sum_u64(k.mu, sh);
+  k.ex = block_sum_u64(k.ex, sh);
+  if (threadIdx.x == 0) {
+    if (k.n) atomicAdd(&c->nx_n, k.n);
+    if (k.m) atomicAdd(&c->nx_m, k.m);
+    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
+    if (k.ex) atomicAdd(&c->nx_examined, k.ex);
+  }
+}
+
+// Bottom-up, part 2: the rest of long rows, one warp per row, with the
+// early-exit test after every 32 entries.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  MsCtl* c = A.ctl;
+  const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
+  uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
+  const unsigned long long live = c->live;
+  const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
+  const int np = c->n_planes;
+  const int64_t nd = c->n_def;
+  const unsigned lane = lane_id();
+  MsCount k;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
+    const int32_t v = A.def[i];
+    const unsigned long long s = A.seen[v];
+    const unsigned long long need = live & ~s;
+    unsigned long long acc = next[v];
+    const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    int64_t j = o + kMsT;
+    while (j < e && (acc & need) != need) {
+      const int64_t p = j + lane;
+      unsigned long long x = 0;
+      if (p < e) x = __ldg(front + A.cols[p]);
+      acc |= warp_or64(x);
+      if (lane == 0) k.ex += (unsigned long long)min((int64_t)32, e - j);
+      j += 32;
+    }
+    const unsigned long long nw = acc & need;
+    if (lane == 0) {
+      next[v] = nw;
+      if (nw) {
+        A.seen[v] = s | nw;
+        set_planes(A, v, nw, T, np);
+        const int64_t d = e - o;
+        k.n += 1;
+        k.m += (unsigned long long)d;
+        if (!s) k.mu += (unsigned long long)d;
+        k.live |= nw;
+      }
+    }
+  }
+  const unsigned long long lv = warp_or64(k.live);
+  if (lane == 0 && lv) atomicOr(&c->nx_live, lv);
+  k.n = block_sum_u64(k.n, sh);
+  k.m = block_sum_u64(k.m, sh);
+  k.mu = block_sum_u64(k.mu, sh);
+  k.ex = block_sum_u64(k.ex, sh);
+  if (threadIdx.x == 0) {
+    if (k.n) atomicAdd(&c->nx_n, k.n);
+    if (k.m) atomicAdd(&c->nx_m, k.m);
+    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
+    if (k.ex) atomicAdd(&c->nx_examined, k.ex);
+  }
+}
+
+// Writes the levels of the lanes in F.lanes for every original ID, and with
+// F.release clears those lanes' bits.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs F) {
+  const int np = A.ctl->n_planes;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = A.o2n ? A.o2n[o] : o;
+    const unsigned long long s = A.seen[v];
+    const unsigned long long hit = s & F.lanes;
+    unsigned long long pl[kMsPlanes];
+#pragma unroll
+    for (int b = 0; b < kMsPlanes; ++b) pl[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n + v] : 0ull;
+    unsigned long long lanes = F.lanes;
+    while (lanes) {
+      const int i = __ffsll((long long)lanes) - 1;
+      lanes &= lanes - 1;
+      int32_t lev = -1;
+      if ((hit >> i) & 1ull) {
+        unsigned T = 0;
+#pragma unroll
+        for (int b = 0; b < kMsPlanes; ++b) T |= (unsigned)((pl[b] >> i) & 1ull) << b;
+        lev = (int32_t)((T - (unsigned)F.start[i]) & kIterMask);
+      }
+      F.out[i][o] = lev;
+    }
+    if (F.release && hit) {
+      A.seen[v] = s & ~F.lanes;
+      for (int b = 0; b < np; ++b) A.planes[(int64_t)b * A.n + v] = pl[b] & ~F.lanes;
+    }
+  }
+}
+
+template <class OffT>
+MsArgs<OffT> ms_args(MsGroup* m) {
+  dobfs_graph* g = m->g;
+  MsArgs<OffT> A;
+  A.off = g->off.as<OffT>();
+  A.cols = g->cols.as<int32_t>();
+  A.firstdeg = g->firstdeg.as<int2>();
+  A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
+  A.seen = m->seen.as<uint64_t>();
+  A.fb0 = m->fb0.as<uint64_t>();
+  A.fb1 = m->fb1.as<uint64_t>();
+  A.planes = m->planes.as<uint64_t>();
+  A.rec = m->rec.as<int2>();
+  A.def = m->def.as<int32_t>();
+  A.ctl = m->ctl.as<MsCtl>();
+  A.n = g->n;
+  A.nnz = g->nnz;
+  A.n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
+  A.rec_cap = m->rec_cap;
+  return A;
+}
+
+int ms_grid(int per_sm = 8) { return sm_count() * per_sm; }
+
+template <class OffT>
+int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
+  const MsArgs<OffT> A = ms_args<OffT>(m);
+  const int G = ms_grid();
+  k_ms_clear_plane<OffT><<<G, kThreads, 0, s>>>(A);
+  if (kase == 0) {
+    k_ms_clear_next<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_td_list<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_td<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_td_post<OffT><<<G, kThreads, 0, s>>>(A);
+  } else {
+    k_ms_bu<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu_long<OffT><<<G, kThreads, 0, s>>>(A);
+  }
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int ms_build_graph(MsGroup* m) {
+  const MsArgs<OffT> A = ms_args<OffT>(m);
+  cudaStream_t cs = nullptr;
+  DOBFS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  auto fail = [&](int rc) {
+    cudaStreamDestroy(cs);
+    if (m->cg) cudaGraphDestroy(m->cg);
+    m->cg = nullptr;
+    return rc;
+  };
+  if (cudaGraphCreate(&m->cg, 0) != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "cudaGraphCreate failed"));
+  cudaGraphConditionalHandle h_while, h_case;
+  if (cudaGraphConditionalHandleCreate(&h_while, m->cg, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "conditional handle failed"));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_while;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (cudaGraphAddNode(&wnode, m->cg, nullptr, nullptr, 0, &wp) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "while node failed"));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  if (cudaGraphConditionalHandleCreate(&h_case, body, 0, 0) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "conditional handle failed"));
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "capture failed"));
+  k_ms_switch<OffT><<<1, 32, 0, cs>>>(A, h_while, h_case, 1);
+  cudaGraph_t captured = nullptr;
+  if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture failed"));
+  size_t nn = 0;
+  cudaGraphGetNodes(body, nullptr, &nn);
+  if (nn != 1) return fail(set_error(DOBFS_ERR_CUDA, "unexpected body node count %zu", nn));
+  cudaGraphNode_t sw;
+  cudaGraphGetNodes(body, &sw, &nn);
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = h_case;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = kMsCases;
+  cudaGraphNode_t snode;
+  if (cudaGraphAddNode(&snode, body, &sw, nullptr, 1, &sp) != cudaSuccess)
+    return fail(set_error(DOBFS_ERR_CUDA, "switch node failed"));
+  for (int k = 0; k < kMsCases; ++k) {
+    if (cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return fail(set_error(DOBFS_ERR_CUDA, "capture case failed"));
+    const int rc = ms_launch_case<OffT>(m, k, cs);
+    cudaGraph_t cap = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &cap);
+    if (rc != DOBFS_OK) return fail(rc);
+    if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture case: %s", cudaGetErrorString(e)));
+  }
+  const cudaError_t e = cudaGraphInstantiate(&m->exec, m->cg, 0);
+  if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e)));
+  cudaStreamDestroy(cs);
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int ms_seed_impl(MsGroup* m, const SeedArgs& S) {
+  k_ms_seed<OffT><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), S);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int ms_step_impl(MsGroup* m) {
+  const MsArgs<OffT> A = ms_args<OffT>(m);
+  k_ms_switch<OffT><<<1, 32, 0, m->stream>>>(A, 0, 0, 0);
+  int32_t hdr[5];
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(hdr, m->ctl.ptr, sizeof(hdr), cudaMemcpyDeviceToHost, m->stream));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (hdr[4]) return DOBFS_OK;  // done: no live lane
+  return ms_launch_case<OffT>(m, hdr[2], m->stream);
+}
+
+template <class OffT>
+int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
+  const int G = (int)std::min<int64_t>(ceil_div(m->g->n, kThreads), (int64_t)ms_grid(16));
+  k_ms_flush<OffT><<<G, kThreads, 0, m->stream>>>(ms_args<OffT>(m), F);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
+}
+
+}  // namespace
+
+int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out) {
+  MsGroup* m = new (std::nothrow) MsGroup();
+  if (!m) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  m->g = g;
+  m->stream = s;
+  const size_t vb = sizeof(uint64_t) * (size_t)g->n;
+  int rc = m->seen.alloc(vb, s);
+  if (rc == DOBFS_OK) rc = m->fb0.alloc(vb, s);
+  if (rc == DOBFS_OK) rc = m->fb1.alloc(vb, s);
+  if (rc == DOBFS_OK) rc = m->planes.alloc(vb * kMsPlanes, s);
+  const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
+  m->rec_cap = n_cand + g->nnz / kMsChunk + 64;
+  if (rc == DOBFS_OK) rc = m->rec.alloc(sizeof(int2) * (size_t)m->rec_cap, s);
+  if (rc == DOBFS_OK) rc = m->def.alloc(sizeof(int32_t) * (size_t)g->n, s);
+  if (rc == DOBFS_OK) rc = m->ctl.alloc(sizeof(MsCtl), s);
+  if (rc != DOBFS_OK) {
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return DOBFS_OK;
+}
+
+void ms_group_destroy(MsGroup* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->cg) cudaGraphDestroy(m->cg);
+  delete m;
+}
+
+int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
+  cudaStream_t s = m->stream;
+  const size_t vb = sizeof(uint64_t) * (size_t)m->g->n;
+  DOBFS_CUDA_TRY(cudaMemsetAsync(m->seen.ptr, 0, vb, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb0.ptr, 0, vb, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb1.ptr, 0, vb, s));
+  constexpr int kFirstPlanes = 4;  // iterations below 16; later planes are cleared on first use
+  DOBFS_CUDA_TRY(cudaMemsetAsync(m->planes.ptr, 0, vb * kFirstPlanes, s));
+  MsCtl c;
+  memset(&c, 0, sizeof(c));
+  c.fresh = 1;
+  c.n_planes = kFirstPlanes;
+  c.clear_plane = -1;
+  c.m_u = m->g->nnz;
+  c.mode = o.direction;
+  c.alpha = o.alpha;
+  c.beta = o.beta;
+  c.sched_seed = o.schedule_seed;
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(m->ctl.ptr, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));  // c is on this stack
+  return DOBFS_OK;
+}
+
+int ms_group_seed(MsGroup* m, int count, const int32_t* lane, const int32_t* root) {
+  if (count < 0 || count > kMsLanes) return set_error(DOBFS_ERR_INVALID, "at most 64 lanes per seeding");
+  SeedArgs S;
+  S.count = count;
+  for (int i = 0; i < count; ++i) {
+    S.lane[i] = lane[i];
+    S.root[i] = root[i];
+  }
+  return m->g->off64 ? ms_seed_impl<int64_t>(m, S) : ms_seed_impl<int32_t>(m, S);
+}
+
+int ms_group_step(MsGroup* m) { return m->g->off64 ? ms_step_impl<int64_t>(m) : ms_step_impl<int32_t>(m); }
+
+int ms_group_run_to_end(MsGroup* m) {
+  if (!m->exec) DOBFS_TRY(m->g->off64 ? ms_build_graph<int64_t>(m) : ms_build_graph<int32_t>(m));
+  DOBFS_CUDA_TRY(cudaGraphLaunch(m->exec, m->stream));
+  return DOBFS_OK;
+}
+
+int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_t* start, bool release) {
+  FlushArgs F;
+  memset(&F, 0, sizeof(F));
+  F.lanes = lanes;
+  F.release = release ? 1 : 0;
+  for (int i = 0; i < kMsLanes; ++i) {
+    F.out[i] = ((lanes >> i) & 1ull) ? out[i] : nullptr;
+    F.start[i] = start ? start[i] : 0;
+  }
+  return m->g->off64 ? ms_flush_impl<int64_t>(m, F) : ms_flush_impl<int32_t>(m, F);
+}
+
+int ms_group_read_ctl(MsGroup* m, MsCtl* c) {
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(c, m->ctl.ptr, sizeof(MsCtl), cudaMemcpyDeviceToHost, m->stream));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return DOBFS_OK;
+}
+
+}  // namespace dobfs
+
+using namespace dobfs;
+
+extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out,
+                               int32_t* parent_out, const dobfs_run_opts* opts, dobfs_run_stats* stats) {
+  clear_error();
+  if (!g || !roots || !level_out || n_roots < 0)
+    return set_error(DOBFS_ERR_INVALID, "graph, roots and level_out are required");
+  if (parent_out)
+    return set_error(DOBFS_ERR_INVALID,
+                     "dobfs_run_batch produces levels only; use dobfs_run for parents (parent_out must be NULL)");
+  dobfs_run_opts o;
+  dobfs_run_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.alpha < 1 || o.beta < 1)
+    return set_error(DOBFS_ERR_INVALID, "bad run options for a batch (direction must be auto, top-down, "
+                                        "bottom-up or random)");
+  std::vector<int32_t> hroots((size_t)n_roots);
+  if (n_roots > 0) {
+    if (is_device_ptr(roots))
+      DOBFS_CUDA_TRY(cudaMemcpy(hroots.data(), roots, sizeof(int32_t) * (size_t)n_roots, cudaMemcpyDeviceToHost));
+    else
+      memcpy(hroots.data(), roots, sizeof(int32_t) * (size_t)n_roots);
+  }
+  for (int32_t i = 0; i < n_roots; ++i)
+    if (hroots[i] < 0 || hroots[i] >= g->n)
+      return set_error(DOBFS_ERR_INVALID, "root %d (index %d) out of range [0, %lld)", hroots[i], i, (long long)g->n);
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t s = o.stream ? (cudaStream_t)o.stream : g->stream;
+  if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+  if (!g->ms) DOBFS_TRY(ms_group_create(g, s, &g->ms));
+  MsGroup* m = g->ms;
+  m->stream = s;
+  const bool dev_out = is_device_ptr(level_out);
+  if (!dev_out && !g->ms_stage.ptr)
+    DOBFS_TRY(g->ms_stage.alloc(sizeof(int32_t) * (size_t)kMsLanes * (size_t)g->n, g->stream));
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
+  int32_t max_levels = 0;
+  int64_t examined = 0;
+  for (int32_t b0 = 0; b0 < n_roots; b0 += kMsLanes) {
+    const int cnt = (int)std::min<int32_t>(kMsLanes, n_roots - b0);
+    DOBFS_TRY(ms_group_reset(m, o));
+    int32_t lanes[kMsLanes];
+    for (int i = 0; i < cnt; ++i) lanes[i] = i;
+    DOBFS_TRY(ms_group_seed(m, cnt, lanes, hroots.data() + b0));
+    DOBFS_TRY(ms_group_run_to_end(m));
+    int32_t* outp[kMsLanes];
+    for (int i = 0; i < kMsLanes; ++i)
+      outp[i] = i < cnt ? (dev_out ? level_out + (int64_t)(b0 + i) * g->n : g->ms_stage.as<int32_t>() + (int64_t)i * g->n)
+                        : nullptr;
+    const uint64_t lm = cnt == 64 ? ~0ull : ((1ull << cnt) - 1ull);
+    DOBFS_TRY(ms_group_flush(m, lm, outp, nullptr, false));
+    if (!dev_out)
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(level_out + (int64_t)b0 * g->n, g->ms_stage.ptr,
+                                     sizeof(int32_t) * (size_t)cnt * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+    if (stats) {
+      MsCtl c;
+      DOBFS_TRY(ms_group_read_ctl(m, &c));
+      max_levels = std::max(max_levels, c.levels_run);
+      examined += c.examined;
+    }
+  }
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t1, s));
+  DOBFS_CUDA_TRY(cudaEventRecord(g->ev_done, s));
+  g->last_stream = s;
+  if (!dev_out || stats) DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev_t0, g->ev_t1);
+    stats->device_ms = ms;
+    stats->levels = max_levels;
+    stats->edges_examined = examined;
+  }
+  return DOBFS_OK;
+}

@@ -1,0 +1,75 @@
+// Bit-parallel multi-source BFS (64 roots per lane group) on a dobfs_graph.
+//
+// Used by dobfs_run_batch (a group runs a batch of up to 64 roots to the end)
+// and by the query server (lanes join and leave a running group at level
+// boundaries). A group owns its per-vertex lane masks and its control block;
+// the graph's CSR is shared read-only.
+#pragma once
+
+#include "common.cuh"
+#include "graph.cuh"
+
+namespace dobfs {
+
+constexpr int kMsLanes = 64;
+constexpr int kMsPlanes = 16;  // discovery iterations are kept mod 2^16
+
+// Device control block of a lane group.
+struct MsCtl {
+  int32_t iter;          // iteration t: the frontier holds the vertices found at iteration t
+  int32_t dir;           // direction of the step expanding iteration t: 0 top-down, 1 bottom-up
+  int32_t step_case;
+  int32_t fresh;
+  int32_t done;
+  int32_t n_planes;      // planes cleared so far (planes >= n_planes hold stale bits)
+  int32_t clear_plane;   // plane the running step clears first (-1: none)
+  int32_t levels_run;    // steps since the last reset
+  unsigned long long active;  // lanes holding a query
+  unsigned long long live;    // lanes with a non-empty frontier
+  int64_t n_f, m_f, m_u, n_f_prev;
+  // accumulators of the running step
+  unsigned long long nx_n, nx_m, nx_mu, nx_live, nx_examined;
+  unsigned int n_rec, n_def;
+  // parameters
+  int32_t mode, alpha, beta, pad;
+  uint64_t sched_seed;
+  int64_t examined;
+};
+
+struct MsGroup {
+  dobfs_graph* g = nullptr;
+  cudaStream_t stream = nullptr;
+  DevBuf seen, fb0, fb1;  // uint64[n]: lanes that reached v; frontier masks by iteration parity
+  DevBuf planes;          // uint64[kMsPlanes][n]: bit b of the discovery iteration, per lane
+  DevBuf rec;             // int2[]: top-down chunk records
+  int64_t rec_cap = 0;
+  DevBuf def;             // int32[n]: bottom-up rows continued warp-wide
+  DevBuf ctl;             // MsCtl
+  DevBuf args;            // device copy of seeding arguments
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// Creates a group on g (allocates its masks); *out owned by the caller.
+int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out);
+void ms_group_destroy(MsGroup* m);
+
+// Clears every mask and counter (all lanes free).
+int ms_group_reset(MsGroup* m, const dobfs_run_opts& o);
+
+// Starts lanes lane[i] at the current iteration from original-ID roots root[i].
+int ms_group_seed(MsGroup* m, int count, const int32_t* lane, const int32_t* root);
+
+// One level from the host (the server's loop) or the whole loop as one graph launch.
+int ms_group_step(MsGroup* m);
+int ms_group_run_to_end(MsGroup* m);
+
+// Writes levels of the lanes in `lanes` into out[i][n] (original IDs; -1 if
+// unreached), levels counted from start[i]; with `release` the lanes' bits
+// are cleared and the lanes freed.
+int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_t* start, bool release);
+
+// Reads the control block (synchronises the group's stream).
+int ms_group_read_ctl(MsGroup* m, MsCtl* c);
+
+}  // namespace dobfs

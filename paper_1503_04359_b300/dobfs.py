@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
         "dobfs_last_trace": (c_int, [G, ctypes.POINTER(dobfs_level_trace), i32, ctypes.POINTER(i32)]),
         "dobfs_run_static": (c_int, [vp, vp, i32, i32, vp, vp, vp]),
+        "dobfs_run_batch": (c_int, [G, vp, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +260,17 @@ def dobfs_run(g: int, root: int, level_out, parent_out=None, opts: dobfs_run_opt
     st = dobfs_run_stats() if want_stats else None
     _check(load().dobfs_run(g, int(root), _ptr(level_out), _ptr(parent_out), ctypes.byref(opts),
                             ctypes.byref(st) if st is not None else None))
+    return st
+
+
+def dobfs_run_batch(g: int, roots, level_out, parent_out=None, opts: dobfs_run_opts | None = None,
+                    want_stats: bool = False) -> dobfs_run_stats | None:
+    """Batched BFS: level_out[len(roots)][n] receives one level row per root."""
+    if opts is None:
+        opts = make_opts()
+    st = dobfs_run_stats() if want_stats else None
+    _check(load().dobfs_run_batch(g, _ptr(roots), int(roots.shape[0]), _ptr(level_out), _ptr(parent_out),
+                                  ctypes.byref(opts), ctypes.byref(st) if st is not None else None))
     return st
 
 

@@ -1,0 +1,105 @@
+"""GPU parity of batched (64-lane bit-parallel) BFS against the CPU oracle.
+
+Every row of the batch output must equal the oracle's level array for that
+root bit-exact, whatever the direction schedule, the batch size (full and
+partial lane groups, several groups) or repeated roots.
+"""
+import numpy as np
+import pytest
+
+import dobfs_inputs as inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def d():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_04359_b300 import build, dobfs
+    build.build()
+    dobfs.load()
+    dobfs.use_torch_allocator()
+    return dobfs
+
+
+@pytest.fixture(scope="module")
+def s14():
+    spec = inputs.rmat(14)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 100, og.degrees() > 0)
+    lv, _ = oracle.bfs_many(og, roots, want_parent=False)
+    return spec, og, roots, lv
+
+
+def _batch(d, g, roots, mode=0, seed=0, host=False):
+    n = g.n
+    roots = np.asarray(roots, dtype=np.int32)
+    if host:
+        out = np.full((len(roots), n), 7, dtype=np.int32)
+        d.dobfs_run_batch(g.handle, roots, out, opts=d.make_opts(direction=mode, schedule_seed=seed))
+        return out
+    out = torch.full((len(roots), n), 7, dtype=torch.int32, device="cuda")
+    d.dobfs_run_batch(g.handle, torch.from_numpy(roots).cuda(), out,
+                      opts=d.make_opts(direction=mode, schedule_seed=seed))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode,seed", [(0, 0), (1, 0), (2, 0), (3, 1), (3, 2)])
+@pytest.mark.parametrize("flags", [0, 0x2])
+def test_batch_levels_bit_exact(d, s14, mode, seed, flags):
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=flags)
+    out = _batch(d, g, roots, mode, seed)          # one full group of 64 and a partial one of 36
+    np.testing.assert_array_equal(out, ref)
+
+
+def test_batch_sizes_duplicates_host(d, s14):
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64)
+    for k in (1, 3, 63, 64, 65):
+        np.testing.assert_array_equal(_batch(d, g, roots[:k]), ref[:k])
+    dup = np.array([roots[0], roots[1], roots[0], roots[0]], dtype=np.int32)
+    np.testing.assert_array_equal(_batch(d, g, dup), ref[[0, 1, 0, 0]])
+    np.testing.assert_array_equal(_batch(d, g, roots[:70], host=True), ref[:70])
+    # same as single-source runs of the same graph
+    lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    g.run(int(roots[5]), lv)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lv.cpu().numpy(), ref[5])
+
+
+def test_batch_closed_forms(d):
+    # a path of 3000 vertices (levels up to 2999: iteration planes cleared as they come into use),
+    # a star, and a separate triangle plus an isolated vertex
+    n_path = 3000
+    pairs = [(i, i + 1) for i in range(n_path - 1)]
+    star0 = n_path
+    pairs += [(star0, star0 + i) for i in range(1, 200)]
+    tri = star0 + 200
+    pairs += [(tri, tri + 1), (tri + 1, tri + 2), (tri + 2, tri)]
+    n = tri + 4
+    src = np.array([p[0] for p in pairs], dtype=np.int32)
+    dst = np.array([p[1] for p in pairs], dtype=np.int32)
+    og = oracle.csr_from_pairs(n, src, dst)
+    roots = np.array([0, 1500, n_path - 1, star0, star0 + 7, tri, n - 1], dtype=np.int32)
+    ref = np.stack([oracle.bfs(og, int(r), want_parent=False)[0] for r in roots])
+    for flags in (0, 0x2):
+        g = d.pairs_graph(n, src, dst, flags=flags)
+        for mode in (0, 1, 2):
+            np.testing.assert_array_equal(_batch(d, g, roots, mode), ref)
+
+
+def test_batch_rejects_parents_and_bad_roots(d, s14):
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=0)
+    out = torch.empty((2, g.n), dtype=torch.int32, device="cuda")
+    with pytest.raises(d.DobfsError) as e:
+        d.dobfs_run_batch(g.handle, roots[:2], out, parent_out=out)
+    assert e.value.status == d.DOBFS_ERR_INVALID
+    with pytest.raises(d.DobfsError) as e:
+        d.dobfs_run_batch(g.handle, np.array([0, g.n], dtype=np.int32), out)
+    assert e.value.status == d.DOBFS_ERR_INVALID
