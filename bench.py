@@ -135,6 +135,59 @@ def cpu_baseline(scale: int = 22, n_roots: int = 4) -> dict:
             "seconds": t_sum}
 
 
+def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps: int = 3) -> dict:
+    """Batched BFS (64-lane bit-parallel groups) against one-at-a-time runs on
+    the same R-MAT graph: roots/s for batches of 64/256/1024 seeded roots and
+    for 64 sequential single-source runs (levels only in both), with device
+    time from CUDA events. Outputs stay on the device (1024 x n int32)."""
+    spec = inputs.rmat(scale)
+    g = dobfs.rmat_graph(spec, flags=dobfs.DOBFS_GRAPH_REINDEX)
+    n = g.n
+    deg = g.degrees()
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0xBA7C, n, max(sizes), deg > 0)
+    stream = torch.cuda.current_stream()
+    opts = dobfs.make_opts(stream=stream)
+    lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    teps = []
+    for r in roots[:64]:
+        teps.append(g.run(int(r), lv, None, opts, want_stats=True).teps_edges)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for r in roots[:64]:
+        g.run(int(r), lv, None, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_rps = 64 / (seq_ms * 1e-3)
+    out = torch.empty((max(sizes), n), dtype=torch.int32, device="cuda")
+    res = {"workload": "rmat-s%d-ef16-reindex" % scale, "n_vertices": n, "n_entries": int(g.info.n_entries),
+           "sequential": {"roots": 64, "ms": seq_ms, "roots_per_s": seq_rps,
+                          "gteps": float(np.sum(teps)) / (seq_ms * 1e-3) / 1e9},
+           "batches": {}}
+    mean_teps = float(np.mean(teps))
+    for b in sizes:
+        rt = torch.from_numpy(np.ascontiguousarray(roots[:b])).cuda()
+        dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=opts)
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        rps = b / (ms * 1e-3)
+        res["batches"][str(b)] = {"ms": ms, "roots_per_s": rps, "speedup_vs_sequential": rps / seq_rps,
+                                  "gteps_est": b * mean_teps / (ms * 1e-3) / 1e9}
+    del out
+    g.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args) -> None:
     ws, rank, _ = _dist()
     if rank != 0:
@@ -178,6 +231,8 @@ def main() -> None:
     ap.add_argument("--no-reindex", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-BFS measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -314,6 +369,15 @@ def main() -> None:
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline()
 
+    # the remaining measurements use their own graphs
+    del level, parent, hl_lv, hl_pa
+    g.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    batch = None
+    if not args.no_batch:
+        batch = measure_batch(torch, inputs, dobfs, args.batch_scale)
+
     if rank != 0:
         return
     result = {
@@ -356,6 +420,8 @@ def main() -> None:
     }
     if cpu is not None:
         result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if batch is not None:
+        result["batch"] = batch
     print(json.dumps(result))
 
 

@@ -1008,6 +1008,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_done, s));
   g->last_stream = s;
   g->last_host_loop = host_loop_mode;
+  g->last_trace_batch = false;
   if (!dev_level) DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   if (want_stats) {
     DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_t1));
@@ -1127,6 +1128,12 @@ int dobfs_last_trace(const dobfs_graph* gc, dobfs_level_trace* out, int32_t max_
   dobfs_graph* g = const_cast<dobfs_graph*>(gc);
   std::lock_guard<std::mutex> lk(g->mu);
   DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
+  if (g->last_trace_batch) {
+    const int32_t nb = (int32_t)std::min<size_t>(g->batch_trace.size(), (size_t)max_levels);
+    for (int32_t i = 0; i < nb; ++i) out[i] = g->batch_trace[i];
+    *n_out = nb;
+    return DOBFS_OK;
+  }
   BfsCtl c;
   DOBFS_CUDA_TRY(cudaMemcpy(&c, g->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost));
   const int32_t n = std::min<int32_t>(std::min<int32_t>(c.n_levels, kMaxTrace), max_levels);

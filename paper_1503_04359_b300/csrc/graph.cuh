@@ -96,6 +96,8 @@ struct dobfs_graph {
   // batched runs: one lane group and a staging buffer for host outputs
   dobfs::MsGroup* ms = nullptr;
   dobfs::DevBuf ms_stage;
+  std::vector<dobfs_level_trace> batch_trace;  // host-driven batch levels (first group)
+  bool last_trace_batch = false;
 
   std::mutex mu;
 };

@@ -89,27 +89,30 @@ __device__ __forceinline__ void set_planes(const MsArgs<OffT>& A, int64_t v, uns
     if ((T >> b) & 1u) A.planes[(int64_t)b * A.n + v] |= nw;
 }
 
+// One thread per seeded lane; repeated roots are counted once in the
+// frontier and unvisited-edge totals (the atomics tell the first one).
 template <class OffT>
 __global__ void k_ms_seed(MsArgs<OffT> A, SeedArgs S) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int i = threadIdx.x;
   MsCtl* c = A.ctl;
   const unsigned T = (unsigned)c->iter & kIterMask;
+  const int np = c->n_planes;
   uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
-  for (int i = 0; i < S.count; ++i) {
+  if (i < S.count) {
     const int32_t r = A.o2n ? A.o2n[S.root[i]] : S.root[i];
     const unsigned long long bit = 1ull << S.lane[i];
-    const unsigned long long s_old = A.seen[r], f_old = front[r];
-    A.seen[r] = s_old | bit;
-    front[r] = f_old | bit;
-    set_planes(A, r, bit, T, c->n_planes);
-    const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
+    const unsigned long long s_old = atomicOr(reinterpret_cast<unsigned long long*>(A.seen + r), bit);
+    const unsigned long long f_old = atomicOr(reinterpret_cast<unsigned long long*>(front + r), bit);
+    for (int b = 0; b < np; ++b)
+      if ((T >> b) & 1u) atomicOr(reinterpret_cast<unsigned long long*>(A.planes + (int64_t)b * A.n + r), bit);
+    const long long d = (long long)A.off[r + 1] - (long long)A.off[r];
     if (!f_old) {
-      c->n_f += 1;
-      c->m_f += d;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&c->n_f), 1ull);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_f), (unsigned long long)d);
     }
-    if (!s_old) c->m_u -= d;
-    c->active |= bit;
-    c->live |= bit;
+    if (!s_old) atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_u), (unsigned long long)(-d));
+    atomicOr(&c->active, bit);
+    atomicOr(&c->live, bit);
   }
 }
 
@@ -358,14 +361,21 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
     const unsigned long long need = live & ~s;
     unsigned long long acc = next[v];
     const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
-    int64_t j = o + kMsT;
-    while (j < e && (acc & need) != need) {
-      const int64_t p = j + lane;
+    const int64_t s0 = o + kMsT;
+    // 128 entries per warp step: one 16-byte column load and four frontier
+    // masks per lane, then one test for the early exit
+    for (int64_t base = s0 & ~3ll; base < e && (acc & need) != need; base += 128) {
+      const int64_t p = base + 4 * (int64_t)lane;
       unsigned long long x = 0;
-      if (p < e) x = __ldg(front + A.cols[p]);
+      if (p < e) {
+        const int4 c4 = *reinterpret_cast<const int4*>(A.cols + p);
+        const int32_t us[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (p + t >= s0 && p + t < e) x |= __ldg(front + us[t]);
+      }
       acc |= warp_or64(x);
-      if (lane == 0) k.ex += (unsigned long long)min((int64_t)32, e - j);
-      j += 32;
+      if (lane == 0) k.ex += (unsigned long long)(min(e, base + 128) - max(s0, base));
     }
     const unsigned long long nw = acc & need;
     if (lane == 0) {
@@ -397,33 +407,54 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
 
 // Writes the levels of the lanes in F.lanes for every original ID, and with
 // F.release clears those lanes' bits.
+// Levels of vertex v (original ID o) for the lanes in F.lanes, with at most
+// NP planes in use: the plane words are shifted right one lane at a time, so
+// every lane costs a few constant-shift operations per plane.
+template <int NP, class OffT>
+__device__ __forceinline__ void flush_vertex(const MsArgs<OffT>& A, const FlushArgs& F, int np, int64_t o, int64_t v,
+                                             int32_t* const* s_out, const int32_t* s_start) {
+  const unsigned long long s = A.seen[v];
+  const unsigned long long hit = s & F.lanes;
+  unsigned long long q[NP];
+#pragma unroll
+  for (int b = 0; b < NP; ++b) q[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n + v] : 0ull;
+  if (F.release && hit) {
+    A.seen[v] = s & ~F.lanes;
+#pragma unroll
+    for (int b = 0; b < NP; ++b)
+      if (b < np) A.planes[(int64_t)b * A.n + v] = q[b] & ~F.lanes;
+  }
+  // lanes unrolled: every bit position is a compile-time constant, and the
+  // lane test is uniform across the warp (F.lanes is the same for all threads)
+#pragma unroll
+  for (int i = 0; i < kMsLanes; ++i) {
+    if (!((F.lanes >> i) & 1ull)) continue;
+    int32_t lev = -1;
+    if ((hit >> i) & 1ull) {
+      unsigned T = 0;
+#pragma unroll
+      for (int b = 0; b < NP; ++b) T |= (unsigned)((q[b] >> i) & 1ull) << b;
+      lev = (int32_t)((T - (unsigned)s_start[i]) & kIterMask);
+    }
+    s_out[i][o] = lev;
+  }
+}
+
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs F) {
+  __shared__ int32_t* s_out[kMsLanes];
+  __shared__ int32_t s_start[kMsLanes];
+  if (threadIdx.x < kMsLanes) {
+    s_out[threadIdx.x] = F.out[threadIdx.x];
+    s_start[threadIdx.x] = F.start[threadIdx.x];
+  }
+  __syncthreads();
   const int np = A.ctl->n_planes;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = A.o2n ? A.o2n[o] : o;
-    const unsigned long long s = A.seen[v];
-    const unsigned long long hit = s & F.lanes;
-    unsigned long long pl[kMsPlanes];
-#pragma unroll
-    for (int b = 0; b < kMsPlanes; ++b) pl[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n + v] : 0ull;
-    unsigned long long lanes = F.lanes;
-    while (lanes) {
-      const int i = __ffsll((long long)lanes) - 1;
-      lanes &= lanes - 1;
-      int32_t lev = -1;
-      if ((hit >> i) & 1ull) {
-        unsigned T = 0;
-#pragma unroll
-        for (int b = 0; b < kMsPlanes; ++b) T |= (unsigned)((pl[b] >> i) & 1ull) << b;
-        lev = (int32_t)((T - (unsigned)F.start[i]) & kIterMask);
-      }
-      F.out[i][o] = lev;
-    }
-    if (F.release && hit) {
-      A.seen[v] = s & ~F.lanes;
-      for (int b = 0; b < np; ++b) A.planes[(int64_t)b * A.n + v] = pl[b] & ~F.lanes;
-    }
+    if (np <= 4) flush_vertex<4>(A, F, np, o, v, s_out, s_start);
+    else if (np <= 8) flush_vertex<8>(A, F, np, o, v, s_out, s_start);
+    else flush_vertex<16>(A, F, np, o, v, s_out, s_start);
   }
 }
 
@@ -531,20 +562,35 @@ int ms_build_graph(MsGroup* m) {
 
 template <class OffT>
 int ms_seed_impl(MsGroup* m, const SeedArgs& S) {
-  k_ms_seed<OffT><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), S);
+  k_ms_seed<OffT><<<1, kMsLanes, 0, m->stream>>>(ms_args<OffT>(m), S);
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
 
 template <class OffT>
-int ms_step_impl(MsGroup* m) {
+int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   k_ms_switch<OffT><<<1, 32, 0, m->stream>>>(A, 0, 0, 0);
-  int32_t hdr[5];
-  DOBFS_CUDA_TRY(cudaMemcpyAsync(hdr, m->ctl.ptr, sizeof(hdr), cudaMemcpyDeviceToHost, m->stream));
+  MsCtl c;
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(&c, m->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost, m->stream));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(m->stream));
-  if (hdr[4]) return DOBFS_OK;  // done: no live lane
-  return ms_launch_case<OffT>(m, hdr[2], m->stream);
+  if (after_switch) *after_switch = c;
+  if (c.done) return DOBFS_OK;  // no live lane
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (case_ms) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, m->stream);
+  }
+  const int rc = ms_launch_case<OffT>(m, c.step_case, m->stream);
+  if (case_ms) {
+    cudaEventRecord(e1, m->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(case_ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return rc;
 }
 
 template <class OffT>
@@ -622,7 +668,10 @@ int ms_group_seed(MsGroup* m, int count, const int32_t* lane, const int32_t* roo
   return m->g->off64 ? ms_seed_impl<int64_t>(m, S) : ms_seed_impl<int32_t>(m, S);
 }
 
-int ms_group_step(MsGroup* m) { return m->g->off64 ? ms_step_impl<int64_t>(m) : ms_step_impl<int32_t>(m); }
+int ms_group_step(MsGroup* m, MsCtl* after_switch, float* case_ms) {
+  return m->g->off64 ? ms_step_impl<int64_t>(m, after_switch, case_ms)
+                     : ms_step_impl<int32_t>(m, after_switch, case_ms);
+}
 
 int ms_group_run_to_end(MsGroup* m) {
   if (!m->exec) DOBFS_TRY(m->g->off64 ? ms_build_graph<int64_t>(m) : ms_build_graph<int32_t>(m));
@@ -685,6 +734,9 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
   const bool dev_out = is_device_ptr(level_out);
   if (!dev_out && !g->ms_stage.ptr)
     DOBFS_TRY(g->ms_stage.alloc(sizeof(int32_t) * (size_t)kMsLanes * (size_t)g->n, g->stream));
+  const bool host_loop = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
+  g->batch_trace.clear();
+  g->last_trace_batch = host_loop;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
   int32_t max_levels = 0;
   int64_t examined = 0;
@@ -694,7 +746,43 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     int32_t lanes[kMsLanes];
     for (int i = 0; i < cnt; ++i) lanes[i] = i;
     DOBFS_TRY(ms_group_seed(m, cnt, lanes, hroots.data() + b0));
-    DOBFS_TRY(ms_group_run_to_end(m));
+    if (host_loop) {
+      // host-driven levels, each timed (diagnostics); the trace keeps the first group
+      for (int guard = 0; guard < (1 << 16) + 2; ++guard) {
+        MsCtl c;
+        float ms_case = 0.f;
+        DOBFS_TRY(ms_group_step(m, &c, &ms_case));
+        if (c.done) break;
+        if (b0 == 0) {
+          dobfs_level_trace t;
+          memset(&t, 0, sizeof(t));
+          t.level = c.levels_run;
+          t.direction = c.dir;
+          t.n_frontier = c.n_f;
+          t.m_frontier = c.m_f;
+          t.m_unvisited = c.m_u;
+          t.edges_examined = c.examined;  // running total; differenced below
+          t.ms = ms_case;
+          t.ms_main = ms_case;
+          g->batch_trace.push_back(t);
+        }
+      }
+      if (b0 == 0 && !g->batch_trace.empty()) {
+        // edges_examined holds running totals taken before each step: turn them into per-step counts
+        MsCtl fin;
+        DOBFS_TRY(ms_group_read_ctl(m, &fin));
+        for (size_t i = 0; i < g->batch_trace.size(); ++i) {
+          const int64_t next_total = (i + 1 < g->batch_trace.size()) ? g->batch_trace[i + 1].edges_examined : fin.examined;
+          g->batch_trace[i].vertices_scanned = next_total;  // scratch
+        }
+        for (size_t i = 0; i < g->batch_trace.size(); ++i) {
+          g->batch_trace[i].edges_examined = g->batch_trace[i].vertices_scanned - g->batch_trace[i].edges_examined;
+          g->batch_trace[i].vertices_scanned = 0;
+        }
+      }
+    } else {
+      DOBFS_TRY(ms_group_run_to_end(m));
+    }
     int32_t* outp[kMsLanes];
     for (int i = 0; i < kMsLanes; ++i)
       outp[i] = i < cnt ? (dev_out ? level_out + (int64_t)(b0 + i) * g->n : g->ms_stage.as<int32_t>() + (int64_t)i * g->n)

@@ -61,7 +61,9 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o);
 int ms_group_seed(MsGroup* m, int count, const int32_t* lane, const int32_t* root);
 
 // One level from the host (the server's loop) or the whole loop as one graph launch.
-int ms_group_step(MsGroup* m);
+// after_switch / case_ms (nullable) receive the control block after the
+// direction switch and the device time of the step's kernels.
+int ms_group_step(MsGroup* m, MsCtl* after_switch, float* case_ms);
 int ms_group_run_to_end(MsGroup* m);
 
 // Writes levels of the lanes in `lanes` into out[i][n] (original IDs; -1 if

@@ -29,6 +29,7 @@ def main(argv=None) -> int:
     ap.add_argument("--modes", default="auto")
     ap.add_argument("--no-reindex", action="store_true")
     ap.add_argument("--json", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="also profile one batched run of this many roots")
     args = ap.parse_args(argv)
 
     import torch
@@ -77,6 +78,27 @@ def main(argv=None) -> int:
                           "bytes=%-12d %.3f ms (main %.3f ms, %.0f GB/s)" % (
                               p["level"], p["dir"], p["n_f"], p["m_f"], p["n_next"], p["examined"], p["scanned"],
                               p["alg_bytes"], p["ms"], p["ms_main"], p["gbs"]))
+    if args.batch > 0:
+        broots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0xBA7C, n, args.batch, deg > 0)
+        bout = torch.empty((args.batch, n), dtype=torch.int32, device="cuda")
+        rt = torch.from_numpy(np.ascontiguousarray(broots)).cuda()
+        for name in args.modes.split(","):
+            o = dobfs.make_opts(direction=modes[name])
+            st = dobfs.dobfs_run_batch(g.handle, rt, bout, opts=o, want_stats=True)
+            o.flags = dobfs.DOBFS_RUN_HOST_LOOP
+            sh = dobfs.dobfs_run_batch(g.handle, rt, bout, opts=o, want_stats=True)
+            tr = g.trace()
+            rec = {"mode": name, "batch": args.batch, "graph_ms": st.device_ms, "host_loop_ms": sh.device_ms,
+                   "levels": st.levels, "per_level": [
+                       {"level": t.level, "dir": "TD" if t.direction == 0 else "BU", "n_f": t.n_frontier,
+                        "m_f": t.m_frontier, "examined": t.edges_examined, "ms": t.ms} for t in tr]}
+            out.append(rec)
+            if not args.json:
+                print("batch %s, %d roots: graph %.3f ms (%.0f roots/s), host-driven %.3f ms, %d levels (first group)"
+                      % (name, args.batch, st.device_ms, args.batch / (st.device_ms * 1e-3), sh.device_ms, st.levels))
+                for p in rec["per_level"]:
+                    print("  L%-3d %s n_f=%-11d m_f=%-12d examined=%-12d %.3f ms" % (
+                        p["level"], p["dir"], p["n_f"], p["m_f"], p["examined"], p["ms"]))
     if args.json:
         print(json.dumps(out))
     torch.cuda.synchronize()
