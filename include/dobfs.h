@@ -236,6 +236,72 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
 int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out, int32_t* parent_out,
                     const dobfs_run_opts* opts, dobfs_run_stats* stats);
 
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * A query server over resident graphs with continuous batching: queries
+ * (graph, root) are admitted as they arrive into free lanes of 64-lane
+ * bit-parallel traversals already running on that graph (lanes join and
+ * leave at level boundaries), each graph's lane groups run on their own
+ * CUDA streams so work overlaps on the device, and a scheduler thread owned
+ * by the server drives the levels. Each level is a step of Algorithm 1 for
+ * all lanes of a group, top-down or bottom-up by the alpha/beta rule on the
+ * union of the lanes' frontiers. A query's result is the level array of a
+ * lone BFS from its root, whatever else is in flight. Levels only.
+ *
+ * Admission: a query takes a free lane of its graph and, if its output is
+ * host memory, a device staging buffer of n int32 counted against
+ * max_device_bytes; queries wait (in arrival order per graph) until both are
+ * available. More lane groups (up to max_groups_per_graph) are created while
+ * queries wait and the budget allows; each group holds 152 bytes per vertex
+ * plus records (see DESIGN notes).
+ */
+typedef struct dobfs_server dobfs_server;
+
+typedef struct {
+  int64_t max_device_bytes;     /* device-memory budget for lane groups and staging (0: 90% of free memory) */
+  int32_t groups_per_graph;     /* lane groups created per graph up front (default 1) */
+  int32_t max_groups_per_graph; /* upper bound on groups per graph (default 4) */
+  int32_t alpha, beta;          /* direction rule (defaults 14, 24) */
+  int32_t direction;            /* DOBFS_DIR_AUTO / TOPDOWN / BOTTOMUP / RANDOM */
+  int32_t pad;
+} dobfs_serve_opts;
+
+typedef struct {
+  int32_t status;      /* DOBFS_OK, or the error that failed the query */
+  int32_t levels;      /* levels of the query's BFS (max level + 1) */
+  int64_t submit_ns;   /* CLOCK_MONOTONIC time of dobfs_serve_submit */
+  int64_t admit_ns;    /* when the query took a lane */
+  int64_t done_ns;     /* when its output was complete and visible to poll */
+  int64_t latency_ns;  /* done_ns - submit_ns */
+} dobfs_query_result;
+
+typedef struct {
+  int64_t iterations;      /* scheduler passes that did work */
+  int64_t completed;       /* queries finished */
+  int64_t in_flight;       /* submitted and not yet polled */
+  int64_t groups_created;  /* lane groups added beyond the initial ones */
+  int64_t reserved_bytes;  /* device memory held against the budget */
+  int64_t budget_bytes;
+} dobfs_serve_stats;
+
+int dobfs_serve_opts_init(dobfs_serve_opts* opts);
+/* Starts the server (and its scheduler thread) on the current device. */
+int dobfs_serve_create(const dobfs_serve_opts* opts, dobfs_server** out);
+/* Adds a resident graph (it must outlive the server); *gid identifies it in submissions.
+ * DOBFS_ERR_BUSY if the budget cannot hold its initial lane groups. */
+int dobfs_serve_add_graph(dobfs_server* s, dobfs_graph* g, int32_t* gid);
+/* Queues the query (gid, root); level_out[n] (host or device) must stay valid until poll
+ * returns DOBFS_OK. parent_out must be NULL. Never blocks on the GPU. */
+int dobfs_serve_submit(dobfs_server* s, int32_t gid, int32_t root, int32_t* level_out, int32_t* parent_out,
+                       uint64_t* ticket);
+/* DOBFS_PENDING while the query runs; DOBFS_OK (result filled, ticket retired) once
+ * level_out is complete; an error status if the query failed (ticket retired). */
+int dobfs_serve_poll(dobfs_server* s, uint64_t ticket, dobfs_query_result* result);
+int dobfs_serve_get_stats(dobfs_server* s, dobfs_serve_stats* stats);
+/* Stops the scheduler and frees the server (unpolled queries are dropped). */
+int dobfs_serve_destroy(dobfs_server* s);
+
 /* Per-level record of the last run on a graph (ready after that run completed). */
 typedef struct {
   int32_t level;            /* level L being expanded (frontier = vertices at level L) */

@@ -135,15 +135,10 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   }
   const int prev_dir = c->fresh ? 0 : c->dir;
   c->fresh = 0;
-  if (c->live == 0 || c->n_f == 0) {
-    c->done = 1;
-    c->live = 0;
-    if (in_graph) {
-      cudaGraphSetConditional(h_case, kMsCaseNone);
-      cudaGraphSetConditional(h_while, 0);
-    }
-    return;
-  }
+  // done: no lane can discover anything; the server may still seed new lanes
+  // and run the step, so the direction is picked in any case
+  const bool done = (c->live == 0 || c->n_f == 0);
+  if (done) c->live = 0;
   int dir;
   switch (c->mode) {
     case DOBFS_DIR_TOPDOWN: dir = 0; break;
@@ -166,8 +161,15 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   }
   c->dir = dir;
   c->step_case = dir;
-  c->done = 0;
-  if (in_graph) cudaGraphSetConditional(h_case, (unsigned)dir);
+  c->done = done ? 1 : 0;
+  if (in_graph) {
+    if (done) {
+      cudaGraphSetConditional(h_case, kMsCaseNone);
+      cudaGraphSetConditional(h_while, 0);
+    } else {
+      cudaGraphSetConditional(h_case, (unsigned)dir);
+    }
+  }
 }
 
 template <class OffT>
@@ -412,17 +414,24 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
 // every lane costs a few constant-shift operations per plane.
 template <int NP, class OffT>
 __device__ __forceinline__ void flush_vertex(const MsArgs<OffT>& A, const FlushArgs& F, int np, int64_t o, int64_t v,
-                                             int32_t* const* s_out, const int32_t* s_start) {
+                                             int32_t* const* s_out, const int32_t* s_start,
+                                             unsigned long long& mu_back) {
   const unsigned long long s = A.seen[v];
   const unsigned long long hit = s & F.lanes;
   unsigned long long q[NP];
 #pragma unroll
   for (int b = 0; b < NP; ++b) q[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n + v] : 0ull;
   if (F.release && hit) {
+    // a frontier bit of a lane only sits on a vertex that lane reached: clear
+    // the released lanes in both frontier buffers too, so a lane reused later
+    // starts from a clean frontier even if no step ran in between
+    A.fb0[v] &= ~F.lanes;
+    A.fb1[v] &= ~F.lanes;
     A.seen[v] = s & ~F.lanes;
 #pragma unroll
     for (int b = 0; b < NP; ++b)
       if (b < np) A.planes[(int64_t)b * A.n + v] = q[b] & ~F.lanes;
+    if (!(s & ~F.lanes)) mu_back += (unsigned long long)A.firstdeg[v].y;  // unseen by every lane again
   }
   // lanes unrolled: every bit position is a compile-time constant, and the
   // lane test is uniform across the warp (F.lanes is the same for all threads)
@@ -450,11 +459,20 @@ __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs
   }
   __syncthreads();
   const int np = A.ctl->n_planes;
+  unsigned long long mu_back = 0;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = A.o2n ? A.o2n[o] : o;
-    if (np <= 4) flush_vertex<4>(A, F, np, o, v, s_out, s_start);
-    else if (np <= 8) flush_vertex<8>(A, F, np, o, v, s_out, s_start);
-    else flush_vertex<16>(A, F, np, o, v, s_out, s_start);
+    if (np <= 4) flush_vertex<4>(A, F, np, o, v, s_out, s_start, mu_back);
+    else if (np <= 8) flush_vertex<8>(A, F, np, o, v, s_out, s_start, mu_back);
+    else flush_vertex<16>(A, F, np, o, v, s_out, s_start, mu_back);
+  }
+  if (F.release) {
+    __shared__ unsigned long long sh[kThreads / 32];
+    mu_back = block_sum_u64(mu_back, sh);
+    if (threadIdx.x == 0) {
+      if (mu_back) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctl->m_u), mu_back);
+      if (blockIdx.x == 0) atomicAnd(&A.ctl->active, ~F.lanes);  // the lanes are free again
+    }
   }
 }
 
@@ -601,7 +619,23 @@ int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
   return DOBFS_OK;
 }
 
+template <class OffT>
+int ms_switch_async_impl(MsGroup* m, MsCtl* dst) {
+  k_ms_switch<OffT><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), 0, 0, 0);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(dst, m->ctl.ptr, sizeof(MsCtl), cudaMemcpyDeviceToHost, m->stream));
+  return DOBFS_OK;
+}
+
 }  // namespace
+
+int ms_group_switch_async(MsGroup* m, MsCtl* dst) {
+  return m->g->off64 ? ms_switch_async_impl<int64_t>(m, dst) : ms_switch_async_impl<int32_t>(m, dst);
+}
+
+int ms_group_case_async(MsGroup* m, int kase) {
+  return m->g->off64 ? ms_launch_case<int64_t>(m, kase, m->stream) : ms_launch_case<int32_t>(m, kase, m->stream);
+}
 
 int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out) {
   MsGroup* m = new (std::nothrow) MsGroup();

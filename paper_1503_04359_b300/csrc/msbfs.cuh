@@ -71,6 +71,12 @@ int ms_group_run_to_end(MsGroup* m);
 // are cleared and the lanes freed.
 int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_t* start, bool release);
 
+// Server loop pieces, all asynchronous on the group's stream: the direction
+// switch followed by a copy of the control block into `dst` (pinned host
+// memory), and the kernels of one step (0 top-down, 1 bottom-up).
+int ms_group_switch_async(MsGroup* m, MsCtl* dst);
+int ms_group_case_async(MsGroup* m, int kase);
+
 // Reads the control block (synchronises the group's stream).
 int ms_group_read_ctl(MsGroup* m, MsCtl* c);
 

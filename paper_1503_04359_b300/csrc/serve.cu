@@ -1,0 +1,508 @@
+// Query server: continuous batching of single-root BFS queries over several
+// resident graphs.
+//
+// Every added graph gets lane groups (64-lane bit-parallel traversals, see
+// msbfs.cu), each on its own CUDA stream, so the work of different graphs
+// and groups overlaps on the device. A scheduler thread runs the loop:
+//   1. launch the direction switch of every group that holds or awaits
+//      queries, with an asynchronous copy of its control block;
+//   2. for each group, once its copy has landed: lanes whose frontier is
+//      empty have finished; their levels are written into the queries'
+//      outputs (flush with release, which frees the lanes), then waiting
+//      queries of that graph are admitted into free lanes (seeded at the
+//      current iteration, so lanes join a traversal already in flight), and
+//      the kernels of the next level are launched;
+//   3. queries whose output copies have completed (CUDA events) become
+//      visible to dobfs_serve_poll.
+// Admission takes a free lane and, for queries whose output is host memory,
+// a device staging buffer of n int32 within the server's device-memory
+// budget; new groups are created while queries wait and the budget allows.
+// Every query's levels are those of a lone BFS from its root: lanes never
+// interact, so a result is the same alone and in any mix.
+#include <time.h>
+
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "msbfs.cuh"
+
+namespace dobfs {
+namespace {
+
+int64_t now_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
+enum QState { kQueued = 0, kRunning = 1, kFlushing = 2, kDone = 3, kFailed = 4 };
+
+struct Query {
+  uint64_t ticket = 0;
+  int32_t gid = 0;
+  int32_t root = 0;
+  int32_t* out = nullptr;
+  bool host_out = false;
+  int64_t t_submit = 0, t_admit = 0, t_done = 0;
+  int state = kQueued;
+  int status = DOBFS_PENDING;
+  int32_t start_iter = 0;
+  int32_t levels = 0;
+  DevBuf stage;  // device copy of the output when out is host memory
+  cudaEvent_t ev = nullptr;
+};
+
+struct Group {
+  MsGroup* ms = nullptr;
+  cudaStream_t stream = nullptr;
+  MsCtl* hctl = nullptr;  // pinned
+  Query* lane_q[kMsLanes] = {};
+  uint64_t busy = 0;  // lanes holding a query
+  bool switched = false;
+  int64_t bytes = 0;
+};
+
+struct Engine {
+  dobfs_graph* g = nullptr;
+  std::vector<Group*> groups;
+  std::deque<Query*> pending;
+};
+
+}  // namespace
+}  // namespace dobfs
+
+using namespace dobfs;
+
+struct dobfs_server {
+  dobfs_serve_opts opts;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread th;
+  bool stop = false;
+  std::vector<Engine*> engines;
+  std::deque<Query*> inbox;
+  std::unordered_map<uint64_t, Query*> queries;
+  std::vector<Query*> flushing;
+  uint64_t next_ticket = 1;
+  int64_t budget = 0;
+  int64_t reserved = 0;
+  int fatal = DOBFS_OK;
+  std::string fatal_msg;
+  int64_t iterations = 0, completed = 0, groups_created = 0;
+};
+
+namespace dobfs {
+namespace {
+
+int64_t group_bytes(const dobfs_graph* g) {
+  const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
+  return (int64_t)sizeof(uint64_t) * g->n * (3 + kMsPlanes) + (int64_t)sizeof(int2) * (n_cand + g->nnz / 1024 + 64) +
+         (int64_t)sizeof(int32_t) * g->n;
+}
+
+// Creates a lane group on engine e (scheduler thread, or add_graph).
+int add_group(dobfs_server* S, Engine* e) {
+  Group* G = new (std::nothrow) Group();
+  if (!G) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  int rc = DOBFS_OK;
+  if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&G->hctl, sizeof(MsCtl)) != cudaSuccess) {
+    rc = set_error(DOBFS_ERR_CUDA, "stream or pinned allocation failed");
+  }
+  if (rc == DOBFS_OK) rc = ms_group_create(e->g, G->stream, &G->ms);
+  if (rc == DOBFS_OK) {
+    dobfs_run_opts o;
+    dobfs_run_opts_init(&o);
+    o.alpha = S->opts.alpha;
+    o.beta = S->opts.beta;
+    o.direction = S->opts.direction;
+    rc = ms_group_reset(G->ms, o);
+  }
+  if (rc != DOBFS_OK) {
+    if (G->ms) ms_group_destroy(G->ms);
+    if (G->hctl) cudaFreeHost(G->hctl);
+    if (G->stream) cudaStreamDestroy(G->stream);
+    delete G;
+    return rc;
+  }
+  G->bytes = group_bytes(e->g);
+  e->groups.push_back(G);
+  return DOBFS_OK;
+}
+
+void fail_all(dobfs_server* S, int rc, const char* msg) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->fatal = rc;
+  S->fatal_msg = msg;
+  for (auto& kv : S->queries)
+    if (kv.second->state != kDone) {
+      kv.second->state = kFailed;
+      kv.second->status = rc;
+    }
+}
+
+// One pass of the scheduler over every group. Returns true if any group did work.
+bool schedule_once(dobfs_server* S) {
+  std::vector<Engine*> engines;  // add_graph may append concurrently: work on a copy
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    while (!S->inbox.empty()) {
+      Query* q = S->inbox.front();
+      S->inbox.pop_front();
+      S->engines[q->gid]->pending.push_back(q);
+    }
+    engines = S->engines;
+  }
+  bool work = false;
+  // 1. switches
+  for (Engine* e : engines)
+    for (Group* G : e->groups) {
+      G->switched = false;
+      if (G->busy || !e->pending.empty()) {
+        if (ms_group_switch_async(G->ms, G->hctl) != DOBFS_OK) {
+          fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+          return false;
+        }
+        G->switched = true;
+        work = true;
+      }
+    }
+  // 2. finish, admit, next level
+  for (Engine* e : engines) {
+    dobfs_graph* g = e->g;
+    for (Group* G : e->groups) {
+      if (!G->switched) continue;
+      if (cudaStreamSynchronize(G->stream) != cudaSuccess) {
+        fail_all(S, DOBFS_ERR_CUDA, "server stream failed");
+        return false;
+      }
+      const MsCtl c = *G->hctl;
+      const uint64_t finished = G->busy & ~c.live;
+      if (finished) {
+        int32_t* outs[kMsLanes] = {};
+        int32_t starts[kMsLanes] = {};
+        for (int i = 0; i < kMsLanes; ++i)
+          if ((finished >> i) & 1ull) {
+            Query* q = G->lane_q[i];
+            outs[i] = q->host_out ? q->stage.as<int32_t>() : q->out;
+            starts[i] = q->start_iter;
+          }
+        int rc = ms_group_flush(G->ms, finished, outs, starts, true);
+        for (int i = 0; i < kMsLanes && rc == DOBFS_OK; ++i)
+          if ((finished >> i) & 1ull) {
+            Query* q = G->lane_q[i];
+            if (q->host_out && cudaMemcpyAsync(q->out, q->stage.ptr, sizeof(int32_t) * (size_t)g->n,
+                                               cudaMemcpyDeviceToHost, G->stream) != cudaSuccess)
+              rc = DOBFS_ERR_CUDA;
+            q->levels = c.iter - q->start_iter;
+            if (rc == DOBFS_OK && cudaEventRecord(q->ev, G->stream) != cudaSuccess) rc = DOBFS_ERR_CUDA;
+            q->state = kFlushing;
+            G->lane_q[i] = nullptr;
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->flushing.push_back(q);
+          }
+        if (rc != DOBFS_OK) {
+          fail_all(S, rc, "flush failed");
+          return false;
+        }
+        G->busy &= ~finished;
+      }
+      // admission into free lanes
+      int32_t lanes[kMsLanes], roots[kMsLanes];
+      int k = 0;
+      uint64_t freel = ~G->busy;
+      while (freel && !e->pending.empty()) {
+        Query* q = e->pending.front();
+        const int64_t need = q->host_out ? (int64_t)sizeof(int32_t) * g->n : 0;
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          if (S->reserved + need > S->budget) break;  // waits for memory to free up
+          S->reserved += need;
+        }
+        if (need && q->stage.alloc((size_t)need, G->stream) != DOBFS_OK) {
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->reserved -= need;
+          break;
+        }
+        e->pending.pop_front();
+        const int lane = __builtin_ctzll(freel);
+        freel &= freel - 1;
+        q->start_iter = c.iter;
+        q->t_admit = now_ns();
+        q->state = kRunning;
+        G->lane_q[lane] = q;
+        G->busy |= 1ull << lane;
+        lanes[k] = lane;
+        roots[k] = q->root;
+        ++k;
+      }
+      if (k && ms_group_seed(G->ms, k, lanes, roots) != DOBFS_OK) {
+        fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+        return false;
+      }
+      if (c.live || k) {
+        if (ms_group_case_async(G->ms, c.step_case) != DOBFS_OK) {
+          fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+          return false;
+        }
+      }
+    }
+    // another group while queries wait, lanes are full and memory allows
+    bool all_full = true;
+    for (Group* G : e->groups) all_full = all_full && (~G->busy == 0);
+    if (!e->pending.empty() && all_full && (int)e->groups.size() < S->opts.max_groups_per_graph) {
+      const int64_t gb = group_bytes(g);
+      bool ok;
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ok = S->reserved + gb <= S->budget;
+        if (ok) S->reserved += gb;
+      }
+      if (ok) {
+        if (add_group(S, e) == DOBFS_OK) {
+          S->groups_created += 1;
+        } else {
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->reserved -= gb;
+        }
+      }
+    }
+  }
+  // 3. completions (staging buffers are released after the lock is dropped)
+  std::vector<DevBuf> to_free;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = 0; i < S->flushing.size();) {
+      Query* q = S->flushing[i];
+      const cudaError_t st = cudaEventQuery(q->ev);
+      if (st == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      q->t_done = now_ns();
+      q->state = (st == cudaSuccess) ? kDone : kFailed;
+      q->status = (st == cudaSuccess) ? DOBFS_OK : DOBFS_ERR_CUDA;
+      if (q->stage.ptr) {
+        S->reserved -= (int64_t)q->stage.bytes;
+        to_free.push_back(std::move(q->stage));
+      }
+      S->completed += 1;
+      S->flushing[i] = S->flushing.back();
+      S->flushing.pop_back();
+      work = true;
+    }
+  }
+  S->iterations += work ? 1 : 0;
+  return work;
+}
+
+void scheduler(dobfs_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop) break;
+      if (S->fatal != DOBFS_OK) {
+        S->cv.wait_for(lk, std::chrono::milliseconds(10));
+        continue;
+      }
+    }
+    const bool work = schedule_once(S);
+    if (!work) {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop) break;
+      if (S->inbox.empty() && S->flushing.empty()) S->cv.wait_for(lk, std::chrono::milliseconds(2));
+    }
+  }
+}
+
+}  // namespace
+}  // namespace dobfs
+
+extern "C" {
+
+int dobfs_serve_opts_init(dobfs_serve_opts* o) {
+  if (!o) return set_error(DOBFS_ERR_INVALID, "opts is NULL");
+  memset(o, 0, sizeof(*o));
+  o->max_device_bytes = 0;
+  o->groups_per_graph = 1;
+  o->max_groups_per_graph = 4;
+  o->alpha = 14;
+  o->beta = 24;
+  o->direction = DOBFS_DIR_AUTO;
+  return DOBFS_OK;
+}
+
+int dobfs_serve_create(const dobfs_serve_opts* opts, dobfs_server** out) {
+  clear_error();
+  if (!out) return set_error(DOBFS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  dobfs_serve_opts o;
+  dobfs_serve_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.groups_per_graph < 1 || o.max_groups_per_graph < o.groups_per_graph || o.alpha < 1 || o.beta < 1 ||
+      o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.max_device_bytes < 0)
+    return set_error(DOBFS_ERR_INVALID, "bad server options");
+  dobfs_server* S = new (std::nothrow) dobfs_server();
+  if (!S) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  S->opts = o;
+  cudaGetDevice(&S->device);
+  if (o.max_device_bytes > 0) {
+    S->budget = o.max_device_bytes;
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete S;
+      return set_error(DOBFS_ERR_CUDA, "cudaMemGetInfo failed");
+    }
+    S->budget = (int64_t)(0.9 * (double)fr);
+  }
+  S->th = std::thread(scheduler, S);
+  *out = S;
+  return DOBFS_OK;
+}
+
+int dobfs_serve_add_graph(dobfs_server* S, dobfs_graph* g, int32_t* gid) {
+  clear_error();
+  if (!S || !g || !gid) return set_error(DOBFS_ERR_INVALID, "NULL argument");
+  Engine* e = new (std::nothrow) Engine();
+  if (!e) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  e->g = g;
+  const int64_t gb = group_bytes(g) * S->opts.groups_per_graph;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->reserved + gb > S->budget) {
+      delete e;
+      return set_error(DOBFS_ERR_BUSY, "device-memory budget too small for the graph's lane groups");
+    }
+    S->reserved += gb;
+  }
+  for (int i = 0; i < S->opts.groups_per_graph; ++i) {
+    const int rc = add_group(S, e);
+    if (rc != DOBFS_OK) {
+      for (Group* G : e->groups) {
+        ms_group_destroy(G->ms);
+        cudaFreeHost(G->hctl);
+        cudaStreamDestroy(G->stream);
+        delete G;
+      }
+      delete e;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->reserved -= gb;
+      return rc;
+    }
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  *gid = (int32_t)S->engines.size();
+  S->engines.push_back(e);
+  return DOBFS_OK;
+}
+
+int dobfs_serve_submit(dobfs_server* S, int32_t gid, int32_t root, int32_t* level_out, int32_t* parent_out,
+                       uint64_t* ticket) {
+  clear_error();
+  if (!S || !level_out || !ticket) return set_error(DOBFS_ERR_INVALID, "server, level_out and ticket are required");
+  if (parent_out) return set_error(DOBFS_ERR_INVALID, "served queries return levels only (parent_out must be NULL)");
+  Query* q = new (std::nothrow) Query();
+  if (!q) return set_error(DOBFS_ERR_OOM, "host allocation failed");
+  q->host_out = !is_device_ptr(level_out);
+  if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete q;
+    return set_error(DOBFS_ERR_CUDA, "event creation failed");
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->fatal != DOBFS_OK) {
+    cudaEventDestroy(q->ev);
+    delete q;
+    return set_error(S->fatal, "server failed: %s", S->fatal_msg.c_str());
+  }
+  if (gid < 0 || gid >= (int32_t)S->engines.size()) {
+    cudaEventDestroy(q->ev);
+    delete q;
+    return set_error(DOBFS_ERR_INVALID, "unknown graph id %d", gid);
+  }
+  if (root < 0 || root >= S->engines[gid]->g->n) {
+    cudaEventDestroy(q->ev);
+    delete q;
+    return set_error(DOBFS_ERR_INVALID, "root %d out of range", root);
+  }
+  q->gid = gid;
+  q->root = root;
+  q->out = level_out;
+  q->t_submit = now_ns();
+  q->ticket = S->next_ticket++;
+  S->queries[q->ticket] = q;
+  S->inbox.push_back(q);
+  *ticket = q->ticket;
+  S->cv.notify_one();
+  return DOBFS_OK;
+}
+
+int dobfs_serve_poll(dobfs_server* S, uint64_t ticket, dobfs_query_result* res) {
+  if (!S) return set_error(DOBFS_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->queries.find(ticket);
+  if (it == S->queries.end()) return set_error(DOBFS_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+  Query* q = it->second;
+  if (q->state != kDone && q->state != kFailed) return DOBFS_PENDING;
+  if (res) {
+    res->status = q->status;
+    res->levels = q->levels;
+    res->submit_ns = q->t_submit;
+    res->admit_ns = q->t_admit;
+    res->done_ns = q->t_done;
+    res->latency_ns = q->t_done - q->t_submit;
+  }
+  const int st = q->status;
+  cudaEventDestroy(q->ev);
+  delete q;
+  S->queries.erase(it);
+  return st == DOBFS_OK ? DOBFS_OK : set_error(st, "query failed");
+}
+
+int dobfs_serve_get_stats(dobfs_server* S, dobfs_serve_stats* st) {
+  if (!S || !st) return set_error(DOBFS_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  st->iterations = S->iterations;
+  st->completed = S->completed;
+  st->in_flight = (int64_t)S->queries.size();
+  st->groups_created = S->groups_created;
+  st->reserved_bytes = S->reserved;
+  st->budget_bytes = S->budget;
+  return S->fatal;
+}
+
+int dobfs_serve_destroy(dobfs_server* S) {
+  if (!S) return DOBFS_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  for (Engine* e : S->engines) {
+    for (Group* G : e->groups) {
+      cudaStreamSynchronize(G->stream);
+      ms_group_destroy(G->ms);
+      cudaFreeHost(G->hctl);
+      cudaStreamDestroy(G->stream);
+      delete G;
+    }
+    delete e;
+  }
+  for (auto& kv : S->queries) {
+    cudaEventDestroy(kv.second->ev);
+    delete kv.second;
+  }
+  delete S;
+  return DOBFS_OK;
+}
+
+}  // extern "C"

@@ -71,6 +71,23 @@ class dobfs_level_trace(ctypes.Structure):
                 ("alg_bytes", ctypes.c_int64), ("ms", ctypes.c_float), ("ms_main", ctypes.c_float)]
 
 
+class dobfs_serve_opts(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_int64), ("groups_per_graph", ctypes.c_int32),
+                ("max_groups_per_graph", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class dobfs_query_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("levels", ctypes.c_int32), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64), ("latency_ns", ctypes.c_int64)]
+
+
+class dobfs_serve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("groups_created", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -103,6 +120,13 @@ def load() -> ctypes.CDLL:
         "dobfs_last_trace": (c_int, [G, ctypes.POINTER(dobfs_level_trace), i32, ctypes.POINTER(i32)]),
         "dobfs_run_static": (c_int, [vp, vp, i32, i32, vp, vp, vp]),
         "dobfs_run_batch": (c_int, [G, vp, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
+        "dobfs_serve_opts_init": (c_int, [ctypes.POINTER(dobfs_serve_opts)]),
+        "dobfs_serve_create": (c_int, [ctypes.POINTER(dobfs_serve_opts), ctypes.POINTER(vp)]),
+        "dobfs_serve_add_graph": (c_int, [vp, G, ctypes.POINTER(i32)]),
+        "dobfs_serve_submit": (c_int, [vp, i32, i32, vp, vp, ctypes.POINTER(u64)]),
+        "dobfs_serve_poll": (c_int, [vp, u64, ctypes.POINTER(dobfs_query_result)]),
+        "dobfs_serve_get_stats": (c_int, [vp, ctypes.POINTER(dobfs_serve_stats)]),
+        "dobfs_serve_destroy": (c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -272,6 +296,65 @@ def dobfs_run_batch(g: int, roots, level_out, parent_out=None, opts: dobfs_run_o
     _check(load().dobfs_run_batch(g, _ptr(roots), int(roots.shape[0]), _ptr(level_out), _ptr(parent_out),
                                   ctypes.byref(opts), ctypes.byref(st) if st is not None else None))
     return st
+
+
+def dobfs_run_opts_init() -> dobfs_run_opts:
+    o = dobfs_run_opts()
+    _check(load().dobfs_run_opts_init(ctypes.byref(o)))
+    return o
+
+
+def dobfs_serve_opts_init() -> dobfs_serve_opts:
+    o = dobfs_serve_opts()
+    _check(load().dobfs_serve_opts_init(ctypes.byref(o)))
+    return o
+
+
+def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 4,
+                    alpha: int = 14, beta: int = 24, direction: int = DOBFS_DIR_AUTO) -> dobfs_serve_opts:
+    o = dobfs_serve_opts()
+    _check(load().dobfs_serve_opts_init(ctypes.byref(o)))
+    o.max_device_bytes = max_device_bytes
+    o.groups_per_graph = groups_per_graph
+    o.max_groups_per_graph = max_groups_per_graph
+    o.alpha, o.beta, o.direction = alpha, beta, direction
+    return o
+
+
+def dobfs_serve_create(opts: dobfs_serve_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dobfs_serve_create(ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def dobfs_serve_add_graph(server: int, g: int) -> int:
+    gid = ctypes.c_int32()
+    _check(load().dobfs_serve_add_graph(server, g, ctypes.byref(gid)))
+    return gid.value
+
+
+def dobfs_serve_submit(server: int, gid: int, root: int, level_out, parent_out=None) -> int:
+    t = ctypes.c_uint64()
+    _check(load().dobfs_serve_submit(server, int(gid), int(root), _ptr(level_out), _ptr(parent_out),
+                                     ctypes.byref(t)))
+    return t.value
+
+
+def dobfs_serve_poll(server: int, ticket: int) -> dobfs_query_result | None:
+    """The result once the query is done, None while it is pending; raises if it failed."""
+    r = dobfs_query_result()
+    st = _check(load().dobfs_serve_poll(server, int(ticket), ctypes.byref(r)))
+    return None if st == DOBFS_PENDING else r
+
+
+def dobfs_serve_get_stats(server: int) -> dobfs_serve_stats:
+    st = dobfs_serve_stats()
+    _check(load().dobfs_serve_get_stats(server, ctypes.byref(st)))
+    return st
+
+
+def dobfs_serve_destroy(server: int) -> None:
+    _check(load().dobfs_serve_destroy(server))
 
 
 def dobfs_last_trace(g: int, max_levels: int = 4096) -> list[dobfs_level_trace]:

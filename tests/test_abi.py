@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_python_binding_has_same_names():
     for n in _declared():
-        if n in ("dobfs_set_allocator", "dobfs_last_error", "dobfs_run_opts_init"):
+        if n in ("dobfs_set_allocator", "dobfs_last_error"):
             continue
         assert hasattr(dobfs, n), n
 
