@@ -188,6 +188,86 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
     return res
 
 
+def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000, 5000, 10000, 20000, 50000),
+                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 60.0) -> dict:
+    """Open-loop serving: R-MAT graphs of the given scales resident, Poisson
+    arrivals (seeded exponential gaps) at each rate, graph ids uniform, roots
+    uniform over degree >= 1 vertices. Latency runs from the scheduled arrival
+    to the completion the server reports (CLOCK_MONOTONIC), so a harness that
+    falls behind its schedule is charged for it. Output buffers come from a
+    per-graph ring of device slots; the one-at-a-time baseline is the device
+    time of single-source runs (levels only) averaged over the same mix."""
+    graphs, pools, slots = [], [], []
+    per_graph_bytes = out_gb * 1e9 / len(scales)
+    base_ms = []
+    for sc in scales:
+        spec = inputs.rmat(sc)
+        g = dobfs.rmat_graph(spec, flags=dobfs.DOBFS_GRAPH_REINDEX)
+        deg = g.degrees()
+        pool = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0x5E7E, g.n, 1024, deg > 0)
+        k = int(max(16, min(1024, per_graph_bytes // (4 * g.n))))
+        slots.append(torch.empty((k, g.n), dtype=torch.int32, device="cuda"))
+        lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        ms = [g.run(int(r), lv, None, want_stats=True).device_ms for r in pool[:8]]
+        base_ms.append(float(np.mean(ms[2:])))
+        graphs.append(g)
+        pools.append(pool)
+    one_at_a_time_qps = 1000.0 / float(np.mean(base_ms))
+    srv = dobfs.dobfs_serve_create(dobfs.make_serve_opts())
+    col = dobfs.Collector()
+    res = {"workload": "rmat-s%s-ef16-reindex resident, gid uniform, Poisson arrivals" % "/".join(map(str, scales)),
+           "one_at_a_time": {"mean_device_ms_per_graph": base_ms, "qps": one_at_a_time_qps}, "rates": {}}
+    try:
+        gids = [dobfs.dobfs_serve_add_graph(srv, g.handle) for g in graphs]
+        for rate in rates:
+            n_q = int(max(200, min(max_queries, rate * seconds)))
+            rng = np.random.default_rng(0xA11CE + rate)
+            gaps = rng.exponential(1.0 / rate, n_q)
+            which = rng.integers(0, len(graphs), n_q)
+            ridx = rng.integers(0, 1024, n_q)
+            free = [list(range(s.shape[0])) for s in slots]
+            inflight = {}
+            lat = []
+            t0 = time.monotonic_ns() + 2_000_000
+            sched = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
+            i = 0
+            last_done = t0
+            while len(lat) < n_q:
+                now = time.monotonic_ns()
+                while i < n_q and sched[i] <= now:
+                    gi = int(which[i])
+                    if not free[gi]:
+                        break  # no output slot: the query waits, its latency still counts from sched[i]
+                    slot = free[gi].pop()
+                    t = dobfs.dobfs_serve_submit(srv, gids[gi], int(pools[gi][ridx[i]]), slots[gi][slot])
+                    inflight[t] = (gi, slot, int(sched[i]))
+                    i += 1
+                done = dobfs.dobfs_serve_collect(srv, col)
+                for t, r in done:
+                    gi, slot, sc_ns = inflight.pop(t)
+                    free[gi].append(slot)
+                    lat.append((r.done_ns - sc_ns) * 1e-6)
+                    last_done = max(last_done, r.done_ns)
+                if not done and (i >= n_q or sched[i] > time.monotonic_ns()):
+                    time.sleep(0.00005)
+            lat = np.asarray(lat)
+            span = (last_done - int(sched[0])) * 1e-9
+            res["rates"][str(rate)] = {"queries": n_q, "p50_ms": float(np.percentile(lat, 50)),
+                                       "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                                       "achieved_qps": n_q / span,
+                                       "vs_one_at_a_time": (n_q / span) / one_at_a_time_qps}
+        st = dobfs.dobfs_serve_get_stats(srv)
+        res["server"] = {"lane_groups_created": int(st.groups_created), "iterations": int(st.iterations)}
+    finally:
+        dobfs.dobfs_serve_destroy(srv)
+        for g in graphs:
+            g.close()
+        del slots
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args) -> None:
     ws, rank, _ = _dist()
     if rank != 0:
@@ -233,6 +313,8 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--batch-scale", type=int, default=24)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-BFS measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -375,8 +457,11 @@ def main() -> None:
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     batch = None
-    if not args.no_batch:
+    if not args.no_batch and ws == 1:
         batch = measure_batch(torch, inputs, dobfs, args.batch_scale)
+    serve = None
+    if not args.no_serve and ws == 1:
+        serve = measure_serve(torch, inputs, dobfs, seconds=args.serve_seconds)
 
     if rank != 0:
         return
@@ -422,6 +507,8 @@ def main() -> None:
         result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if batch is not None:
         result["batch"] = batch
+    if serve is not None:
+        result["serve"] = serve
     print(json.dumps(result))
 
 

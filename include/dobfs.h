@@ -249,7 +249,11 @@ int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32
  * union of the lanes' frontiers. A query's result is the level array of a
  * lone BFS from its root, whatever else is in flight. Levels only.
  *
- * Admission: a query takes a free lane of its graph and, if its output is
+ * Lanes of a group form cohorts: an idle group starts one with the queries
+ * waiting for its graph, and later arrivals join it only within join_window
+ * levels of its start (while the levels are light), so the wide middle
+ * levels of its lanes coincide; other arrivals go to the graph's other
+ * groups. Admission: a query takes a free lane of its graph and, if its output is
  * host memory, a device staging buffer of n int32 counted against
  * max_device_bytes; queries wait (in arrival order per graph) until both are
  * available. More lane groups (up to max_groups_per_graph) are created while
@@ -261,10 +265,16 @@ typedef struct dobfs_server dobfs_server;
 typedef struct {
   int64_t max_device_bytes;     /* device-memory budget for lane groups and staging (0: 90% of free memory) */
   int32_t groups_per_graph;     /* lane groups created per graph up front (default 1) */
-  int32_t max_groups_per_graph; /* upper bound on groups per graph (default 4) */
+  int32_t max_groups_per_graph; /* upper bound on groups per graph (default 2) */
   int32_t alpha, beta;          /* direction rule (defaults 14, 24) */
   int32_t direction;            /* DOBFS_DIR_AUTO / TOPDOWN / BOTTOMUP / RANDOM */
-  int32_t pad;
+  int32_t admit_div;            /* a busy group admits new queries only at levels whose union frontier
+                                   n_f satisfies n_f * admit_div < n (0: at every level; default 64) */
+  int32_t join_window;          /* ... and only within this many levels of its cohort's start; an idle
+                                   group always admits (default 1; large values: join at any light level) */
+  int32_t flush_delay;          /* finished lanes of a group are written out together when no lane is
+                                   left running, or once the oldest has waited this many levels
+                                   (default 3; 0: at once) */
 } dobfs_serve_opts;
 
 typedef struct {
@@ -298,6 +308,10 @@ int dobfs_serve_submit(dobfs_server* s, int32_t gid, int32_t root, int32_t* leve
 /* DOBFS_PENDING while the query runs; DOBFS_OK (result filled, ticket retired) once
  * level_out is complete; an error status if the query failed (ticket retired). */
 int dobfs_serve_poll(dobfs_server* s, uint64_t ticket, dobfs_query_result* result);
+/* Retires up to max_results finished queries in completion order without naming them:
+ * tickets[i] and results[i] for i < *n_out (for load generators that track many tickets). */
+int dobfs_serve_collect(dobfs_server* s, uint64_t* tickets, dobfs_query_result* results, int32_t max_results,
+                        int32_t* n_out);
 int dobfs_serve_get_stats(dobfs_server* s, dobfs_serve_stats* stats);
 /* Stops the scheduler and frees the server (unpolled queries are dropped). */
 int dobfs_serve_destroy(dobfs_server* s);

@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -64,6 +65,9 @@ struct Group {
   MsCtl* hctl = nullptr;  // pinned
   Query* lane_q[kMsLanes] = {};
   uint64_t busy = 0;  // lanes holding a query
+  int32_t cohort_iter = 0;  // iteration at which the group last went from idle to busy
+  uint64_t finished = 0;    // lanes done but not yet flushed
+  int32_t finish_iter[kMsLanes] = {};
   bool switched = false;
   int64_t bytes = 0;
 };
@@ -90,6 +94,7 @@ struct dobfs_server {
   std::deque<Query*> inbox;
   std::unordered_map<uint64_t, Query*> queries;
   std::vector<Query*> flushing;
+  std::list<Query*> done_list;  // finished and not yet polled or collected
   uint64_t next_ticket = 1;
   int64_t budget = 0;
   int64_t reserved = 0;
@@ -184,7 +189,17 @@ bool schedule_once(dobfs_server* S) {
         return false;
       }
       const MsCtl c = *G->hctl;
-      const uint64_t finished = G->busy & ~c.live;
+      // lanes whose frontier emptied; each flush is a pass over the whole
+      // graph, so finished lanes are flushed together: when the group has no
+      // live lane left, or once the oldest has waited flush_delay levels
+      const uint64_t done_now = G->busy & ~c.live & ~G->finished;
+      for (int i = 0; i < kMsLanes; ++i)
+        if ((done_now >> i) & 1ull) G->finish_iter[i] = c.iter;
+      G->finished |= done_now;
+      bool flush_now = G->finished && (c.live == 0 || S->opts.flush_delay <= 0);
+      for (int i = 0; i < kMsLanes && G->finished && !flush_now; ++i)
+        if (((G->finished >> i) & 1ull) && c.iter - G->finish_iter[i] >= S->opts.flush_delay) flush_now = true;
+      const uint64_t finished = flush_now ? G->finished : 0ull;
       if (finished) {
         int32_t* outs[kMsLanes] = {};
         int32_t starts[kMsLanes] = {};
@@ -201,7 +216,7 @@ bool schedule_once(dobfs_server* S) {
             if (q->host_out && cudaMemcpyAsync(q->out, q->stage.ptr, sizeof(int32_t) * (size_t)g->n,
                                                cudaMemcpyDeviceToHost, G->stream) != cudaSuccess)
               rc = DOBFS_ERR_CUDA;
-            q->levels = c.iter - q->start_iter;
+            q->levels = G->finish_iter[i] - q->start_iter;
             if (rc == DOBFS_OK && cudaEventRecord(q->ev, G->stream) != cudaSuccess) rc = DOBFS_ERR_CUDA;
             q->state = kFlushing;
             G->lane_q[i] = nullptr;
@@ -213,11 +228,20 @@ bool schedule_once(dobfs_server* S) {
           return false;
         }
         G->busy &= ~finished;
+        G->finished = 0;
       }
-      // admission into free lanes
+      // admission into free lanes: an idle group starts a new cohort; a busy
+      // group takes more lanes only within join_window levels of its
+      // cohort's start and at light levels (small union frontier). Lanes of
+      // one cohort then reach their wide middle levels together, so one
+      // bottom-up step serves all of them; queries arriving later go to
+      // another group of the graph (created while the budget allows).
       int32_t lanes[kMsLanes], roots[kMsLanes];
       int k = 0;
-      uint64_t freel = ~G->busy;
+      if (G->busy == 0) G->cohort_iter = c.iter;
+      const bool light = S->opts.admit_div <= 0 || c.n_f * (int64_t)S->opts.admit_div < g->n;
+      const bool can_join = (G->busy == 0) || (light && c.iter - G->cohort_iter <= S->opts.join_window);
+      uint64_t freel = can_join ? ~G->busy : 0ull;
       while (freel && !e->pending.empty()) {
         Query* q = e->pending.front();
         const int64_t need = q->host_out ? (int64_t)sizeof(int32_t) * g->n : 0;
@@ -255,8 +279,13 @@ bool schedule_once(dobfs_server* S) {
       }
     }
     // another group while queries wait, lanes are full and memory allows
-    bool all_full = true;
-    for (Group* G : e->groups) all_full = all_full && (~G->busy == 0);
+    bool all_full = true;  // no group can take a waiting query now
+    for (Group* G : e->groups) {
+      const bool light = S->opts.admit_div <= 0 || G->hctl->n_f * (int64_t)S->opts.admit_div < g->n;
+      const bool can_join =
+          (G->busy == 0) || (light && G->hctl->iter - G->cohort_iter <= S->opts.join_window && ~G->busy != 0);
+      all_full = all_full && !can_join;
+    }
     if (!e->pending.empty() && all_full && (int)e->groups.size() < S->opts.max_groups_per_graph) {
       const int64_t gb = group_bytes(g);
       bool ok;
@@ -294,6 +323,7 @@ bool schedule_once(dobfs_server* S) {
         to_free.push_back(std::move(q->stage));
       }
       S->completed += 1;
+      S->done_list.push_back(q);
       S->flushing[i] = S->flushing.back();
       S->flushing.pop_back();
       work = true;
@@ -333,10 +363,13 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   memset(o, 0, sizeof(*o));
   o->max_device_bytes = 0;
   o->groups_per_graph = 1;
-  o->max_groups_per_graph = 4;
+  o->max_groups_per_graph = 2;
   o->alpha = 14;
   o->beta = 24;
   o->direction = DOBFS_DIR_AUTO;
+  o->admit_div = 64;
+  o->join_window = 1;
+  o->flush_delay = 3;
   return DOBFS_OK;
 }
 
@@ -348,7 +381,8 @@ int dobfs_serve_create(const dobfs_serve_opts* opts, dobfs_server** out) {
   dobfs_serve_opts_init(&o);
   if (opts) o = *opts;
   if (o.groups_per_graph < 1 || o.max_groups_per_graph < o.groups_per_graph || o.alpha < 1 || o.beta < 1 ||
-      o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.max_device_bytes < 0)
+      o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.max_device_bytes < 0 || o.admit_div < 0 ||
+      o.join_window < 0 || o.flush_delay < 0)
     return set_error(DOBFS_ERR_INVALID, "bad server options");
   dobfs_server* S = new (std::nothrow) dobfs_server();
   if (!S) return set_error(DOBFS_ERR_OOM, "host allocation failed");
@@ -461,10 +495,35 @@ int dobfs_serve_poll(dobfs_server* S, uint64_t ticket, dobfs_query_result* res) 
     res->latency_ns = q->t_done - q->t_submit;
   }
   const int st = q->status;
+  S->done_list.remove(q);
   cudaEventDestroy(q->ev);
   delete q;
   S->queries.erase(it);
   return st == DOBFS_OK ? DOBFS_OK : set_error(st, "query failed");
+}
+
+int dobfs_serve_collect(dobfs_server* S, uint64_t* tickets, dobfs_query_result* results, int32_t max_results,
+                        int32_t* n_out) {
+  if (!S || !tickets || !results || !n_out || max_results < 0) return set_error(DOBFS_ERR_INVALID, "bad arguments");
+  std::lock_guard<std::mutex> lk(S->mu);
+  int32_t n = 0;
+  for (auto it = S->done_list.begin(); it != S->done_list.end() && n < max_results;) {
+    Query* q = *it;
+    tickets[n] = q->ticket;
+    results[n].status = q->status;
+    results[n].levels = q->levels;
+    results[n].submit_ns = q->t_submit;
+    results[n].admit_ns = q->t_admit;
+    results[n].done_ns = q->t_done;
+    results[n].latency_ns = q->t_done - q->t_submit;
+    ++n;
+    S->queries.erase(q->ticket);
+    cudaEventDestroy(q->ev);
+    delete q;
+    it = S->done_list.erase(it);
+  }
+  *n_out = n;
+  return DOBFS_OK;
 }
 
 int dobfs_serve_get_stats(dobfs_server* S, dobfs_serve_stats* st) {

@@ -74,7 +74,8 @@ class dobfs_level_trace(ctypes.Structure):
 class dobfs_serve_opts(ctypes.Structure):
     _fields_ = [("max_device_bytes", ctypes.c_int64), ("groups_per_graph", ctypes.c_int32),
                 ("max_groups_per_graph", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
-                ("direction", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("direction", ctypes.c_int32), ("admit_div", ctypes.c_int32), ("join_window", ctypes.c_int32),
+                ("flush_delay", ctypes.c_int32)]
 
 
 class dobfs_query_result(ctypes.Structure):
@@ -126,6 +127,8 @@ def load() -> ctypes.CDLL:
         "dobfs_serve_submit": (c_int, [vp, i32, i32, vp, vp, ctypes.POINTER(u64)]),
         "dobfs_serve_poll": (c_int, [vp, u64, ctypes.POINTER(dobfs_query_result)]),
         "dobfs_serve_get_stats": (c_int, [vp, ctypes.POINTER(dobfs_serve_stats)]),
+        "dobfs_serve_collect": (c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(dobfs_query_result), i32,
+                                        ctypes.POINTER(i32)]),
         "dobfs_serve_destroy": (c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -310,10 +313,18 @@ def dobfs_serve_opts_init() -> dobfs_serve_opts:
     return o
 
 
-def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 4,
-                    alpha: int = 14, beta: int = 24, direction: int = DOBFS_DIR_AUTO) -> dobfs_serve_opts:
+def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 2,
+                    alpha: int = 14, beta: int = 24, direction: int = DOBFS_DIR_AUTO,
+                    admit_div: int | None = None, join_window: int | None = None,
+                    flush_delay: int | None = None) -> dobfs_serve_opts:
     o = dobfs_serve_opts()
     _check(load().dobfs_serve_opts_init(ctypes.byref(o)))
+    if admit_div is not None:
+        o.admit_div = admit_div
+    if join_window is not None:
+        o.join_window = join_window
+    if flush_delay is not None:
+        o.flush_delay = flush_delay
     o.max_device_bytes = max_device_bytes
     o.groups_per_graph = groups_per_graph
     o.max_groups_per_graph = max_groups_per_graph
@@ -345,6 +356,21 @@ def dobfs_serve_poll(server: int, ticket: int) -> dobfs_query_result | None:
     r = dobfs_query_result()
     st = _check(load().dobfs_serve_poll(server, int(ticket), ctypes.byref(r)))
     return None if st == DOBFS_PENDING else r
+
+
+class Collector:
+    """Reusable buffers for dobfs_serve_collect."""
+
+    def __init__(self, cap: int = 4096):
+        self.cap = cap
+        self.tickets = (ctypes.c_uint64 * cap)()
+        self.results = (dobfs_query_result * cap)()
+        self.n = ctypes.c_int32()
+
+
+def dobfs_serve_collect(server: int, col: Collector) -> list[tuple[int, dobfs_query_result]]:
+    _check(load().dobfs_serve_collect(server, col.tickets, col.results, col.cap, ctypes.byref(col.n)))
+    return [(col.tickets[i], col.results[i]) for i in range(col.n.value)]
 
 
 def dobfs_serve_get_stats(server: int) -> dobfs_serve_stats:
