@@ -189,7 +189,7 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
 
 
 def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000, 5000, 10000, 20000, 50000),
-                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 60.0) -> dict:
+                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 60.0, serve_opts=None) -> dict:
     """Open-loop serving: R-MAT graphs of the given scales resident, Poisson
     arrivals (seeded exponential gaps) at each rate, graph ids uniform, roots
     uniform over degree >= 1 vertices. Latency runs from the scheduled arrival
@@ -213,7 +213,7 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
         graphs.append(g)
         pools.append(pool)
     one_at_a_time_qps = 1000.0 / float(np.mean(base_ms))
-    srv = dobfs.dobfs_serve_create(dobfs.make_serve_opts())
+    srv = dobfs.dobfs_serve_create(serve_opts if serve_opts is not None else dobfs.make_serve_opts())
     col = dobfs.Collector()
     res = {"workload": "rmat-s%s-ef16-reindex resident, gid uniform, Poisson arrivals" % "/".join(map(str, scales)),
            "one_at_a_time": {"mean_device_ms_per_graph": base_ms, "qps": one_at_a_time_qps}, "rates": {}}

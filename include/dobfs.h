@@ -253,7 +253,10 @@ int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32
  * waiting for its graph, and later arrivals join it only within join_window
  * levels of its start (while the levels are light), so the wide middle
  * levels of its lanes coincide; other arrivals go to the graph's other
- * groups. Admission: a query takes a free lane of its graph and, if its output is
+ * groups. Under light load (a graph with at most ss_max waiting queries) a
+ * query instead runs as a single-source BFS on that graph's own stream, which
+ * answers one query faster than a lane group does. The server expects to be
+ * the only user of its graphs while it runs. Admission: a query takes a free lane of its graph and, if its output is
  * host memory, a device staging buffer of n int32 counted against
  * max_device_bytes; queries wait (in arrival order per graph) until both are
  * available. More lane groups (up to max_groups_per_graph) are created while
@@ -275,6 +278,12 @@ typedef struct {
   int32_t flush_delay;          /* finished lanes of a group are written out together when no lane is
                                    left running, or once the oldest has waited this many levels
                                    (default 3; 0: at once) */
+  int32_t gather_us;            /* an idle group starts a cohort when 64 queries wait or the oldest has
+                                   waited this long (default 2000 us; 0: at once) */
+  int32_t ss_max;               /* while at most this many queries of a graph wait, they run as single-
+                                   source BFS (dobfs_run) on the graph's own stream instead (device
+                                   outputs only; default 2; 0: never) */
+  int32_t ss_backlog;           /* ... as long as fewer than this many are already queued there (default 4) */
 } dobfs_serve_opts;
 
 typedef struct {

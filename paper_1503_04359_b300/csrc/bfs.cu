@@ -1071,9 +1071,17 @@ int graph_alloc_workspace(dobfs_graph* g) {
   return DOBFS_OK;
 }
 
+int graph_levels_async(dobfs_graph* g, int32_t* dst, cudaStream_t s) {
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(dst, &g->ctl.as<BfsCtl>()->n_levels, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  return DOBFS_OK;
+}
+
 void graph_release(dobfs_graph* g) {
+  // wait through the graph's own event: the stream of the last run may no
+  // longer exist (a caller's or the server's stream)
   if (g->stream) cudaStreamSynchronize(g->stream);
-  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  if (g->ev_done) cudaEventSynchronize(g->ev_done);
+  g->last_stream = nullptr;
   ms_group_destroy(g->ms);
   g->ms = nullptr;
   if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);

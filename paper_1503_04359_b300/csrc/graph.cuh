@@ -105,6 +105,8 @@ struct dobfs_graph {
 namespace dobfs {
 
 int graph_alloc_workspace(dobfs_graph* g);
+// Copies the level count of the last single-source run on g to dst (pinned host memory), on s.
+int graph_levels_async(dobfs_graph* g, int32_t* dst, cudaStream_t s);
 void graph_release(dobfs_graph* g);
 
 // builds g's CSR from n_keys edge keys (row<<bits | col, or kSentinelKey),

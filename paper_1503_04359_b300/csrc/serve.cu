@@ -44,6 +44,8 @@ int64_t now_ns() {
 
 enum QState { kQueued = 0, kRunning = 1, kFlushing = 2, kDone = 3, kFailed = 4 };
 
+struct Engine;
+
 struct Query {
   uint64_t ticket = 0;
   int32_t gid = 0;
@@ -57,6 +59,8 @@ struct Query {
   int32_t levels = 0;
   DevBuf stage;  // device copy of the output when out is host memory
   cudaEvent_t ev = nullptr;
+  int32_t* levels_h = nullptr;  // pinned slot the single-source path writes the level count to
+  Engine* ss_engine = nullptr;  // set while the query runs on its engine's single-source path
 };
 
 struct Group {
@@ -65,10 +69,11 @@ struct Group {
   MsCtl* hctl = nullptr;  // pinned
   Query* lane_q[kMsLanes] = {};
   uint64_t busy = 0;  // lanes holding a query
+  bool in_flight = false;  // a switch and its control-block copy are queued
+  cudaEvent_t ctl_ev = nullptr;
   int32_t cohort_iter = 0;  // iteration at which the group last went from idle to busy
   uint64_t finished = 0;    // lanes done but not yet flushed
   int32_t finish_iter[kMsLanes] = {};
-  bool switched = false;
   int64_t bytes = 0;
 };
 
@@ -76,7 +81,13 @@ struct Engine {
   dobfs_graph* g = nullptr;
   std::vector<Group*> groups;
   std::deque<Query*> pending;
+  // single-source path: lone queries run back to back as dobfs_run on this stream
+  cudaStream_t ss_stream = nullptr;
+  int32_t* ss_levels = nullptr;  // pinned ring of level counts
+  int ss_next = 0;
+  int ss_inflight = 0;
 };
+constexpr int kSsRing = 1024;
 
 }  // namespace
 }  // namespace dobfs
@@ -101,6 +112,7 @@ struct dobfs_server {
   int fatal = DOBFS_OK;
   std::string fatal_msg;
   int64_t iterations = 0, completed = 0, groups_created = 0;
+  bool waiting_gpu = false;  // scheduler thread only: some group's switch is still running
 };
 
 namespace dobfs {
@@ -118,7 +130,8 @@ int add_group(dobfs_server* S, Engine* e) {
   if (!G) return set_error(DOBFS_ERR_OOM, "host allocation failed");
   int rc = DOBFS_OK;
   if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost((void**)&G->hctl, sizeof(MsCtl)) != cudaSuccess) {
+      cudaMallocHost((void**)&G->hctl, sizeof(MsCtl)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&G->ctl_ev, cudaEventDisableTiming) != cudaSuccess) {
     rc = set_error(DOBFS_ERR_CUDA, "stream or pinned allocation failed");
   }
   if (rc == DOBFS_OK) rc = ms_group_create(e->g, G->stream, &G->ms);
@@ -133,6 +146,7 @@ int add_group(dobfs_server* S, Engine* e) {
   if (rc != DOBFS_OK) {
     if (G->ms) ms_group_destroy(G->ms);
     if (G->hctl) cudaFreeHost(G->hctl);
+    if (G->ctl_ev) cudaEventDestroy(G->ctl_ev);
     if (G->stream) cudaStreamDestroy(G->stream);
     delete G;
     return rc;
@@ -166,28 +180,77 @@ bool schedule_once(dobfs_server* S) {
     engines = S->engines;
   }
   bool work = false;
-  // 1. switches
-  for (Engine* e : engines)
-    for (Group* G : e->groups) {
-      G->switched = false;
-      if (G->busy || !e->pending.empty()) {
-        if (ms_group_switch_async(G->ms, G->hctl) != DOBFS_OK) {
-          fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
-          return false;
-        }
-        G->switched = true;
-        work = true;
+  S->waiting_gpu = false;
+  // Light load: a few waiting queries (device outputs) run as single-source
+  // BFS on the engine's own stream, back to back with no host wait, as long
+  // as that path's backlog is short; a longer queue is left to the lane
+  // groups, whose cohorts amortise a traversal over many queries.
+  for (Engine* e : engines) {
+    while (!e->pending.empty() && (int)e->pending.size() <= S->opts.ss_max && e->ss_inflight < S->opts.ss_backlog &&
+           !e->pending.front()->host_out) {
+      Query* q = e->pending.front();
+      e->pending.pop_front();
+      dobfs_run_opts o;
+      dobfs_run_opts_init(&o);
+      o.alpha = S->opts.alpha;
+      o.beta = S->opts.beta;
+      o.stream = (void*)e->ss_stream;
+      int rc = dobfs_run(e->g, q->root, q->out, nullptr, &o, nullptr);
+      q->levels_h = e->ss_levels + (e->ss_next++ % kSsRing);
+      if (rc == DOBFS_OK) rc = graph_levels_async(e->g, q->levels_h, e->ss_stream);
+      if (rc == DOBFS_OK && cudaEventRecord(q->ev, e->ss_stream) != cudaSuccess) rc = DOBFS_ERR_CUDA;
+      if (rc != DOBFS_OK) {
+        fail_all(S, rc, dobfs_last_error());
+        return false;
       }
+      q->t_admit = now_ns();
+      q->state = kFlushing;
+      q->ss_engine = e;
+      e->ss_inflight += 1;
+      work = true;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->flushing.push_back(q);
     }
-  // 2. finish, admit, next level
+  }
+  // Each group advances on its own: a group whose control block has landed
+  // (its event has fired) is finished, admitted and relaunched; the others
+  // are left running. A group's next switch is queued right behind its
+  // level kernels, so its stream never waits for the host.
   for (Engine* e : engines) {
     dobfs_graph* g = e->g;
     for (Group* G : e->groups) {
-      if (!G->switched) continue;
-      if (cudaStreamSynchronize(G->stream) != cudaSuccess) {
+      if (!G->in_flight) {
+        if (!G->busy) {
+          // an idle group starts a cohort once a full group of queries waits or
+          // the oldest waiting query has waited gather_us
+          if (e->pending.empty()) continue;
+          const bool full = e->pending.size() >= (size_t)kMsLanes;
+          const bool old = now_ns() - e->pending.front()->t_submit >= (int64_t)S->opts.gather_us * 1000;
+          if (!full && !old) {
+            S->waiting_gpu = true;  // poll again shortly
+            continue;
+          }
+        }
+        if (ms_group_switch_async(G->ms, G->hctl) != DOBFS_OK ||
+            cudaEventRecord(G->ctl_ev, G->stream) != cudaSuccess) {
+          fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+          return false;
+        }
+        G->in_flight = true;
+        work = true;
+        continue;
+      }
+      const cudaError_t evs = cudaEventQuery(G->ctl_ev);
+      if (evs == cudaErrorNotReady) {
+        S->waiting_gpu = true;
+        continue;
+      }
+      if (evs != cudaSuccess) {
         fail_all(S, DOBFS_ERR_CUDA, "server stream failed");
         return false;
       }
+      G->in_flight = false;
+      work = true;
       const MsCtl c = *G->hctl;
       // lanes whose frontier emptied; each flush is a pass over the whole
       // graph, so finished lanes are flushed together: when the group has no
@@ -277,6 +340,14 @@ bool schedule_once(dobfs_server* S) {
           return false;
         }
       }
+      if (G->busy || !e->pending.empty()) {  // next level's switch, queued behind the kernels
+        if (ms_group_switch_async(G->ms, G->hctl) != DOBFS_OK ||
+            cudaEventRecord(G->ctl_ev, G->stream) != cudaSuccess) {
+          fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+          return false;
+        }
+        G->in_flight = true;
+      }
     }
     // another group while queries wait, lanes are full and memory allows
     bool all_full = true;  // no group can take a waiting query now
@@ -317,6 +388,11 @@ bool schedule_once(dobfs_server* S) {
       }
       q->t_done = now_ns();
       q->state = (st == cudaSuccess) ? kDone : kFailed;
+      if (q->ss_engine) {
+        q->levels = *q->levels_h;
+        q->ss_engine->ss_inflight -= 1;
+        q->ss_engine = nullptr;
+      }
       q->status = (st == cudaSuccess) ? DOBFS_OK : DOBFS_ERR_CUDA;
       if (q->stage.ptr) {
         S->reserved -= (int64_t)q->stage.bytes;
@@ -346,6 +422,10 @@ void scheduler(dobfs_server* S) {
     }
     const bool work = schedule_once(S);
     if (!work) {
+      if (S->waiting_gpu) {  // some group's level is running: poll again shortly
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        continue;
+      }
       std::unique_lock<std::mutex> lk(S->mu);
       if (S->stop) break;
       if (S->inbox.empty() && S->flushing.empty()) S->cv.wait_for(lk, std::chrono::milliseconds(2));
@@ -370,6 +450,9 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   o->admit_div = 64;
   o->join_window = 1;
   o->flush_delay = 3;
+  o->gather_us = 2000;
+  o->ss_max = 2;
+  o->ss_backlog = 4;
   return DOBFS_OK;
 }
 
@@ -382,7 +465,7 @@ int dobfs_serve_create(const dobfs_serve_opts* opts, dobfs_server** out) {
   if (opts) o = *opts;
   if (o.groups_per_graph < 1 || o.max_groups_per_graph < o.groups_per_graph || o.alpha < 1 || o.beta < 1 ||
       o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.max_device_bytes < 0 || o.admit_div < 0 ||
-      o.join_window < 0 || o.flush_delay < 0)
+      o.join_window < 0 || o.flush_delay < 0 || o.gather_us < 0 || o.ss_max < 0 || o.ss_backlog < 0)
     return set_error(DOBFS_ERR_INVALID, "bad server options");
   dobfs_server* S = new (std::nothrow) dobfs_server();
   if (!S) return set_error(DOBFS_ERR_OOM, "host allocation failed");
@@ -409,10 +492,18 @@ int dobfs_serve_add_graph(dobfs_server* S, dobfs_graph* g, int32_t* gid) {
   Engine* e = new (std::nothrow) Engine();
   if (!e) return set_error(DOBFS_ERR_OOM, "host allocation failed");
   e->g = g;
+  if (cudaStreamCreateWithFlags(&e->ss_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&e->ss_levels, sizeof(int32_t) * kSsRing) != cudaSuccess) {
+    if (e->ss_stream) cudaStreamDestroy(e->ss_stream);
+    delete e;
+    return set_error(DOBFS_ERR_CUDA, "stream or pinned allocation failed");
+  }
   const int64_t gb = group_bytes(g) * S->opts.groups_per_graph;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->reserved + gb > S->budget) {
+      cudaStreamDestroy(e->ss_stream);
+      cudaFreeHost(e->ss_levels);
       delete e;
       return set_error(DOBFS_ERR_BUSY, "device-memory budget too small for the graph's lane groups");
     }
@@ -424,9 +515,12 @@ int dobfs_serve_add_graph(dobfs_server* S, dobfs_graph* g, int32_t* gid) {
       for (Group* G : e->groups) {
         ms_group_destroy(G->ms);
         cudaFreeHost(G->hctl);
+        cudaEventDestroy(G->ctl_ev);
         cudaStreamDestroy(G->stream);
         delete G;
       }
+      cudaStreamDestroy(e->ss_stream);
+      cudaFreeHost(e->ss_levels);
       delete e;
       std::lock_guard<std::mutex> lk(S->mu);
       S->reserved -= gb;
@@ -551,9 +645,18 @@ int dobfs_serve_destroy(dobfs_server* S) {
       cudaStreamSynchronize(G->stream);
       ms_group_destroy(G->ms);
       cudaFreeHost(G->hctl);
+      cudaEventDestroy(G->ctl_ev);
       cudaStreamDestroy(G->stream);
       delete G;
     }
+    cudaStreamSynchronize(e->ss_stream);
+    {
+      // the graph's next run must not wait on a stream that is about to go away
+      std::lock_guard<std::mutex> lk(e->g->mu);
+      if (e->g->last_stream == e->ss_stream) e->g->last_stream = nullptr;
+    }
+    cudaStreamDestroy(e->ss_stream);
+    cudaFreeHost(e->ss_levels);
     delete e;
   }
   for (auto& kv : S->queries) {

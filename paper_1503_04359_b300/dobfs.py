@@ -75,7 +75,8 @@ class dobfs_serve_opts(ctypes.Structure):
     _fields_ = [("max_device_bytes", ctypes.c_int64), ("groups_per_graph", ctypes.c_int32),
                 ("max_groups_per_graph", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("admit_div", ctypes.c_int32), ("join_window", ctypes.c_int32),
-                ("flush_delay", ctypes.c_int32)]
+                ("flush_delay", ctypes.c_int32), ("gather_us", ctypes.c_int32), ("ss_max", ctypes.c_int32),
+                ("ss_backlog", ctypes.c_int32)]
 
 
 class dobfs_query_result(ctypes.Structure):
@@ -316,7 +317,8 @@ def dobfs_serve_opts_init() -> dobfs_serve_opts:
 def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 2,
                     alpha: int = 14, beta: int = 24, direction: int = DOBFS_DIR_AUTO,
                     admit_div: int | None = None, join_window: int | None = None,
-                    flush_delay: int | None = None) -> dobfs_serve_opts:
+                    flush_delay: int | None = None, gather_us: int | None = None, ss_max: int | None = None,
+                    ss_backlog: int | None = None) -> dobfs_serve_opts:
     o = dobfs_serve_opts()
     _check(load().dobfs_serve_opts_init(ctypes.byref(o)))
     if admit_div is not None:
@@ -325,6 +327,12 @@ def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_gr
         o.join_window = join_window
     if flush_delay is not None:
         o.flush_delay = flush_delay
+    if gather_us is not None:
+        o.gather_us = gather_us
+    if ss_max is not None:
+        o.ss_max = ss_max
+    if ss_backlog is not None:
+        o.ss_backlog = ss_backlog
     o.max_device_bytes = max_device_bytes
     o.groups_per_graph = groups_per_graph
     o.max_groups_per_graph = max_groups_per_graph

@@ -50,8 +50,11 @@ def _wait(d, srv, ticket, timeout=60.0):
         time.sleep(0.0005)
 
 
-def test_alone_and_in_the_mix(d, graphs):
-    srv = d.dobfs_serve_create(d.make_serve_opts(max_groups_per_graph=2))
+@pytest.mark.parametrize("ss_max", [0, 2])
+def test_alone_and_in_the_mix(d, graphs, ss_max):
+    """ss_max = 0: every query runs in a lane group; 2: lone queries take the
+    single-source path and bursts the lane groups."""
+    srv = d.dobfs_serve_create(d.make_serve_opts(max_groups_per_graph=2, ss_max=ss_max))
     try:
         gids = [d.dobfs_serve_add_graph(srv, g.handle) for g, _, _, _ in graphs]
         # alone: one query at a time
