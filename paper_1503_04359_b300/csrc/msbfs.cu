@@ -449,8 +449,13 @@ __device__ __forceinline__ void flush_vertex(const MsArgs<OffT>& A, const FlushA
   }
 }
 
-template <class OffT>
+// One kernel per plane-count class (NP = 4, 8, 16 planes at most): all three
+// are launched and the ones that do not match the planes in use return at
+// once, so the common case keeps a small register footprint.
+template <class OffT, int NP>
 __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs F) {
+  const int np = A.ctl->n_planes;
+  if (np > NP || (NP > 4 && np <= NP / 2)) return;
   __shared__ int32_t* s_out[kMsLanes];
   __shared__ int32_t s_start[kMsLanes];
   if (threadIdx.x < kMsLanes) {
@@ -458,13 +463,10 @@ __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs
     s_start[threadIdx.x] = F.start[threadIdx.x];
   }
   __syncthreads();
-  const int np = A.ctl->n_planes;
   unsigned long long mu_back = 0;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = A.o2n ? A.o2n[o] : o;
-    if (np <= 4) flush_vertex<4>(A, F, np, o, v, s_out, s_start, mu_back);
-    else if (np <= 8) flush_vertex<8>(A, F, np, o, v, s_out, s_start, mu_back);
-    else flush_vertex<16>(A, F, np, o, v, s_out, s_start, mu_back);
+    flush_vertex<NP>(A, F, np, o, v, s_out, s_start, mu_back);
   }
   if (F.release) {
     __shared__ unsigned long long sh[kThreads / 32];
@@ -614,7 +616,10 @@ int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
 template <class OffT>
 int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
   const int G = (int)std::min<int64_t>(ceil_div(m->g->n, kThreads), (int64_t)ms_grid(16));
-  k_ms_flush<OffT><<<G, kThreads, 0, m->stream>>>(ms_args<OffT>(m), F);
+  const MsArgs<OffT> A = ms_args<OffT>(m);
+  k_ms_flush<OffT, 4><<<G, kThreads, 0, m->stream>>>(A, F);
+  k_ms_flush<OffT, 8><<<G, kThreads, 0, m->stream>>>(A, F);
+  k_ms_flush<OffT, 16><<<G, kThreads, 0, m->stream>>>(A, F);
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
