@@ -2,6 +2,7 @@
 
     python -m paper_1503_04359_b300.levels [--scale S] [--roots R] [--max-root-degree D]
                                            [--modes auto,topdown] [--no-reindex] [--json]
+                                           [--alpha A] [--beta B] [--td-bitmap-div D] [--batch K]
 
 For every root and direction policy it runs one BFS driven from the host
 (``DOBFS_RUN_HOST_LOOP``), so each level's kernels are timed with CUDA
@@ -30,6 +31,10 @@ def main(argv=None) -> int:
     ap.add_argument("--no-reindex", action="store_true")
     ap.add_argument("--json", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="also profile one batched run of this many roots")
+    ap.add_argument("--alpha", type=int, default=None, help="direction switch alpha (default: the library's)")
+    ap.add_argument("--beta", type=int, default=None)
+    ap.add_argument("--td-bitmap-div", type=int, default=None,
+                    help="top-down steps with m_f * div >= n mark a bitmap (0: never)")
     args = ap.parse_args(argv)
 
     import torch
@@ -51,12 +56,13 @@ def main(argv=None) -> int:
     lv = torch.empty(n, dtype=torch.int32, device="cuda")
     pa = torch.empty(n, dtype=torch.int32, device="cuda")
     out = []
+    knobs = {"alpha": args.alpha, "beta": args.beta, "td_bitmap_div": args.td_bitmap_div}
     for name in args.modes.split(","):
         mode = modes[name]
         for r in roots:
-            g.run(int(r), lv, pa, dobfs.make_opts(direction=mode))  # warm
-            st = g.run(int(r), lv, pa, dobfs.make_opts(direction=mode), want_stats=True)
-            sh = g.run(int(r), lv, pa, dobfs.make_opts(direction=mode, flags=dobfs.DOBFS_RUN_HOST_LOOP),
+            g.run(int(r), lv, pa, dobfs.make_opts(direction=mode, **knobs))  # warm
+            st = g.run(int(r), lv, pa, dobfs.make_opts(direction=mode, **knobs), want_stats=True)
+            sh = g.run(int(r), lv, pa, dobfs.make_opts(direction=mode, flags=dobfs.DOBFS_RUN_HOST_LOOP, **knobs),
                        want_stats=True)
             rec = {"mode": name, "root": int(r), "root_degree": int(deg[r]), "graph_ms": st.device_ms,
                    "host_loop_ms": sh.device_ms, "levels": st.levels, "reached": st.reached,
@@ -83,7 +89,7 @@ def main(argv=None) -> int:
         bout = torch.empty((args.batch, n), dtype=torch.int32, device="cuda")
         rt = torch.from_numpy(np.ascontiguousarray(broots)).cuda()
         for name in args.modes.split(","):
-            o = dobfs.make_opts(direction=modes[name])
+            o = dobfs.make_opts(direction=modes[name], **knobs)
             st = dobfs.dobfs_run_batch(g.handle, rt, bout, opts=o, want_stats=True)
             o.flags = dobfs.DOBFS_RUN_HOST_LOOP
             sh = dobfs.dobfs_run_batch(g.handle, rt, bout, opts=o, want_stats=True)
