@@ -14,16 +14,23 @@ GPU: BFS from a single root does not shard without a per-level exchange, so
 the job's value is the sum of the ranks' rates measured over the max time.
 
 Also reported: the roofline of the dominant kernel (the bottom-up step,
-measured per level with CUDA events in host-driven mode on the same roots),
+measured per level with CUDA events in host-driven mode on a fixed sample of
+16 roots, the same whatever --steps and --warmup are, so that an ncu capture
+of this command measures the same launches; its DRAM traffic per level is
+read from the committed ncu summary when the kernel sources still match it),
 an end-to-end number through the C ABI with host (pinned) output buffers,
 the CPU oracle on a bounded sample, SM clocks sampled during the timed
-region, and the number of kernels launched.
+region, and the number of kernels launched. With --tune the direction policy
+and degree-bin cutoffs are first tuned on 8 other roots (autotune.py) and
+the timed pass uses the tuned options.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -43,6 +50,48 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+KERNEL_SOURCES = ("paper_1503_04359_b300/csrc/bfs.cu", "paper_1503_04359_b300/csrc/graph.cuh",
+                  "paper_1503_04359_b300/csrc/common.cuh")
+TRAFFIC_PROFILE = "profiles/bu_step_rmat_s28.md"
+STEP_NAMES = {0: "top-down", 1: "bottom-up", 2: "mixed"}
+STEP_KERNELS = {0: "top-down step (k_td_bin + k_td_chunks [+ k_bu parent search])",
+                1: "bottom-up step (k_bu + k_bu_long)",
+                2: "mixed step (k_td_bin + k_td_chunks + k_bu + k_bu_long)"}
+
+
+def kernel_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per bottom-up level from the committed ncu summary, if it
+    was taken on this workload with the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
+            m = re.search(r"<!-- traffic (\{.*?\}) -->", f.read(), re.S)
+        rec = json.loads(m.group(1))
+    except Exception:
+        return None
+    if rec.get("kernel_sha256") != kernel_sha256() or rec.get("workload") != workload:
+        return None
+    return rec
+
+
+def aggregate_ranks(dist, device, total_ms: float, total_edges: float) -> tuple[float, float]:
+    """Whole-job GTEPS of independent replicas: the edges every rank traversed
+    over the slowest rank's timed region (max over ranks). Returns (GTEPS, max ms)."""
+    import torch
+    t = torch.tensor([total_ms, total_edges], dtype=torch.float64, device=device)
+    allt = [torch.zeros_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(allt, t)
+    mx = max(float(x[0]) for x in allt)
+    return sum(float(x[1]) for x in allt) / (mx * 1e-3) / 1e9, mx
 
 
 def _peaks():
@@ -315,6 +364,7 @@ def main() -> None:
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-BFS measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
+    ap.add_argument("--tune", action="store_true", help="tune the run options on 8 other roots first")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -360,6 +410,16 @@ def main() -> None:
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     opts = dobfs.make_opts(stream=stream)
+    tuning = None
+    if args.tune:
+        from paper_1503_04359_b300 import autotune
+        tune_roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0x7E57, n, 8, deg > 0)
+        t0 = time.perf_counter()
+        _, rec = autotune.tune(g, tune_roots)
+        opts = dobfs.make_opts(stream=stream, **rec["params"])
+        tuning = {"policy": rec["policy"], "params": rec["params"], "sample_roots": len(tune_roots),
+                  "default_ms_per_root": rec["default_ms"], "tuned_ms_per_root": rec["ms"],
+                  "seconds": round(time.perf_counter() - t0, 1)}
 
     # untimed pass: per-root edge counts, levels and algorithmic bytes
     teps, alg_bytes, launches, levels = [], [], [], []
@@ -404,29 +464,26 @@ def main() -> None:
     total_edges = float(sum(teps))
     clocks = clk.summary()
 
-    # job value over ranks: sum of per-rank rates at the slowest rank's time
+    # job value over ranks: all ranks' edges over the slowest rank's time
     job_value, job_ms = hmean, total_ms
     if dist:
-        t = torch.tensor([total_ms, total_edges, hmean], dtype=torch.float64, device="cuda")
-        allt = [torch.zeros_like(t) for _ in range(ws)]
-        dist.all_gather(allt, t)
-        mx = max(float(x[0]) for x in allt)
-        job_ms = mx
-        job_value = sum(float(x[1]) for x in allt) / (mx * 1e-3) / 1e9
+        job_value, job_ms = aggregate_ranks(dist, "cuda", total_ms, total_edges)
 
-    # roofline of the dominant kernel: per-level events in host-driven mode on the same roots
+    # roofline of the dominant kernel: per-level events in host-driven mode on
+    # a fixed root sample with the default options
     peak, peak_kind = _peaks()
     hl = dobfs.make_opts(stream=stream, flags=dobfs.DOBFS_RUN_HOST_LOOP)
-    per_kind = {0: [0.0, 0], 1: [0.0, 0]}  # direction -> [ms, bytes]
-    n_launch = {0: 0, 1: 0}
-    for r in roots[:min(len(roots), 16)]:
+    per_kind = {0: [0.0, 0], 1: [0.0, 0], 2: [0.0, 0]}  # direction (top-down, bottom-up, mixed) -> [ms, bytes]
+    n_launch = {0: 0, 1: 0, 2: 0}
+    roof_roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0x500F, n, 16, deg > 0)
+    for r in roof_roots:
         g.run(int(r), level, parent, hl)
         torch.cuda.synchronize()
         for t in g.trace():
             per_kind[t.direction][0] += t.ms_main
             per_kind[t.direction][1] += t.alg_bytes
             n_launch[t.direction] += 1
-    dom = 1 if per_kind[1][0] >= per_kind[0][0] else 0
+    dom = max(per_kind, key=lambda k: per_kind[k][0])
     dom_ms, dom_bytes = per_kind[dom]
     achieved = (dom_bytes / n_launch[dom]) / ((dom_ms / n_launch[dom]) * 1e-3) / 1e9 if n_launch[dom] else 0.0
     whole_gbs = (sum(alg_bytes) / (total_ms * 1e-3)) / 1e9
@@ -465,6 +522,8 @@ def main() -> None:
 
     if rank != 0:
         return
+    workload = "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex")
+    prof = profiled_traffic(workload) if dom == 1 else None
     result = {
         "metric": METRIC,
         "value": job_value,
@@ -479,22 +538,29 @@ def main() -> None:
         "dtype": "int32",
         "data": "synthetic",
         "config": {
-            "workload": "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex"),
+            "workload": workload,
             "scale": args.scale, "edgefactor": 16, "a": spec.a, "b": spec.b, "c": spec.c, "seed": spec.seed,
             "n_vertices": n, "n_entries": int(info.n_entries), "n_nonisolated": int(info.n_nonisolated),
             "offsets_int64": int(info.offsets_int64), "reindexed": int(info.reindexed),
             "roots": len(roots), "parallelism": "replicas" if ws > 1 else "single-gpu",
             "l2": "inputs larger than L2 (graph %.1f GB resident), no flush" % (info.device_bytes / 1e9),
             "build_s": round(build_s, 2), "device_bytes": int(info.device_bytes),
+            "run_options": "tuned" if tuning is not None else "defaults",
         },
         "per_root": {"ms_mean": total_ms / len(roots), "ms_min": min(ms), "ms_max": max(ms),
                      "gteps_min": min(rates), "gteps_max": max(rates), "levels_mean": float(np.mean(levels)),
                      "teps_edges_mean": total_edges / len(roots), "aggregate_gteps": total_edges / total_ms / 1e6,
                      "wall_s": wall},
         "roofline": {
-            "kernel": "bottom-up step (k_bu + k_bu_long)" if dom == 1 else "top-down step (k_td_bin + k_td_chunks)",
+            "kernel": STEP_KERNELS[dom],
+            "time_share_by_step": {STEP_NAMES[k]: per_kind[k][0] / max(1e-9, sum(v[0] for v in per_kind.values()))
+                                   for k in per_kind},
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_kind, "traffic": None,
+            "peak_source": peak_kind, "traffic": prof["bytes_per_level"] if prof else None,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per bottom-up level (%s)"
+                               % TRAFFIC_PROFILE) if prof else None,
+            "alg_bytes_per_level": (dom_bytes / n_launch[dom]) if n_launch[dom] else None,
+            "levels_timed": n_launch[dom], "roots": len(roof_roots), "options": "defaults, host-driven levels",
             "whole_bfs_alg_gbs": whole_gbs, "whole_bfs_frac": whole_gbs / peak,
             "alg_bytes_per_root": float(np.mean(alg_bytes)),
         },
@@ -503,6 +569,8 @@ def main() -> None:
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
     }
+    if tuning is not None:
+        result["tuning"] = tuning
     if cpu is not None:
         result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if batch is not None:

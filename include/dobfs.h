@@ -190,6 +190,19 @@ typedef struct {
   void* stream;             /* cudaStream_t (NULL: the graph's creation stream) */
   int32_t td_bitmap_div;    /* a top-down level with m_f * td_bitmap_div >= n marks a next-frontier
                                bitmap and finds parents afterwards (0: never; default 2) */
+  /* Degree-bin cutoffs of the step kernels (0: the path's default). They
+     change only the speed, never the result. */
+  int32_t td_small_max;     /* top-down rows of at most this many entries are expanded by one
+                               thread, longer ones are cut into chunk records (8..256; default 16;
+                               single-source runs) */
+  int32_t td_chunk;         /* entries per top-down chunk record, expanded by one warp (multiple
+                               of 128 in 256..8192; default 512 single-source, 1024 batched) */
+  int32_t bu_scan;          /* bottom-up entries one thread scans before the rest of the row goes
+                               to a warp (1..256; default 32) */
+  int32_t td_split_pct;     /* mixed levels (degree-sorted graphs): a bitmap-output top-down level
+                               searches the vertices of degree >= td_split_pct/100 * nnz / m_f
+                               bottom-up and expands only the rest of each frontier row top-down
+                               (0: off; 0..100000; default 150) */
 } dobfs_run_opts;
 
 typedef struct {
@@ -328,7 +341,8 @@ int dobfs_serve_destroy(dobfs_server* s);
 /* Per-level record of the last run on a graph (ready after that run completed). */
 typedef struct {
   int32_t level;            /* level L being expanded (frontier = vertices at level L) */
-  int32_t direction;        /* 0 top-down, 1 bottom-up */
+  int32_t direction;        /* 0 top-down, 1 bottom-up, 2 mixed (bottom-up for the high-degree
+                               vertices, top-down for the rest; see td_split_pct) */
   int64_t n_frontier;       /* n_f: vertices at level L */
   int64_t m_frontier;       /* m_f: sum of their degrees */
   int64_t m_unvisited;      /* m_u: sum of degrees of unvisited vertices before the step */

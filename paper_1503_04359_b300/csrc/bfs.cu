@@ -12,15 +12,15 @@
 //   top-down  (Algorithm 1, top-down branch): every frontier vertex reads its
 //             row and claims unvisited neighbours with atomicOr on the visited
 //             bitmap; the winner writes (level, parent) and appends the vertex
-//             to the next queue. Rows of up to kTdSmall entries are expanded
+//             to the next queue. Rows of up to td_small_max entries are expanded
 //             by one thread in the binning kernel; longer rows are cut into
-//             kChunk-entry records expanded one warp each with 16-byte loads.
+//             td_chunk-entry records expanded one warp each with 16-byte loads.
 //   bottom-up (Algorithm 1, bottom-up branch): a warp owns one visited-bitmap
 //             word (32 consecutive vertices); each unvisited vertex scans its
 //             row in order and stops at the first neighbour whose frontier
 //             bit is set. The warp writes the next-frontier word and the
 //             visited word with one store each (ballot), no atomics. Rows
-//             with no hit among their first kBuT entries continue in a
+//             with no hit among their first bu_scan entries continue in a
 //             warp-per-row kernel (16-byte loads, ballot for the first hit).
 //   switch    (Sec. 3.3): a one-thread kernel folds the step's counters into
 //             n_f, m_f, m_u and picks the next direction: top-down -> bottom-up
@@ -49,9 +49,12 @@ namespace dobfs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTdSmall = 16;   // top-down rows up to this length: one thread
-constexpr int kChunk = 512;    // top-down chunk record length (entries)
-constexpr int kBuT = 32;       // bottom-up entries scanned per thread before deferring
+// Degree-bin cutoffs (defaults; a run may set others, read from BfsCtl):
+constexpr int kTdSmall = 16;     // top-down rows up to this length: one thread
+constexpr int kChunk = 512;      // top-down chunk record length (entries)
+constexpr int kBuT = 32;         // bottom-up entries scanned per thread before deferring
+constexpr int kTdSmallMin = 8;   // smallest allowed cutoffs (they size the record buffer)
+constexpr int kChunkMin = 256;
 constexpr int kCases = 6;      // step kinds of the level loop's switch node
 constexpr int kCaseNone = 7;   // switch value with no body: loop ends
 
@@ -62,6 +65,7 @@ struct BfsArgs {
   const uint32_t* iso;
   const int32_t* o2n;  // NULL when not reindexed
   const int2* firstdeg;  // (first neighbour, degree) per vertex; first = -1 for isolated vertices
+  const int64_t* deg_ge;  // [33]: vertices of degree >= 2^k
   uint32_t* visited;
   uint32_t* fbm0;
   uint32_t* fbm1;
@@ -77,6 +81,15 @@ struct BfsArgs {
 
 __device__ __forceinline__ bool test_bit(const uint32_t* __restrict__ bm, int32_t v) {
   return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// First position in the sorted row cols[s, e) whose column is >= x.
+__device__ __forceinline__ int64_t lower_bound_col(const int32_t* __restrict__ cols, int64_t s, int64_t e, int32_t x) {
+  while (s < e) {
+    const int64_t m = s + ((e - s) >> 1);
+    if (__ldg(cols + m) < x) s = m + 1; else e = m;
+  }
+  return s;
 }
 
 // Appends v to q at an index taken from *tail, one atomic per group of
@@ -147,7 +160,8 @@ __device__ __forceinline__ void td_mark4(const BfsArgs<OffT>& A, const int32_t (
 
 template <class OffT>
 __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t alpha, int32_t beta,
-                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed, int32_t td_bm_div) {
+                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed, int32_t td_bm_div,
+                       int32_t td_small, int32_t td_chunk, int32_t bu_scan, int32_t td_split_pct) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int32_t r = A.o2n ? A.o2n[root_orig] : root_orig;
   const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
@@ -179,6 +193,11 @@ __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t
   c->bu_steps = bu_steps;
   c->sched_seed = sched_seed;
   c->td_bm_div = td_bm_div;
+  c->td_small = td_small;
+  c->td_chunk = td_chunk;
+  c->bu_scan = bu_scan;
+  c->td_split_pct = td_split_pct;
+  c->split_w = 0;
   A.q0[0] = r;
   A.visited[r >> 5] |= 1u << (r & 31);
   A.lp[r] = make_int2(0, r);
@@ -198,14 +217,18 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
     const int64_t m_new = (int64_t)c->nx_m;
     const int64_t ex = (int64_t)c->nx_examined, sc = (int64_t)c->nx_scanned;
     int64_t bytes;
-    if (c->dir == 0)  // queue read 4, row bounds 16, columns 4 each, level+parent 8 and enqueue 4 per new vertex
+    if (c->step_case >= 4)  // bitmap-output top-down (+ bottom-up part of a mixed level, + parent search):
+      // queue 4 and row bounds 16 per frontier vertex, columns 4 each read, row bounds 8 per vertex
+      // searched bottom-up, level+parent 8 and bitmap conversion 4 per new vertex, conversion 4 per frontier vertex
+      bytes = 24 * c->n_f + 4 * ex + 8 * sc + 12 * n_new;
+    else if (c->dir == 0)  // queue read 4, row bounds 16, columns 4 each, level+parent 8 and enqueue 4 per new vertex
       bytes = 20 * c->n_f + 4 * c->m_f + 12 * n_new + (c->step_case >= 2 ? 4 * c->n_f : 0);
     else  // row bounds 8 per scanned vertex, columns 4 each read, level+parent 8 per new vertex
       bytes = 8 * sc + 4 * ex + 8 * n_new + (c->step_case == 3 ? 4 * c->n_f : 0);
     if (L < kMaxTrace) {
       LevelRec& t = A.trace[L];
       t.level = L;
-      t.dir = c->dir;
+      t.dir = (c->dir == 0 && c->split_w > 0) ? 2 : c->dir;
       t.n_f = c->n_f;
       t.m_f = c->m_f;
       t.m_u = c->m_u;
@@ -262,10 +285,22 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
       break;
   }
   int kase;
+  c->split_w = 0;
   if (dir == 0) {
     // heavy top-down levels mark a bitmap and recover parents afterwards
     const bool bm = c->td_bm_div > 0 && c->m_f * (int64_t)c->td_bm_div >= A.n;
     kase = bm ? (c->fmt == 0 ? 4 : 5) : (c->fmt == 0 ? 0 : 2);
+    if (bm && A.o2n && c->td_split_pct > 0 && c->m_f > 0) {
+      // mixed level: a vertex of degree d receives about d * m_f / nnz of the
+      // frontier's edges, so top-down pays that many probes for it, a bottom-up
+      // search about one (its first neighbours are the hubs). Vertices of degree
+      // >= 2^k >= td_split_pct/100 * nnz / m_f (a prefix of the degree-sorted
+      // IDs) are searched bottom-up; the rows' entries beyond them go top-down.
+      const double dx = (double)c->td_split_pct * (double)A.nnz / (100.0 * (double)c->m_f);
+      int k = 0;
+      while (k < 32 && (double)(1ll << k) < dx) ++k;
+      c->split_w = (A.deg_ge[k] >> 10) << 5;  // whole groups of 32 words
+    }
   } else {
     kase = (c->fmt == 1) ? 1 : 3;
   }
@@ -284,19 +319,25 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
   const int64_t nf = c->n_f;
   const int32_t* cur = (L & 1) ? A.q1 : A.q0;
   int32_t* nxt = (L & 1) ? A.q0 : A.q1;
+  const int64_t small = c->td_small, chunk = c->td_chunk;
+  // mixed level: targets below x are searched bottom-up; only the rest of
+  // each (sorted) row is expanded here
+  const int32_t x = BM ? (int32_t)(c->split_w << 5) : 0;
   unsigned long long m_new = 0, ex = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = cur[i];
-    const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+    int64_t s = (int64_t)A.off[u];
+    const int64_t e = (int64_t)A.off[u + 1];
+    if (BM && x > 0 && e - s > small) s = lower_bound_col(A.cols, s, e, x);
     ex += (unsigned long long)(e - s);
-    if (e - s <= kTdSmall) {
+    if (e - s <= small) {
       for (int64_t j = s; j < e; j += 4) {
         int32_t v[4];
         unsigned valid = 0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           v[t] = (j + t < e) ? A.cols[j + t] : 0;
-          if (j + t < e) valid |= 1u << t;
+          if (j + t < e && v[t] >= x) valid |= 1u << t;
         }
         if (BM) {
           td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
@@ -311,13 +352,25 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
       }
     } else {
       const int64_t a = s & ~3ll;
-      const unsigned nch = (unsigned)ceil_div(e - a, kChunk);
+      const unsigned nch = (unsigned)ceil_div(e - a, chunk);
       const unsigned base = atomicAdd(&A.ctl->n_rec, nch);
       if ((int64_t)base + nch > A.rec_cap) {
         A.ctl->overflow = 1;
         continue;
       }
-      for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2(u, (int)k);
+      if (BM) {
+        // marking needs no parent: the record holds the chunk's position
+        // (start, length, entries to skip before the row's part starts)
+        unsigned long long* r64 = reinterpret_cast<unsigned long long*>(A.rec);
+        for (unsigned k = 0; k < nch; ++k) {
+          const int64_t lo = a + (int64_t)k * chunk;
+          const int64_t hi = min(e, lo + chunk);
+          r64[base + k] = ((unsigned long long)lo << 16) | ((unsigned long long)(hi - lo) << 2) |
+                          (unsigned long long)(max(s, lo) - lo);
+        }
+      } else {
+        for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2(u, (int)k);
+      }
     }
   }
   m_new = block_sum_u64(m_new, sh);
@@ -335,17 +388,27 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
+  const int64_t chunk = c->td_chunk;
   int32_t* nxt = (L & 1) ? A.q0 : A.q1;
   unsigned long long m_new = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const unsigned lane = lane_id();
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
-    const int2 rc = A.rec[r];
-    const int32_t u = rc.x;
-    const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
-    const int64_t lo = (s & ~3ll) + (int64_t)rc.y * kChunk;
-    const int64_t hi = min(e, lo + kChunk);
-    const int64_t lo_ok = max(s, lo);
+    int32_t u = 0;
+    int64_t lo, hi, lo_ok;
+    if (BM) {
+      const unsigned long long rc = reinterpret_cast<const unsigned long long*>(A.rec)[r];
+      lo = (int64_t)(rc >> 16);
+      hi = lo + (int64_t)((rc >> 2) & 0x3FFFu);
+      lo_ok = lo + (int64_t)(rc & 3u);
+    } else {
+      const int2 rc = A.rec[r];
+      u = rc.x;
+      const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+      lo = (s & ~3ll) + (int64_t)rc.y * chunk;
+      hi = min(e, lo + chunk);
+      lo_ok = max(s, lo);
+    }
     for (int64_t pb = lo; pb < hi; pb += 128) {  // uniform trip count: the warp enqueues together
       const int64_t p = pb + 4 * (int64_t)lane;
       int32_t v[4] = {0, 0, 0, 0};
@@ -441,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // degree from the packed (first, degree) array: rows are sorted with the
 // highest-degree neighbour first, so most vertices that have a frontier
 // neighbour resolve with that one 8-byte load. Otherwise the lane scans the
-// rest of its first kBuT entries, four loads at a time, and stops at the
+// rest of its first bu_scan entries, four loads at a time, and stops at the
 // first neighbour in the frontier; longer rows without a hit go to the
 // deferred list. Found vertices are collected per word in shared memory and
 // every lane writes its own next-frontier and visited word: no global atomics.
@@ -454,14 +517,22 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   const int32_t L = c->level;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
   uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
+  const int32_t scan = c->bu_scan;
   const unsigned lane = lane_id();
   const int wid = threadIdx.x >> 5;
   unsigned long long n_new = 0, m_new = 0, ex = 0, sc = 0;
-  const int64_t groups = ceil_div(A.cand_words, 32);
+  // words searched: all candidates in a bottom-up level; in a bitmap-output
+  // top-down level, the search covers [0, split_w) (the mixed level's
+  // bottom-up part; empty otherwise) and the parent recovery the rest
+  const int64_t split = c->split_w;
+  const int64_t w_lo = RECOVER ? split : 0;
+  const int64_t w_hi = RECOVER ? A.cand_words : (c->step_case >= 4 ? split : A.cand_words);
+  const int64_t groups = ceil_div(w_hi, 32);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; grp < groups; grp += warps) {
+  for (int64_t grp = w_lo / 32 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); grp < groups;
+       grp += warps) {
     const int64_t w = grp * 32 + lane;
-    const bool in = w < A.cand_words;
+    const bool in = w < w_hi;
     const uint32_t vis = in ? A.visited[w] : ~0u;
     // recovery: the candidates are the vertices the top-down marking found
     const uint32_t cand = in ? (RECOVER ? next[w] : ~(vis | A.iso[w])) : 0u;
@@ -516,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
         unsigned long long exv = 1;
         if (!hit0[c2] && fd[c2].y > 1) {
           const int64_t s0 = (int64_t)A.off[v];
-          const int64_t lim = s0 + min(fd[c2].y, kBuT);
+          const int64_t lim = s0 + min(fd[c2].y, scan);
           for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
             int32_t u[4];
 #pragma unroll
@@ -529,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
               if (h[t]) parent = u[t];
             exv += (unsigned long long)min((int64_t)4, lim - p);
           }
-          if (parent < 0 && fd[c2].y > kBuT) enqueue(&A.ctl->n_def, A.def, v);
+          if (parent < 0 && fd[c2].y > scan) enqueue(&A.ctl->n_def, A.def, v);
         }
         ex += exv;
         if (parent >= 0) {
@@ -570,7 +641,7 @@ __global__ void k_clear_next(BfsArgs<OffT> A) {
     next[w] = 0u;
 }
 
-// Bottom-up, part 2: rows with no frontier neighbour among their first kBuT
+// Bottom-up, part 2: rows with no frontier neighbour among their first bu_scan
 // entries; one warp per row, 16-byte loads, the ballot picks the first hit
 // in row order.
 template <class OffT>
@@ -587,7 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
     const int32_t v = A.def[i];
     const int64_t s0 = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
-    const int64_t s = s0 + kBuT;
+    const int64_t s = s0 + c->bu_scan;
     int32_t parent = -1;
     for (int64_t base = s & ~3ll; base < e; base += 128) {
       const int64_t p = base + 4 * (int64_t)lane;
@@ -757,6 +828,7 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   A.iso = g->isolated.as<uint32_t>();
   A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
   A.firstdeg = g->firstdeg.as<int2>();
+  A.deg_ge = g->degge.as<int64_t>();
   A.visited = g->visited.as<uint32_t>();
   A.fbm0 = g->fbm0.as<uint32_t>();
   A.fbm1 = g->fbm1.as<uint32_t>();
@@ -848,6 +920,7 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
       if (main_begin) cudaEventRecord(main_begin, s);
       k_td_bin<OffT, true><<<G.td_bin, kThreads, 0, s>>>(A);
       k_td_chunks<OffT, true><<<G.td_chunks, kThreads, 0, s>>>(A);
+      k_bu<OffT, false><<<G.bu, kThreads, 0, s>>>(A);  // the bottom-up part of a mixed level
       k_bu<OffT, true><<<G.bu, kThreads, 0, s>>>(A);
       k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
@@ -986,7 +1059,9 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
   k_init<OffT><<<1, 32, 0, s>>>(A, root, o.direction, o.alpha, o.beta, o.static_pct, o.bu_steps, o.schedule_seed,
-                                o.td_bitmap_div);
+                                o.td_bitmap_div, o.td_small_max ? o.td_small_max : kTdSmall,
+                                o.td_chunk ? o.td_chunk : kChunk, o.bu_scan ? o.bu_scan : kBuT,
+                                o.td_split_pct);
   DOBFS_CUDA_TRY(cudaGetLastError());
   if (host_loop_mode) {
     DOBFS_TRY(host_loop<OffT>(g, A, s));
@@ -1046,10 +1121,12 @@ int graph_alloc_workspace(dobfs_graph* g) {
   DOBFS_TRY(g->lp.alloc(sizeof(int2) * (size_t)g->n, s));
   DOBFS_TRY(g->q0.alloc(sizeof(int32_t) * (size_t)g->n, s));
   DOBFS_TRY(g->q1.alloc(sizeof(int32_t) * (size_t)g->n, s));
-  g->rec_cap = std::min<int64_t>(g->n, g->nnz / (kTdSmall + 1)) + g->nnz / kChunk + 64;
+  g->rec_cap = std::min<int64_t>(g->n, g->nnz / (kTdSmallMin + 1)) + g->nnz / kChunkMin + 64;
   DOBFS_TRY(g->rec.alloc(sizeof(int2) * (size_t)g->rec_cap, s));
   DOBFS_TRY(g->deferred.alloc(sizeof(int32_t) * (size_t)g->n, s));
   DOBFS_TRY(g->firstdeg.alloc(sizeof(int2) * (size_t)g->n, s));
+  DOBFS_TRY(g->degge.alloc(sizeof(g->deg_ge), s));
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(g->degge.ptr, g->deg_ge, sizeof(g->deg_ge), cudaMemcpyHostToDevice, s));
   {
     const int grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
     if (g->off64)
@@ -1111,6 +1188,10 @@ int dobfs_run_opts_init(dobfs_run_opts* o) {
   o->schedule_seed = 0;
   o->stream = nullptr;
   o->td_bitmap_div = 2;
+  o->td_small_max = 0;
+  o->td_chunk = 0;
+  o->bu_scan = 0;
+  o->td_split_pct = 150;
   return DOBFS_OK;
 }
 
@@ -1126,6 +1207,7 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
   if (o.direction < 0 || o.direction > DOBFS_DIR_STATIC || o.alpha < 1 || o.beta < 1 || o.static_pct < 0 ||
       o.bu_steps < 1 || o.td_bitmap_div < 0)
     return set_error(DOBFS_ERR_INVALID, "bad run options");
+  if (!cutoffs_valid(o)) return set_error(DOBFS_ERR_INVALID, "bad degree-bin cutoffs");
   std::lock_guard<std::mutex> lk(g->mu);
   return g->off64 ? run_impl<int64_t>(g, root, level_out, parent_out, o, stats)
                   : run_impl<int32_t>(g, root, level_out, parent_out, o, stats);

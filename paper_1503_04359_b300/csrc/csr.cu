@@ -214,7 +214,12 @@ __global__ void k_check_sym(const uint64_t* __restrict__ keys, int64_t m, int b,
 template <class OffT>
 __global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t words, uint32_t* __restrict__ iso,
                             unsigned long long* __restrict__ stats) {
+  // stats: [0] vertices with an edge, [1] max degree, [2 + k] vertices with
+  // floor(log2(degree)) == k
   __shared__ unsigned long long sh[kThreads / 32];
+  __shared__ unsigned int s_hist[32];
+  if (threadIdx.x < 32) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
   unsigned long long nonzero = 0, mx = 0;
   const int64_t total = words * 32;
   for (int64_t v0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; v0 < total;
@@ -226,10 +231,13 @@ __global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t wor
       isolated = (d == 0);
       nonzero += isolated ? 0 : 1;
       mx = max(mx, (unsigned long long)d);
+      if (!isolated) atomicAdd(&s_hist[63 - __clzll((unsigned long long)d)], 1u);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, isolated);
     if (lane_id() == 0) iso[v0 >> 5] = bal;
   }
+  __syncthreads();
+  if (threadIdx.x < 32 && s_hist[threadIdx.x]) atomicAdd(&stats[2 + threadIdx.x], (unsigned long long)s_hist[threadIdx.x]);
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if (lane_id() == 0) atomicMax(&stats[1], mx);
   nonzero = block_sum_u64(nonzero, sh);
@@ -346,17 +354,24 @@ int finish_stats(dobfs_graph* g, cudaStream_t s) {
   g->words = ceil_div(g->n, 32);
   DOBFS_TRY(g->isolated.alloc(sizeof(uint32_t) * (size_t)g->words, s));
   DevBuf st;
-  DOBFS_TRY(st.alloc(sizeof(unsigned long long) * 2, s));
-  DOBFS_CUDA_TRY(cudaMemsetAsync(st.ptr, 0, sizeof(unsigned long long) * 2, s));
+  DOBFS_TRY(st.alloc(sizeof(unsigned long long) * 34, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(st.ptr, 0, sizeof(unsigned long long) * 34, s));
   k_deg_stats<OffT><<<grid_for(g->words * 32), kThreads, 0, s>>>(g->off.as<OffT>(), g->n, g->words,
                                                                   g->isolated.as<uint32_t>(),
                                                                   st.as<unsigned long long>());
   DOBFS_CUDA_TRY(cudaGetLastError());
-  unsigned long long h[2];
+  unsigned long long h[34];
   DOBFS_CUDA_TRY(cudaMemcpyAsync(h, st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   g->n_nonisolated = (int64_t)h[0];
   g->max_degree = (int64_t)h[1];
+  // vertices of degree >= 2^k; with the degree-sorted renumbering they are
+  // the first deg_ge[k] vertex IDs (every power of two is a class boundary)
+  int64_t acc = 0;
+  for (int k = 32; k >= 0; --k) {
+    if (k < 32) acc += (int64_t)h[2 + k];
+    g->deg_ge[k] = acc;
+  }
   return DOBFS_OK;
 }
 

@@ -14,6 +14,16 @@ struct MsGroup;
 // Sentinel edge key: a dropped entry (self-loop or duplicate). Sorts last.
 constexpr uint64_t kSentinelKey = ~0ull;
 
+// Degree-bin cutoffs of a run: 0 (the path's default) or within the ranges
+// the record buffers are sized for.
+inline bool cutoffs_valid(const dobfs_run_opts& o) {
+  const bool small_ok = o.td_small_max == 0 || (o.td_small_max >= 8 && o.td_small_max <= 256);
+  const bool chunk_ok = o.td_chunk == 0 || (o.td_chunk >= 256 && o.td_chunk <= 8192 && o.td_chunk % 128 == 0);
+  const bool scan_ok = o.bu_scan == 0 || (o.bu_scan >= 1 && o.bu_scan <= 256);
+  const bool split_ok = o.td_split_pct >= 0 && o.td_split_pct <= 100000;
+  return small_ok && chunk_ok && scan_ok && split_ok;
+}
+
 // Device-side control block of one BFS run (one per graph). The level loop
 // reads and updates it on the device; the host reads it only after a run.
 struct BfsCtl {
@@ -42,6 +52,8 @@ struct BfsCtl {
   int32_t pad2;
   // parameters
   int32_t mode, alpha, beta, static_pct, bu_steps, td_bm_div;
+  int32_t td_small, td_chunk, bu_scan, td_split_pct;  // degree-bin cutoffs; mixed-level threshold
+  int64_t split_w;      // mixed level: words [0, split_w) bottom-up, targets beyond them top-down (0: none)
   uint64_t sched_seed;
 };
 
@@ -70,6 +82,7 @@ struct dobfs_graph {
   dobfs::DevBuf off, cols;
   dobfs::DevBuf new2orig, orig2new;  // int32[n] each, only when reindexed
   dobfs::DevBuf isolated;            // bitmap: degree-0 vertices and bits >= n
+  int64_t deg_ge[33] = {};           // vertices of degree >= 2^k (a prefix of the IDs when reindexed)
   int64_t words = 0;                 // bitmap words = ceil(n/32)
 
   // BFS workspace
@@ -80,6 +93,7 @@ struct dobfs_graph {
   int64_t rec_cap = 0;
   dobfs::DevBuf deferred;             // int32[n]
   dobfs::DevBuf firstdeg;             // int2[n]: (first neighbour, degree)
+  dobfs::DevBuf degge;                // int64[33]: device copy of deg_ge
   dobfs::DevBuf ctl;                  // BfsCtl
   dobfs::DevBuf trace;                // LevelRec[kMaxTrace]
   dobfs::DevBuf out_stage;            // int32[2n] staging for host outputs (lazy)

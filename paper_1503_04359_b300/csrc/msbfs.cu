@@ -32,8 +32,9 @@ namespace dobfs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMsChunk = 1024;  // top-down chunk record length
-constexpr int kMsT = 32;        // bottom-up entries per thread before a row continues warp-wide
+constexpr int kMsChunk = 1024;  // top-down chunk record length (default; a run may set another)
+constexpr int kMsT = 32;        // bottom-up entries per thread before a row continues warp-wide (default)
+constexpr int kMsChunkMin = 256;
 constexpr int kMsCases = 2;
 constexpr int kMsCaseNone = 7;
 constexpr unsigned kIterMask = (1u << kMsPlanes) - 1u;
@@ -192,13 +193,14 @@ __global__ void k_ms_clear_next(MsArgs<OffT> A) {
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
   const uint64_t* front = (A.ctl->iter & 1) ? A.fb1 : A.fb0;
+  const int64_t chunk = A.ctl->td_chunk;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
     if (!front[v]) continue;
     const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
     if (d == 0) continue;
-    const unsigned nch = (unsigned)ceil_div(d, kMsChunk);
+    const unsigned nch = (unsigned)ceil_div(d, chunk);
     const unsigned base = atomicAdd(&A.ctl->n_rec, nch);
-    if ((int64_t)base + nch > A.rec_cap) continue;  // cannot happen: one record per kMsChunk entries or vertex
+    if ((int64_t)base + nch > A.rec_cap) continue;  // cannot happen: one record per kMsChunkMin entries or vertex
     for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2((int32_t)v, (int32_t)k);
   }
 }
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
+  const int64_t chunk = c->td_chunk;
   const unsigned lane = lane_id();
   unsigned long long ex = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -219,8 +222,8 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
     const int2 rc = A.rec[r];
     const int32_t u = rc.x;
     const unsigned long long fu = front[u];
-    const int64_t s = (int64_t)A.off[u] + (int64_t)rc.y * kMsChunk;
-    const int64_t e = min((int64_t)A.off[u + 1], s + kMsChunk);
+    const int64_t s = (int64_t)A.off[u] + (int64_t)rc.y * chunk;
+    const int64_t e = min((int64_t)A.off[u + 1], s + chunk);
     if (lane == 0) ex += (unsigned long long)(e - s);
     for (int64_t j = s + lane; j < e; j += 32) {
       const int32_t v = A.cols[j];
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
+  const int64_t scan = c->bu_scan;
   MsCount k;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long nx = next[v];
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
 }
 
 // Bottom-up, part 1: one vertex per thread. A vertex missing live lanes ORs
-// the frontier masks of its first kMsT neighbours and stops once every
+// the frontier masks of its first bu_scan neighbours and stops once every
 // missing lane is found; longer rows continue in k_ms_bu_long with the
 // partial mask kept in next[v].
 template <class OffT>
@@ -286,6 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
   const unsigned long long live = c->live;
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
+  const int64_t scan = c->bu_scan;
   MsCount k;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long s = A.seen[v];
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
       acc = __ldg(front + fd.x);
       j = 1;
       const int64_t o = (int64_t)A.off[v];
-      const int64_t lim = min((int64_t)fd.y, (int64_t)kMsT);
+      const int64_t lim = min((int64_t)fd.y, scan);
       while (j < lim && (acc & need) != need) {
         int32_t u[4];
 #pragma unroll
@@ -314,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
     }
     k.ex += (unsigned long long)j;
     const unsigned long long nw = acc & need;
-    if (nw != need && fd.y > kMsT) {
+    if (nw != need && fd.y > scan) {
       next[v] = nw;  // partial: k_ms_bu_long finishes the row
       enqueue_ms(&c->n_def, A.def, (int32_t)v);
       continue;
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
     const unsigned long long need = live & ~s;
     unsigned long long acc = next[v];
     const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
-    const int64_t s0 = o + kMsT;
+    const int64_t s0 = o + c->bu_scan;
     // 128 entries per warp step: one 16-byte column load and four frontier
     // masks per lane, then one test for the early exit
     for (int64_t base = s0 & ~3ll; base < e && (acc & need) != need; base += 128) {
@@ -653,7 +658,7 @@ int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out) {
   if (rc == DOBFS_OK) rc = m->fb1.alloc(vb, s);
   if (rc == DOBFS_OK) rc = m->planes.alloc(vb * kMsPlanes, s);
   const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
-  m->rec_cap = n_cand + g->nnz / kMsChunk + 64;
+  m->rec_cap = n_cand + g->nnz / kMsChunkMin + 64;
   if (rc == DOBFS_OK) rc = m->rec.alloc(sizeof(int2) * (size_t)m->rec_cap, s);
   if (rc == DOBFS_OK) rc = m->def.alloc(sizeof(int32_t) * (size_t)g->n, s);
   if (rc == DOBFS_OK) rc = m->ctl.alloc(sizeof(MsCtl), s);
@@ -690,6 +695,8 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   c.mode = o.direction;
   c.alpha = o.alpha;
   c.beta = o.beta;
+  c.td_chunk = o.td_chunk ? o.td_chunk : kMsChunk;
+  c.bu_scan = o.bu_scan ? o.bu_scan : kMsT;
   c.sched_seed = o.schedule_seed;
   DOBFS_CUDA_TRY(cudaMemcpyAsync(m->ctl.ptr, &c, sizeof(c), cudaMemcpyHostToDevice, s));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));  // c is on this stack
@@ -754,6 +761,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
   if (o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.alpha < 1 || o.beta < 1)
     return set_error(DOBFS_ERR_INVALID, "bad run options for a batch (direction must be auto, top-down, "
                                         "bottom-up or random)");
+  if (!cutoffs_valid(o)) return set_error(DOBFS_ERR_INVALID, "bad degree-bin cutoffs");
   std::vector<int32_t> hroots((size_t)n_roots);
   if (n_roots > 0) {
     if (is_device_ptr(roots))

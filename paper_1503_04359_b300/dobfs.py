@@ -55,7 +55,9 @@ class dobfs_graph_info(ctypes.Structure):
 class dobfs_run_opts(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("static_pct", ctypes.c_int32), ("bu_steps", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("schedule_seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("td_bitmap_div", ctypes.c_int32)]
+                ("schedule_seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("td_bitmap_div", ctypes.c_int32),
+                ("td_small_max", ctypes.c_int32), ("td_chunk", ctypes.c_int32), ("bu_scan", ctypes.c_int32),
+                ("td_split_pct", ctypes.c_int32)]
 
 
 class dobfs_run_stats(ctypes.Structure):
@@ -261,7 +263,9 @@ def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
 
 def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: int | None = None,
               static_pct: int | None = None, bu_steps: int | None = None, flags: int = 0, schedule_seed: int = 0,
-              stream=None, td_bitmap_div: int | None = None) -> dobfs_run_opts:
+              stream=None, td_bitmap_div: int | None = None, td_small_max: int | None = None,
+              td_chunk: int | None = None, bu_scan: int | None = None,
+              td_split_pct: int | None = None) -> dobfs_run_opts:
     o = dobfs_run_opts()
     _check(load().dobfs_run_opts_init(ctypes.byref(o)))
     o.direction = direction
@@ -275,6 +279,14 @@ def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: i
         o.bu_steps = bu_steps
     if td_bitmap_div is not None:
         o.td_bitmap_div = td_bitmap_div
+    if td_small_max is not None:
+        o.td_small_max = td_small_max
+    if td_chunk is not None:
+        o.td_chunk = td_chunk
+    if bu_scan is not None:
+        o.bu_scan = bu_scan
+    if td_split_pct is not None:
+        o.td_split_pct = td_split_pct
     o.flags = flags
     o.schedule_seed = schedule_seed
     o.stream = _stream(stream)

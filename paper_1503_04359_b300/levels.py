@@ -2,7 +2,8 @@
 
     python -m paper_1503_04359_b300.levels [--scale S] [--roots R] [--max-root-degree D]
                                            [--modes auto,topdown] [--no-reindex] [--json]
-                                           [--alpha A] [--beta B] [--td-bitmap-div D] [--batch K]
+                                           [--alpha A] [--beta B] [--td-bitmap-div D] [--td-split-pct P]
+                                           [--batch K]
 
 For every root and direction policy it runs one BFS driven from the host
 (``DOBFS_RUN_HOST_LOOP``), so each level's kernels are timed with CUDA
@@ -22,6 +23,9 @@ import sys
 import numpy as np
 
 
+DIRS = {0: "TD", 1: "BU", 2: "MX"}  # MX: mixed level (bottom-up for high degrees, top-down for the rest)
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--scale", type=int, default=28)
@@ -35,6 +39,7 @@ def main(argv=None) -> int:
     ap.add_argument("--beta", type=int, default=None)
     ap.add_argument("--td-bitmap-div", type=int, default=None,
                     help="top-down steps with m_f * div >= n mark a bitmap (0: never)")
+    ap.add_argument("--td-split-pct", type=int, default=None, help="mixed-level threshold (0: no mixed levels)")
     args = ap.parse_args(argv)
 
     import torch
@@ -56,7 +61,8 @@ def main(argv=None) -> int:
     lv = torch.empty(n, dtype=torch.int32, device="cuda")
     pa = torch.empty(n, dtype=torch.int32, device="cuda")
     out = []
-    knobs = {"alpha": args.alpha, "beta": args.beta, "td_bitmap_div": args.td_bitmap_div}
+    knobs = {"alpha": args.alpha, "beta": args.beta, "td_bitmap_div": args.td_bitmap_div,
+             "td_split_pct": args.td_split_pct}
     for name in args.modes.split(","):
         mode = modes[name]
         for r in roots:
@@ -70,7 +76,7 @@ def main(argv=None) -> int:
                    "per_level": []}
             for t in g.trace():
                 rec["per_level"].append({
-                    "level": t.level, "dir": "TD" if t.direction == 0 else "BU", "n_f": t.n_frontier,
+                    "level": t.level, "dir": DIRS.get(t.direction, "?"), "n_f": t.n_frontier,
                     "m_f": t.m_frontier, "n_next": t.n_next, "examined": t.edges_examined,
                     "scanned": t.vertices_scanned, "alg_bytes": t.alg_bytes, "ms": t.ms, "ms_main": t.ms_main,
                     "gbs": t.alg_bytes / (t.ms_main * 1e-3) / 1e9 if t.ms_main > 0 else 0.0})
@@ -96,7 +102,7 @@ def main(argv=None) -> int:
             tr = g.trace()
             rec = {"mode": name, "batch": args.batch, "graph_ms": st.device_ms, "host_loop_ms": sh.device_ms,
                    "levels": st.levels, "per_level": [
-                       {"level": t.level, "dir": "TD" if t.direction == 0 else "BU", "n_f": t.n_frontier,
+                       {"level": t.level, "dir": DIRS.get(t.direction, "?"), "n_f": t.n_frontier,
                         "m_f": t.m_frontier, "examined": t.edges_examined, "ms": t.ms} for t in tr]}
             out.append(rec)
             if not args.json:

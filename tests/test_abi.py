@@ -58,6 +58,13 @@ def test_argument_errors_without_gpu(lib):
     o = dobfs.dobfs_run_opts()
     assert lib.dobfs_run_opts_init(ctypes.byref(o)) == 0
     assert (o.direction, o.alpha, o.beta) == (dobfs.DOBFS_DIR_AUTO, 14, 24)
+    assert (o.td_bitmap_div, o.td_small_max, o.td_chunk, o.bu_scan, o.td_split_pct) == (2, 0, 0, 0, 150)
+    # the library writes exactly the bytes of the binding's struct: no field is missing at the end
+    buf = (ctypes.c_ubyte * (ctypes.sizeof(dobfs.dobfs_run_opts) + 64))(*([0xA5] * (ctypes.sizeof(dobfs.dobfs_run_opts) + 64)))
+    assert lib.dobfs_run_opts_init(ctypes.cast(buf, ctypes.POINTER(dobfs.dobfs_run_opts))) == 0
+    assert list(buf[ctypes.sizeof(dobfs.dobfs_run_opts):]) == [0xA5] * 64
+    last = dobfs.dobfs_run_opts.td_split_pct.offset
+    assert list(buf[last:last + 4]) == [150, 0, 0, 0]
     # allocator hook: both or neither
     assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(lambda n, s, c: None), dobfs.FREE_FN(), None) == dobfs.DOBFS_ERR_INVALID
     assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(), dobfs.FREE_FN(), None) == dobfs.DOBFS_OK

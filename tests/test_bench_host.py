@@ -1,0 +1,86 @@
+"""Host logic of bench.py: the replica aggregation over ranks (gloo, two
+processes on the CPU) and the lookup of committed ncu traffic."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, inputs, q):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=ws)
+    ms, edges = inputs[rank]
+    q.put((rank, bench.aggregate_ranks(dist, "cpu", ms, edges)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_ranks_gloo_two_processes():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    inputs = [(10.0, 1e9), (20.0, 3e9)]  # rank 1 is the slowest
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, inputs, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(2):
+        value, mx = got[r]
+        assert mx == 20.0
+        assert value == pytest.approx(4e9 / 0.020 / 1e9)
+
+
+def test_profiled_traffic_needs_matching_sources_and_workload(tmp_path, monkeypatch):
+    prof = tmp_path / "p.md"
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
+    rec = {"kernel_sha256": bench.kernel_sha256(), "workload": "rmat-s28-ef16-reindex", "bytes_per_level": 123}
+    prof.write_text("summary\n<!-- traffic %s -->\n" % json.dumps(rec))
+    assert bench.profiled_traffic("rmat-s28-ef16-reindex")["bytes_per_level"] == 123
+    assert bench.profiled_traffic("rmat-s24-ef16-reindex") is None
+    rec["kernel_sha256"] = "0" * 64
+    prof.write_text("<!-- traffic %s -->" % json.dumps(rec))
+    assert bench.profiled_traffic("rmat-s28-ef16-reindex") is None
+    prof.write_text("no record")
+    assert bench.profiled_traffic("rmat-s28-ef16-reindex") is None
+
+
+def test_ncu_summary_groups_bottom_up_levels(tmp_path):
+    from paper_1503_04359_b300 import ncu_summary
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    seq = [("k_bu<long, 1>", 9.0), ("k_bu_long<long>", 1.0),      # recovery of a top-down level: left out
+           ("k_bu<long, 0>", 100.0), ("k_bu_long<long>", 5.0),    # bottom-up level 1
+           ("k_td_bin<long, 0>", 7.0),
+           ("k_bu<long, 0>", 50.0), ("k_bu<long, 0>", 20.0), ("k_bu_long<long>", 2.0)]  # levels 2 and 3
+    for i, (name, mb) in enumerate(seq):
+        rows.append('"%d","void dobfs::(anonymous namespace)::%s(args)","dram__bytes_read.sum","Mbyte","%s"' % (i, name, mb))
+        rows.append('"%d","void dobfs::(anonymous namespace)::%s(args)","dram__bytes_write.sum","Kbyte","0"' % (i, name))
+        rows.append('"%d","void dobfs::(anonymous namespace)::%s(args)","gpu__time_duration.sum","usecond","10"' % (i, name))
+    p = tmp_path / "x.csv"
+    p.write_text("==PROF== noise\n" + "\n".join(rows) + "\n")
+    launches = ncu_summary.read_launches(str(p))
+    assert len(launches) == len(seq)
+    lv = ncu_summary.bu_levels(launches)
+    assert [x["bytes"] for x in lv] == [105e6, 50e6, 22e6]
+    assert [x["launches"] for x in lv] == [2, 1, 2]
+    table = {k: (c, t) for k, c, t, _ in ncu_summary.launch_table(launches)}
+    assert table["k_bu<long, 0>"] == (3, 30.0) and table["k_bu_long<long>"] == (3, 30.0)

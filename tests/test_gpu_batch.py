@@ -34,16 +34,16 @@ def s14():
     return spec, og, roots, lv
 
 
-def _batch(d, g, roots, mode=0, seed=0, host=False):
+def _batch(d, g, roots, mode=0, seed=0, host=False, **kw):
     n = g.n
     roots = np.asarray(roots, dtype=np.int32)
     if host:
         out = np.full((len(roots), n), 7, dtype=np.int32)
-        d.dobfs_run_batch(g.handle, roots, out, opts=d.make_opts(direction=mode, schedule_seed=seed))
+        d.dobfs_run_batch(g.handle, roots, out, opts=d.make_opts(direction=mode, schedule_seed=seed, **kw))
         return out
     out = torch.full((len(roots), n), 7, dtype=torch.int32, device="cuda")
     d.dobfs_run_batch(g.handle, torch.from_numpy(roots).cuda(), out,
-                      opts=d.make_opts(direction=mode, schedule_seed=seed))
+                      opts=d.make_opts(direction=mode, schedule_seed=seed, **kw))
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -55,6 +55,17 @@ def test_batch_levels_bit_exact(d, s14, mode, seed, flags):
     g = d.rmat_graph(spec, flags=flags)
     out = _batch(d, g, roots, mode, seed)          # one full group of 64 and a partial one of 36
     np.testing.assert_array_equal(out, ref)
+
+
+@pytest.mark.parametrize("cut", [dict(td_chunk=256, bu_scan=1), dict(td_chunk=8192, bu_scan=256),
+                                 dict(td_chunk=640, bu_scan=9)])
+def test_batch_degree_bin_cutoffs(d, s14, cut):
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=0x2)
+    for mode, seed in ((0, 0), (3, 4)):
+        np.testing.assert_array_equal(_batch(d, g, roots[:64], mode, seed, **cut), ref[:64])
+    with pytest.raises(d.DobfsError):
+        _batch(d, g, roots[:4], td_chunk=100)
 
 
 def test_batch_sizes_duplicates_host(d, s14):

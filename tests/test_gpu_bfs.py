@@ -198,19 +198,55 @@ def test_levels_bit_exact_s16_exact_reindex(d, s16):
 
 
 @pytest.mark.parametrize("div", [0, 1 << 30])
+@pytest.mark.parametrize("split", [0, 1, 150, 5000])
 @pytest.mark.parametrize("mode,seed", [(0, 0), (1, 0), (3, 5), (3, 9)])
-def test_topdown_bitmap_output(d, s16, div, mode, seed):
+def test_topdown_bitmap_output(d, s16, div, split, mode, seed):
     """Top-down levels with bitmap output and parent recovery (div = 2^30 makes
-    every top-down level take it) against the queue form (div = 0)."""
+    every top-down level take it) against the queue form (div = 0); on the
+    degree-sorted graph, bitmap-output levels are mixed levels unless split = 0
+    (split = 1 puts every vertex in the bottom-up part, 5000 only the hubs)."""
     spec, og, roots, ref_l, ref_p = s16
     for flags in (0, d.DOBFS_GRAPH_REINDEX):
         g = d.rmat_graph(spec, flags=flags)
+        mixed = 0
         for i, r in enumerate(roots[:4]):
-            lv, pa, st = _run(d, g, int(r), mode, seed, td_bitmap_div=div)
+            lv, pa, st = _run(d, g, int(r), mode, seed, td_bitmap_div=div, td_split_pct=split)
             _check_run(og, int(r), lv, pa, ref_l[i])
             assert st.teps_edges == oracle.teps_edges(og, ref_l[i])
-            lv, pa, _ = _run(d, g, int(r), mode, seed, flags=d.DOBFS_RUN_CANONICAL_PARENT, td_bitmap_div=div)
+            mixed += sum(t.direction == 2 for t in g.trace())
+            lv, pa, _ = _run(d, g, int(r), mode, seed, flags=d.DOBFS_RUN_CANONICAL_PARENT, td_bitmap_div=div,
+                             td_split_pct=split)
             _check_run(og, int(r), lv, pa, ref_l[i], ref_p[i])
+        if flags == 0 or split == 0 or div == 0:
+            assert mixed == 0
+        elif mode == 1 and split in (1, 150):  # every level top-down: the heavy ones are mixed
+            assert mixed > 0
+
+
+@pytest.mark.parametrize("cut", [dict(td_small_max=8, td_chunk=256, bu_scan=1),
+                                 dict(td_small_max=256, td_chunk=8192, bu_scan=256),
+                                 dict(td_small_max=33, td_chunk=1152, bu_scan=7)])
+@pytest.mark.parametrize("mode,seed", [(0, 0), (3, 5)])
+def test_degree_bin_cutoffs(d, s16, cut, mode, seed):
+    """Non-default degree-bin cutoffs change which kernel expands a row, never
+    the levels; the bitmap-output top-down form is covered too."""
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    for i, r in enumerate(roots[:4]):
+        for div in (0, 2, 1 << 30):
+            lv, pa, _ = _run(d, g, int(r), mode, seed, td_bitmap_div=div, **cut)
+            _check_run(og, int(r), lv, pa, ref_l[i])
+
+
+@pytest.mark.parametrize("bad", [dict(td_small_max=7), dict(td_small_max=257), dict(td_chunk=200),
+                                 dict(td_chunk=8320), dict(td_chunk=300), dict(bu_scan=-1), dict(bu_scan=257),
+                                 dict(td_split_pct=-1), dict(td_split_pct=100001)])
+def test_bad_cutoffs_rejected(d, s16, bad):
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec)
+    with pytest.raises(d.DobfsError) as e:
+        _run(d, g, int(roots[0]), **bad)
+    assert e.value.status == d.DOBFS_ERR_INVALID
 
 
 def test_canonical_parent_bit_exact(d, s16):
