@@ -6,9 +6,10 @@
 The launch table lists, per kernel, its launches, total gpu__time_duration
 and share of the captured total. The bottom-up view groups the captured
 launches into bottom-up levels (one k_bu launch in search mode plus the
-k_bu_long launch that follows it; a k_bu launch in recovery mode belongs to a
-bitmap-output top-down level and is left out) and reports DRAM bytes read +
-written per level, the figure bench.py compares with the algorithmic bytes.
+k_bu_long launch that follows it; the k_bu launches of bitmap-output and
+mixed levels, which are followed by a recovery-mode k_bu, are left out) and
+reports DRAM bytes read + written per level, the figure bench.py compares
+with the algorithmic bytes.
 """
 from __future__ import annotations
 
@@ -62,24 +63,26 @@ def launch_table(launches: list[dict]) -> list[tuple[str, int, float, float]]:
 
 
 def bu_levels(launches: list[dict]) -> list[dict]:
-    """Bottom-up levels: k_bu<..., 0> (search) + the k_bu_long right after it."""
+    """Bottom-up levels: a k_bu<..., 0> (search) launch directly followed by
+    k_bu_long. In a mixed level the search launch is followed by the parent
+    recovery (k_bu<..., 1>) instead; such launches are not bottom-up levels."""
     levels = []
-    cur = None
+    pending = None
     for L in launches:
         n = short_name(L["name"])
         m = L["metrics"]
         dram = m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
         t = m.get("gpu__time_duration.sum", 0.0)
         if re.match(r"k_bu<[^,]+,\s*(0|false)>", n):
-            cur = {"bytes": dram, "us": t, "launches": 1}
-            levels.append(cur)
-        elif n.startswith("k_bu_long") and cur is not None:
-            cur["bytes"] += dram
-            cur["us"] += t
-            cur["launches"] += 1
-            cur = None
+            pending = {"bytes": dram, "us": t, "launches": 1}
+        elif n.startswith("k_bu_long") and pending is not None:
+            pending["bytes"] += dram
+            pending["us"] += t
+            pending["launches"] += 1
+            levels.append(pending)
+            pending = None
         else:
-            cur = None
+            pending = None
     return levels
 
 

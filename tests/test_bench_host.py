@@ -67,10 +67,11 @@ def test_profiled_traffic_needs_matching_sources_and_workload(tmp_path, monkeypa
 def test_ncu_summary_groups_bottom_up_levels(tmp_path):
     from paper_1503_04359_b300 import ncu_summary
     rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
-    seq = [("k_bu<long, 1>", 9.0), ("k_bu_long<long>", 1.0),      # recovery of a top-down level: left out
+    seq = [("k_bu<long, 0>", 3.0), ("k_bu<long, 1>", 9.0), ("k_bu_long<long>", 1.0),  # a mixed level: left out
            ("k_bu<long, 0>", 100.0), ("k_bu_long<long>", 5.0),    # bottom-up level 1
            ("k_td_bin<long, 0>", 7.0),
-           ("k_bu<long, 0>", 50.0), ("k_bu<long, 0>", 20.0), ("k_bu_long<long>", 2.0)]  # levels 2 and 3
+           ("k_bu<long, 0>", 50.0), ("k_bu_long<long>", 0.0),     # level 2
+           ("k_bu<long, 0>", 20.0), ("k_bu_long<long>", 2.0)]     # level 3
     for i, (name, mb) in enumerate(seq):
         rows.append('"%d","void dobfs::(anonymous namespace)::%s(args)","dram__bytes_read.sum","Mbyte","%s"' % (i, name, mb))
         rows.append('"%d","void dobfs::(anonymous namespace)::%s(args)","dram__bytes_write.sum","Kbyte","0"' % (i, name))
@@ -81,6 +82,6 @@ def test_ncu_summary_groups_bottom_up_levels(tmp_path):
     assert len(launches) == len(seq)
     lv = ncu_summary.bu_levels(launches)
     assert [x["bytes"] for x in lv] == [105e6, 50e6, 22e6]
-    assert [x["launches"] for x in lv] == [2, 1, 2]
+    assert [x["launches"] for x in lv] == [2, 2, 2]
     table = {k: (c, t) for k, c, t, _ in ncu_summary.launch_table(launches)}
-    assert table["k_bu<long, 0>"] == (3, 30.0) and table["k_bu_long<long>"] == (3, 30.0)
+    assert table["k_bu<long, 0>"] == (4, 40.0) and table["k_bu_long<long>"] == (4, 40.0)
