@@ -7,11 +7,11 @@ and the faster one is kept:
 
   alpha/beta  the rule of the direction-optimizing BFS the paper builds on:
               top-down -> bottom-up when m_f * alpha > m_u, back when
-              n_f * beta < n (knobs: alpha, beta, td_bitmap_div);
+              n_f * beta < n (knobs: alpha, beta, td_bitmap_div, td_split_pct);
   static      the paper's own policy (Sec. 3.3): bottom-up once the next
               frontier, estimated as static_pct percent of the frontier's
               out-edges, exceeds n / beta, then bu_steps bottom-up levels
-              (knobs: static_pct, bu_steps, td_bitmap_div).
+              (knobs: static_pct, bu_steps, td_bitmap_div, td_split_pct).
 
 Both also tune the degree-bin cutoffs of the step kernels (td_small_max,
 td_chunk, bu_scan); batched runs tune alpha, beta, td_chunk and bu_scan.
@@ -45,12 +45,14 @@ ALPHA_BETA_GRID = {
     "alpha": [4, 8, 14, 24, 48],
     "beta": [8, 16, 24, 48, 96],
     "td_bitmap_div": [0, 1, 2, 4, 16],
+    "td_split_pct": [0, 75, 150, 300, 600],
     **CUTOFF_GRID,
 }
 STATIC_GRID = {
     "static_pct": [2, 5, 10, 20, 40],
     "bu_steps": [1, 2, 3, 4, 6],
     "td_bitmap_div": [0, 1, 2, 4, 16],
+    "td_split_pct": [0, 75, 150, 300, 600],
     **CUTOFF_GRID,
 }
 BATCH_GRID = {"alpha": [2, 4, 8, 14, 32], "beta": [8, 24, 64], "td_chunk": [256, 512, 1024, 2048, 4096],
@@ -145,18 +147,19 @@ def tune(g: dobfs.Graph, roots, cache_path: str | None = None, key: str | None =
     def measure(p):
         return _time_single(g, roots, p, level, parent, reps)
 
-    default = {"direction": dobfs.DOBFS_DIR_AUTO, "alpha": d.alpha, "beta": d.beta, "td_bitmap_div": d.td_bitmap_div}
+    default = {"direction": dobfs.DOBFS_DIR_AUTO, "alpha": d.alpha, "beta": d.beta, "td_bitmap_div": d.td_bitmap_div,
+               "td_split_pct": d.td_split_pct}
     default_ms = measure(default)
     per_policy = {}
     if "alpha_beta" in policies:
         grid = ALPHA_BETA_GRID
-        start = dict({k: default[k] for k in ("alpha", "beta", "td_bitmap_div")}, **CUTOFF_DEFAULTS)
+        start = dict({k: default[k] for k in ("alpha", "beta", "td_bitmap_div", "td_split_pct")}, **CUTOFF_DEFAULTS)
         b, ms, log = descend(grid, lambda p: measure(dict(p, direction=dobfs.DOBFS_DIR_AUTO)), start)
         per_policy["alpha_beta"] = (dict(b, direction=dobfs.DOBFS_DIR_AUTO), ms, len(log))
     if "static" in policies:
         grid = STATIC_GRID
-        start = dict({"static_pct": d.static_pct, "bu_steps": d.bu_steps, "td_bitmap_div": d.td_bitmap_div},
-                     **CUTOFF_DEFAULTS)
+        start = dict({"static_pct": d.static_pct, "bu_steps": d.bu_steps, "td_bitmap_div": d.td_bitmap_div,
+                      "td_split_pct": d.td_split_pct}, **CUTOFF_DEFAULTS)
         b, ms, log = descend(grid, lambda p: measure(dict(p, direction=dobfs.DOBFS_DIR_STATIC, beta=d.beta)), start)
         per_policy["static"] = (dict(b, direction=dobfs.DOBFS_DIR_STATIC, beta=d.beta), ms, len(log))
     name = min(per_policy, key=lambda k: per_policy[k][1])
