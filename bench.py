@@ -27,6 +27,7 @@ the timed pass uses the tuned options.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -238,14 +239,16 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
 
 
 def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000, 5000, 10000, 20000, 50000),
-                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 60.0, serve_opts=None) -> dict:
+                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 120.0, serve_opts=None) -> dict:
     """Open-loop serving: R-MAT graphs of the given scales resident, Poisson
     arrivals (seeded exponential gaps) at each rate, graph ids uniform, roots
     uniform over degree >= 1 vertices. Latency runs from the scheduled arrival
     to the completion the server reports (CLOCK_MONOTONIC), so a harness that
     falls behind its schedule is charged for it. Output buffers come from a
-    per-graph ring of device slots; the one-at-a-time baseline is the device
-    time of single-source runs (levels only) averaged over the same mix."""
+    per-graph pool of device slots (out_gb in all); a query whose graph has no
+    free slot waits in its graph's FIFO without holding up other graphs. The
+    one-at-a-time baseline is the device time of single-source runs (levels
+    only) averaged over the same mix."""
     graphs, pools, slots = [], [], []
     per_graph_bytes = out_gb * 1e9 / len(scales)
     base_ms = []
@@ -269,12 +272,14 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
     try:
         gids = [dobfs.dobfs_serve_add_graph(srv, g.handle) for g in graphs]
         for rate in rates:
+            st0 = dobfs.dobfs_serve_get_stats(srv)
             n_q = int(max(200, min(max_queries, rate * seconds)))
             rng = np.random.default_rng(0xA11CE + rate)
             gaps = rng.exponential(1.0 / rate, n_q)
             which = rng.integers(0, len(graphs), n_q)
             ridx = rng.integers(0, 1024, n_q)
             free = [list(range(s.shape[0])) for s in slots]
+            waiting = [collections.deque() for _ in graphs]  # arrived, no output slot yet (per graph)
             inflight = {}
             lat = []
             t0 = time.monotonic_ns() + 2_000_000
@@ -284,13 +289,16 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
             while len(lat) < n_q:
                 now = time.monotonic_ns()
                 while i < n_q and sched[i] <= now:
-                    gi = int(which[i])
-                    if not free[gi]:
-                        break  # no output slot: the query waits, its latency still counts from sched[i]
-                    slot = free[gi].pop()
-                    t = dobfs.dobfs_serve_submit(srv, gids[gi], int(pools[gi][ridx[i]]), slots[gi][slot])
-                    inflight[t] = (gi, slot, int(sched[i]))
+                    waiting[int(which[i])].append(i)
                     i += 1
+                for gi in range(len(graphs)):
+                    # a query without a free output slot of its graph waits (its latency still
+                    # counts from its scheduled arrival); other graphs' queries go ahead
+                    while waiting[gi] and free[gi]:
+                        j = waiting[gi].popleft()
+                        slot = free[gi].pop()
+                        t = dobfs.dobfs_serve_submit(srv, gids[gi], int(pools[gi][ridx[j]]), slots[gi][slot])
+                        inflight[t] = (gi, slot, int(sched[j]))
                 done = dobfs.dobfs_serve_collect(srv, col)
                 for t, r in done:
                     gi, slot, sc_ns = inflight.pop(t)
@@ -305,8 +313,17 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
                                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                                        "achieved_qps": n_q / span,
                                        "vs_one_at_a_time": (n_q / span) / one_at_a_time_qps}
+            st1 = dobfs.dobfs_serve_get_stats(srv)
+            coh = st1.cohorts - st0.cohorts
+            res["rates"][str(rate)]["server"] = {
+                "cohorts": int(coh), "mean_cohort_lanes": (st1.lanes_admitted - st0.lanes_admitted) / max(1, coh),
+                "group_steps": int(st1.group_steps - st0.group_steps),
+                "single_source_queries": int(st1.single_source - st0.single_source)}
         st = dobfs.dobfs_serve_get_stats(srv)
-        res["server"] = {"lane_groups_created": int(st.groups_created), "iterations": int(st.iterations)}
+        res["server"] = {"lane_groups_created": int(st.groups_created), "iterations": int(st.iterations),
+                         "cohorts": int(st.cohorts), "lanes_admitted": int(st.lanes_admitted),
+                         "mean_cohort_lanes": st.lanes_admitted / max(1, st.cohorts),
+                         "group_steps": int(st.group_steps), "single_source_queries": int(st.single_source)}
     finally:
         dobfs.dobfs_serve_destroy(srv)
         for g in graphs:

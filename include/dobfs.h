@@ -315,6 +315,10 @@ typedef struct {
   int64_t groups_created;  /* lane groups added beyond the initial ones */
   int64_t reserved_bytes;  /* device memory held against the budget */
   int64_t budget_bytes;
+  int64_t cohorts;         /* traversals started by an idle lane group */
+  int64_t lanes_admitted;  /* queries that took a lane (lanes_admitted / cohorts: mean cohort size) */
+  int64_t group_steps;     /* levels stepped by lane groups */
+  int64_t single_source;   /* queries served by the single-source path */
 } dobfs_serve_stats;
 
 int dobfs_serve_opts_init(dobfs_serve_opts* opts);

@@ -38,6 +38,7 @@ constexpr int kMsChunkMin = 256;
 constexpr int kMsCases = 2;
 constexpr int kMsCaseNone = 7;
 constexpr unsigned kIterMask = (1u << kMsPlanes) - 1u;
+constexpr int kFirstPlanes = 4;  // planes cleared by a reset: iterations below 16
 
 template <class OffT>
 struct MsArgs {
@@ -171,6 +172,20 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
       cudaGraphSetConditional(h_case, (unsigned)dir);
     }
   }
+}
+
+// Restarts the iteration count of a group none of whose lanes holds a query.
+// The releasing flushes cleared every lane's bits in the planes in use, so
+// all planes are clean; planes from kFirstPlanes up are cleared again when an
+// iteration first needs them. Discovery iterations then stay small: fewer
+// plane bits to set per discovery and fewer planes per flush.
+template <class OffT>
+__global__ void k_ms_rebase(MsArgs<OffT> A) {
+  MsCtl* c = A.ctl;
+  if (threadIdx.x != 0 || blockIdx.x != 0 || c->active != 0) return;
+  c->iter = 0;
+  if (c->n_planes > kFirstPlanes) c->n_planes = kFirstPlanes;
+  c->clear_plane = -1;
 }
 
 template <class OffT>
@@ -684,7 +699,7 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->seen.ptr, 0, vb, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb0.ptr, 0, vb, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb1.ptr, 0, vb, s));
-  constexpr int kFirstPlanes = 4;  // iterations below 16; later planes are cleared on first use
+  // iterations below 16 need kFirstPlanes planes; later planes are cleared on first use
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->planes.ptr, 0, vb * kFirstPlanes, s));
   MsCtl c;
   memset(&c, 0, sizeof(c));
@@ -735,6 +750,15 @@ int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_
     F.start[i] = start ? start[i] : 0;
   }
   return m->g->off64 ? ms_flush_impl<int64_t>(m, F) : ms_flush_impl<int32_t>(m, F);
+}
+
+int ms_group_rebase(MsGroup* m) {
+  if (m->g->off64)
+    k_ms_rebase<int64_t><<<1, 32, 0, m->stream>>>(ms_args<int64_t>(m));
+  else
+    k_ms_rebase<int32_t><<<1, 32, 0, m->stream>>>(ms_args<int32_t>(m));
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
 }
 
 int ms_group_read_ctl(MsGroup* m, MsCtl* c) {

@@ -79,5 +79,7 @@ int ms_group_case_async(MsGroup* m, int kase);
 
 // Reads the control block (synchronises the group's stream).
 int ms_group_read_ctl(MsGroup* m, MsCtl* c);
+// Iteration count back to 0 once no lane holds a query (on the group's stream).
+int ms_group_rebase(MsGroup* m);
 
 }  // namespace dobfs

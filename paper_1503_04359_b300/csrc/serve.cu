@@ -112,6 +112,7 @@ struct dobfs_server {
   int fatal = DOBFS_OK;
   std::string fatal_msg;
   int64_t iterations = 0, completed = 0, groups_created = 0;
+  int64_t cohorts = 0, lanes_admitted = 0, group_steps = 0, single_source = 0;  // scheduler thread writes
   bool waiting_gpu = false;  // scheduler thread only: some group's switch is still running
 };
 
@@ -207,6 +208,7 @@ bool schedule_once(dobfs_server* S) {
       q->state = kFlushing;
       q->ss_engine = e;
       e->ss_inflight += 1;
+      S->single_source += 1;
       work = true;
       std::lock_guard<std::mutex> lk(S->mu);
       S->flushing.push_back(q);
@@ -251,7 +253,7 @@ bool schedule_once(dobfs_server* S) {
       }
       G->in_flight = false;
       work = true;
-      const MsCtl c = *G->hctl;
+      MsCtl c = *G->hctl;
       // lanes whose frontier emptied; each flush is a pass over the whole
       // graph, so finished lanes are flushed together: when the group has no
       // live lane left, or once the oldest has waited flush_delay levels
@@ -292,6 +294,16 @@ bool schedule_once(dobfs_server* S) {
         }
         G->busy &= ~finished;
         G->finished = 0;
+        if (G->busy == 0) {
+          // every lane released: restart the iteration count (few discovery planes)
+          if (ms_group_rebase(G->ms) != DOBFS_OK) {
+            fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
+            return false;
+          }
+          c.iter = 0;
+          if (c.n_planes > 4) c.n_planes = 4;
+          G->hctl->iter = 0;
+        }
       }
       // admission into free lanes: an idle group starts a new cohort; a busy
       // group takes more lanes only within join_window levels of its
@@ -301,7 +313,8 @@ bool schedule_once(dobfs_server* S) {
       // another group of the graph (created while the budget allows).
       int32_t lanes[kMsLanes], roots[kMsLanes];
       int k = 0;
-      if (G->busy == 0) G->cohort_iter = c.iter;
+      const bool idle = (G->busy == 0);
+      if (idle) G->cohort_iter = c.iter;
       const bool light = S->opts.admit_div <= 0 || c.n_f * (int64_t)S->opts.admit_div < g->n;
       const bool can_join = (G->busy == 0) || (light && c.iter - G->cohort_iter <= S->opts.join_window);
       uint64_t freel = can_join ? ~G->busy : 0ull;
@@ -330,11 +343,17 @@ bool schedule_once(dobfs_server* S) {
         roots[k] = q->root;
         ++k;
       }
+      if (k) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->lanes_admitted += k;
+        S->cohorts += idle ? 1 : 0;
+      }
       if (k && ms_group_seed(G->ms, k, lanes, roots) != DOBFS_OK) {
         fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
         return false;
       }
       if (c.live || k) {
+        S->group_steps += 1;
         if (ms_group_case_async(G->ms, c.step_case) != DOBFS_OK) {
           fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
           return false;
@@ -629,6 +648,10 @@ int dobfs_serve_get_stats(dobfs_server* S, dobfs_serve_stats* st) {
   st->groups_created = S->groups_created;
   st->reserved_bytes = S->reserved;
   st->budget_bytes = S->budget;
+  st->cohorts = S->cohorts;
+  st->lanes_admitted = S->lanes_admitted;
+  st->group_steps = S->group_steps;
+  st->single_source = S->single_source;
   return S->fatal;
 }
 

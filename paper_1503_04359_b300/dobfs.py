@@ -89,7 +89,8 @@ class dobfs_query_result(ctypes.Structure):
 class dobfs_serve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("groups_created", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
-                ("budget_bytes", ctypes.c_int64)]
+                ("budget_bytes", ctypes.c_int64), ("cohorts", ctypes.c_int64), ("lanes_admitted", ctypes.c_int64),
+                ("group_steps", ctypes.c_int64), ("single_source", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
