@@ -196,7 +196,8 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
     deg = g.degrees()
     roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0xBA7C, n, max(sizes), deg > 0)
     stream = torch.cuda.current_stream()
-    opts = dobfs.make_opts(stream=stream)
+    opts = dobfs.make_opts(stream=stream)  # single-source defaults
+    bopts = dobfs.make_opts(stream=stream, alpha=dobfs.DOBFS_BATCH_ALPHA)  # the batch default
     lv = torch.empty(n, dtype=torch.int32, device="cuda")
     teps = []
     for r in roots[:64]:
@@ -218,12 +219,12 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
     mean_teps = float(np.mean(teps))
     for b in sizes:
         rt = torch.from_numpy(np.ascontiguousarray(roots[:b])).cuda()
-        dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=opts)
+        dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=bopts)
         times = []
         for _ in range(reps):
             torch.cuda.synchronize()
             e0.record(stream)
-            dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=opts)
+            dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=bopts)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))

@@ -243,9 +243,12 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
  * to n_roots separate dobfs_run calls. Levels only: parent_out must be NULL.
  * roots and level_out may be host or device memory. A lane runs at most 65535
  * levels. opts: direction auto, top-down, bottom-up or random; alpha, beta,
- * schedule_seed, stream. stats (nullable): device_ms, levels (deepest
- * group), edges_examined.
+ * td_chunk, bu_scan, schedule_seed, stream; with opts NULL, the defaults of
+ * dobfs_run_opts_init except alpha = DOBFS_BATCH_ALPHA (the union frontier of
+ * 64 lanes reaches a bottom-up size sooner than one lane's). stats
+ * (nullable): device_ms, levels (deepest group), edges_examined.
  */
+#define DOBFS_BATCH_ALPHA 4
 int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out, int32_t* parent_out,
                     const dobfs_run_opts* opts, dobfs_run_stats* stats);
 
@@ -282,7 +285,8 @@ typedef struct {
   int64_t max_device_bytes;     /* device-memory budget for lane groups and staging (0: 90% of free memory) */
   int32_t groups_per_graph;     /* lane groups created per graph up front (default 1) */
   int32_t max_groups_per_graph; /* upper bound on groups per graph (default 2) */
-  int32_t alpha, beta;          /* direction rule (defaults 14, 24) */
+  int32_t alpha, beta;          /* direction rule of the lane groups (defaults DOBFS_BATCH_ALPHA, 24);
+                                   the single-source path uses dobfs_run_opts_init's */
   int32_t direction;            /* DOBFS_DIR_AUTO / TOPDOWN / BOTTOMUP / RANDOM */
   int32_t admit_div;            /* a busy group admits new queries only at levels whose union frontier
                                    n_f satisfies n_f * admit_div < n (0: at every level; default 64) */

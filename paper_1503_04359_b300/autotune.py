@@ -190,7 +190,7 @@ def tune_batch(g: dobfs.Graph, roots, cache_path: str | None = None, key: str | 
         return min(dobfs.dobfs_run_batch(g.handle, rt, out, opts=o, want_stats=True).device_ms for _ in range(reps))
 
     d = dobfs.dobfs_run_opts_init()
-    start = dict({"alpha": d.alpha, "beta": d.beta}, **BATCH_DEFAULTS)
+    start = dict({"alpha": dobfs.DOBFS_BATCH_ALPHA, "beta": d.beta}, **BATCH_DEFAULTS)
     default_ms = measure(start)
     best, ms, log = descend(BATCH_GRID, measure, start)
     record = {"policy": "alpha_beta", "params": best, "ms": ms, "default_ms": default_ms, "roots": len(roots),

@@ -65,6 +65,7 @@ struct SeedArgs {
 struct FlushArgs {
   unsigned long long lanes;
   int32_t release;
+  int32_t vec;  // n % 4 == 0 and every flushed output row 16-byte aligned
   int32_t* out[kMsLanes];
   int32_t start[kMsLanes];
 };
@@ -633,11 +634,90 @@ int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
   return rc;
 }
 
+// The flush for up to four discovery planes (iterations below 16, the usual
+// case) with four consecutive original IDs per thread: one 16-byte map load
+// and one 16-byte store per lane row instead of four of each.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_flush4v(MsArgs<OffT> A, FlushArgs F) {
+  const int np = A.ctl->n_planes;
+  if (np > 4) return;
+  __shared__ int32_t* s_out[kMsLanes];
+  __shared__ int32_t s_start[kMsLanes];
+  if (threadIdx.x < kMsLanes) {
+    s_out[threadIdx.x] = F.out[threadIdx.x];
+    s_start[threadIdx.x] = F.start[threadIdx.x];
+  }
+  __syncthreads();
+  unsigned long long mu_back = 0;
+  const int64_t quads = A.n >> 2;
+  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < quads; qd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = qd * 4;
+    int64_t v[4];
+    if (A.o2n) {
+      const int4 m4 = __ldg(reinterpret_cast<const int4*>(A.o2n) + qd);
+      v[0] = m4.x;
+      v[1] = m4.y;
+      v[2] = m4.z;
+      v[3] = m4.w;
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = o + t;
+    }
+    unsigned long long sv[4], hit[4], q[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      sv[t] = A.seen[v[t]];
+      hit[t] = sv[t] & F.lanes;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) q[t][b] = (hit[t] && b < np) ? A.planes[(int64_t)b * A.n + v[t]] : 0ull;
+    if (F.release) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (!hit[t]) continue;
+        A.fb0[v[t]] &= ~F.lanes;
+        A.fb1[v[t]] &= ~F.lanes;
+        A.seen[v[t]] = sv[t] & ~F.lanes;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (b < np) A.planes[(int64_t)b * A.n + v[t]] = q[t][b] & ~F.lanes;
+        if (!(sv[t] & ~F.lanes)) mu_back += (unsigned long long)A.firstdeg[v[t]].y;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMsLanes; ++i) {
+      if (!((F.lanes >> i) & 1ull)) continue;
+      int32_t lev[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        unsigned T = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) T |= (unsigned)((q[t][b] >> i) & 1ull) << b;
+        lev[t] = ((hit[t] >> i) & 1ull) ? (int32_t)((T - (unsigned)s_start[i]) & kIterMask) : -1;
+      }
+      *reinterpret_cast<int4*>(s_out[i] + o) = make_int4(lev[0], lev[1], lev[2], lev[3]);
+    }
+  }
+  if (F.release) {
+    __shared__ unsigned long long sh[kThreads / 32];
+    mu_back = block_sum_u64(mu_back, sh);
+    if (threadIdx.x == 0) {
+      if (mu_back) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctl->m_u), mu_back);
+      if (blockIdx.x == 0) atomicAnd(&A.ctl->active, ~F.lanes);
+    }
+  }
+}
+
 template <class OffT>
 int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
   const int G = (int)std::min<int64_t>(ceil_div(m->g->n, kThreads), (int64_t)ms_grid(16));
   const MsArgs<OffT> A = ms_args<OffT>(m);
-  k_ms_flush<OffT, 4><<<G, kThreads, 0, m->stream>>>(A, F);
+  if (F.vec)
+    k_ms_flush4v<OffT><<<G, kThreads, 0, m->stream>>>(A, F);
+  else
+    k_ms_flush<OffT, 4><<<G, kThreads, 0, m->stream>>>(A, F);
   k_ms_flush<OffT, 8><<<G, kThreads, 0, m->stream>>>(A, F);
   k_ms_flush<OffT, 16><<<G, kThreads, 0, m->stream>>>(A, F);
   DOBFS_CUDA_TRY(cudaGetLastError());
@@ -745,9 +825,11 @@ int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_
   memset(&F, 0, sizeof(F));
   F.lanes = lanes;
   F.release = release ? 1 : 0;
+  F.vec = (m->g->n % 4 == 0) ? 1 : 0;
   for (int i = 0; i < kMsLanes; ++i) {
     F.out[i] = ((lanes >> i) & 1ull) ? out[i] : nullptr;
     F.start[i] = start ? start[i] : 0;
+    if (F.out[i] && (reinterpret_cast<uintptr_t>(F.out[i]) & 15)) F.vec = 0;
   }
   return m->g->off64 ? ms_flush_impl<int64_t>(m, F) : ms_flush_impl<int32_t>(m, F);
 }
@@ -781,6 +863,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
                      "dobfs_run_batch produces levels only; use dobfs_run for parents (parent_out must be NULL)");
   dobfs_run_opts o;
   dobfs_run_opts_init(&o);
+  o.alpha = DOBFS_BATCH_ALPHA;
   if (opts) o = *opts;
   if (o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.alpha < 1 || o.beta < 1)
     return set_error(DOBFS_ERR_INVALID, "bad run options for a batch (direction must be auto, top-down, "

@@ -192,9 +192,7 @@ bool schedule_once(dobfs_server* S) {
       Query* q = e->pending.front();
       e->pending.pop_front();
       dobfs_run_opts o;
-      dobfs_run_opts_init(&o);
-      o.alpha = S->opts.alpha;
-      o.beta = S->opts.beta;
+      dobfs_run_opts_init(&o);  // single-source defaults (the lane groups' alpha suits 64 lanes)
       o.stream = (void*)e->ss_stream;
       int rc = dobfs_run(e->g, q->root, q->out, nullptr, &o, nullptr);
       q->levels_h = e->ss_levels + (e->ss_next++ % kSsRing);
@@ -463,7 +461,7 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   o->max_device_bytes = 0;
   o->groups_per_graph = 1;
   o->max_groups_per_graph = 2;
-  o->alpha = 14;
+  o->alpha = DOBFS_BATCH_ALPHA;
   o->beta = 24;
   o->direction = DOBFS_DIR_AUTO;
   o->admit_div = 64;

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdobfs.so")
 
 DOBFS_OK, DOBFS_PENDING = 0, 1
 DOBFS_ERR_INVALID, DOBFS_ERR_OOM, DOBFS_ERR_CUDA = -1, -2, -3
+DOBFS_BATCH_ALPHA = 4
 DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY = -4, -5, -6
 
 DOBFS_GRAPH_SYMMETRIZE = 0x1
@@ -328,7 +329,7 @@ def dobfs_serve_opts_init() -> dobfs_serve_opts:
 
 
 def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 2,
-                    alpha: int = 14, beta: int = 24, direction: int = DOBFS_DIR_AUTO,
+                    alpha: int | None = None, beta: int | None = None, direction: int = DOBFS_DIR_AUTO,
                     admit_div: int | None = None, join_window: int | None = None,
                     flush_delay: int | None = None, gather_us: int | None = None, ss_max: int | None = None,
                     ss_backlog: int | None = None) -> dobfs_serve_opts:
@@ -349,7 +350,11 @@ def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_gr
     o.max_device_bytes = max_device_bytes
     o.groups_per_graph = groups_per_graph
     o.max_groups_per_graph = max_groups_per_graph
-    o.alpha, o.beta, o.direction = alpha, beta, direction
+    if alpha is not None:
+        o.alpha = alpha
+    if beta is not None:
+        o.beta = beta
+    o.direction = direction
     return o
 
 
