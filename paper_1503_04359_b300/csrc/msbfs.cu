@@ -742,6 +742,12 @@ int ms_group_case_async(MsGroup* m, int kase) {
   return m->g->off64 ? ms_launch_case<int64_t>(m, kase, m->stream) : ms_launch_case<int32_t>(m, kase, m->stream);
 }
 
+int64_t ms_group_bytes(const dobfs_graph* g) {
+  const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
+  return (int64_t)sizeof(uint64_t) * g->n * (3 + kMsPlanes) + (int64_t)sizeof(int2) * (n_cand + g->nnz / kMsChunkMin + 64) +
+         (int64_t)sizeof(int32_t) * g->n + (int64_t)sizeof(MsCtl);
+}
+
 int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out) {
   MsGroup* m = new (std::nothrow) MsGroup();
   if (!m) return set_error(DOBFS_ERR_OOM, "host allocation failed");

@@ -50,6 +50,8 @@ struct MsGroup {
   cudaGraphExec_t exec = nullptr;
 };
 
+// Device bytes of one lane group on g (what ms_group_create allocates).
+int64_t ms_group_bytes(const dobfs_graph* g);
 // Creates a group on g (allocates its masks); *out owned by the caller.
 int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out);
 void ms_group_destroy(MsGroup* m);

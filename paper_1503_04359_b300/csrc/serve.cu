@@ -119,11 +119,7 @@ struct dobfs_server {
 namespace dobfs {
 namespace {
 
-int64_t group_bytes(const dobfs_graph* g) {
-  const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
-  return (int64_t)sizeof(uint64_t) * g->n * (3 + kMsPlanes) + (int64_t)sizeof(int2) * (n_cand + g->nnz / 1024 + 64) +
-         (int64_t)sizeof(int32_t) * g->n;
-}
+int64_t group_bytes(const dobfs_graph* g) { return ms_group_bytes(g); }
 
 // Creates a lane group on engine e (scheduler thread, or add_graph).
 int add_group(dobfs_server* S, Engine* e) {
