@@ -95,6 +95,13 @@ def aggregate_ranks(dist, device, total_ms: float, total_edges: float) -> tuple[
     return sum(float(x[1]) for x in allt) / (mx * 1e-3) / 1e9, mx
 
 
+def gpu_bus_id(torch, dev: int) -> str:
+    """PCI bus id of CUDA device `dev` (as nvidia-smi and NVML name it), so the
+    samplers read the GPU this process runs on whatever the visible-device mapping."""
+    p = torch.cuda.get_device_properties(dev)
+    return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -111,8 +118,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu: str):
+        self.gpu = gpu  # nvidia-smi -i accepts an index or a PCI bus id
         self.proc = None
         self.path = None
 
@@ -159,6 +166,64 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def nvml_energy_reader(bus_id: str):
+    """A function returning the GPU's cumulative energy in mJ
+    (nvmlDeviceGetTotalEnergyConsumption through the driver's NVML library,
+    read only), or None where NVML or the counter is unavailable."""
+    import ctypes
+    try:
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(h)) != 0:
+            return None
+        mj = ctypes.c_ulonglong()
+
+        def read():
+            if lib.nvmlDeviceGetTotalEnergyConsumption(h, ctypes.byref(mj)) != 0:
+                raise RuntimeError("NVML energy counter read failed")
+            return int(mj.value)
+
+        read()
+        return read
+    except (OSError, AttributeError, RuntimeError):
+        return None
+
+
+def energy_pass(torch, g, roots, level, parent, opts, teps, bus_id: str, seconds: float = 2.0):
+    """Energy per BFS from the GPU's cumulative energy counter (NVML, read only),
+    over repeated passes of the timed roots lasting about `seconds`; None if
+    NVML is unavailable. MTEPS/W = traversed edges / joules / 1e6 (the
+    paper's energy metric, Sec. 4)."""
+    energy_mj = nvml_energy_reader(bus_id)
+    if energy_mj is None:
+        return None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for r in roots:
+        g.run(int(r), level, parent, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    reps = max(1, int(seconds / max(1e-3, e0.elapsed_time(e1) * 1e-3)))
+    torch.cuda.synchronize()
+    mj0 = energy_mj()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for r in roots:
+            g.run(int(r), level, parent, opts)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    mj1 = energy_mj()
+    joules = (mj1 - mj0) * 1e-3
+    edges = float(sum(teps)) * reps
+    n = reps * len(roots)
+    return {"bfs": n, "seconds": round(dt, 3), "joules_per_bfs": joules / n, "mean_power_w": joules / dt,
+            "mteps_per_w": edges / joules / 1e6 if joules > 0 else None,
+            "source": "NVML total energy counter (read only), graph-driven runs of the timed roots"}
 
 
 def cpu_baseline(scale: int = 22, n_roots: int = 4) -> dict:
@@ -465,7 +530,7 @@ def main() -> None:
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
+    with ClockSampler(gpu_bus_id(torch, dev)) as clk:
         wall0 = time.perf_counter()
         ev[0].record(stream)
         for i, r in enumerate(roots):
@@ -505,6 +570,8 @@ def main() -> None:
     dom_ms, dom_bytes = per_kind[dom]
     achieved = (dom_bytes / n_launch[dom]) / ((dom_ms / n_launch[dom]) * 1e-3) / 1e9 if n_launch[dom] else 0.0
     whole_gbs = (sum(alg_bytes) / (total_ms * 1e-3)) / 1e9
+
+    energy = energy_pass(torch, g, roots, level, parent, opts, teps, gpu_bus_id(torch, dev)) if rank == 0 else None
 
     # end to end through the C ABI with pinned host outputs (D2H inside the timed region)
     hl_lv = torch.empty(n, dtype=torch.int32, pin_memory=True)
@@ -589,6 +656,8 @@ def main() -> None:
     }
     if tuning is not None:
         result["tuning"] = tuning
+    if energy is not None:
+        result["energy"] = energy
     if cpu is not None:
         result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if batch is not None:
