@@ -76,6 +76,8 @@ const char* dobfs_last_error(void);
 #define DOBFS_GRAPH_VALIDATE 0x8u     /* reject input that is not symmetric */
 #define DOBFS_GRAPH_OFFSETS64 0x10u   /* store int64 row offsets even if int32 would do */
 #define DOBFS_GRAPH_REINDEX_EXACT 0x20u /* degree-sorted renumbering by exact degree (Sec. 3.4) */
+#define DOBFS_GRAPH_CHUNKED 0x40u     /* dobfs_graph_create_rmat: build in chunks of source rows even
+                                         if the one-shot key buffers would fit (same result) */
 
 /*
  * Builds a graph from CSR arrays: row_offsets[n_vertices+1] (int32, or int64

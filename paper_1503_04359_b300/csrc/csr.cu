@@ -375,6 +375,381 @@ int finish_stats(dobfs_graph* g, cudaStream_t s) {
   return DOBFS_OK;
 }
 
+// ---------------------------------------------------------------- chunked R-MAT build
+// The one-shot build holds 16 bytes of key scratch per directed entry (two
+// 64-bit key buffers), 275 GB at scale 29. The chunked build never holds
+// more than one chunk of keys: the counter-based edge stream is regenerated
+// for every chunk of source rows, and a chunk's keys are sorted,
+// de-duplicated and written straight into the final CSR. Two passes: the
+// first (original IDs) finds each vertex's degree and raw entry count, the
+// renumbering is computed from the degrees, the second writes the columns
+// in the final IDs. The result is identical to the one-shot build's.
+
+constexpr int kHistBuckets = 4096;
+
+// Raw directed entries (self-loops dropped) per bucket of source IDs.
+__global__ void __launch_bounds__(kThreads) k_rmat_src_hist(int64_t m, int scale, uint32_t ta, uint32_t tab,
+                                                            uint32_t tabc, uint64_t kp, uint64_t kq, int shift,
+                                                            unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[kHistBuckets];
+  for (int i = threadIdx.x; i < kHistBuckets; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t u, v;
+    gen_rmat_pair((uint64_t)i, scale, ta, tab, tabc, kp, kq, &u, &v);
+    if (u == v) continue;
+    atomicAdd(&h[u >> shift], 1u);
+    atomicAdd(&h[v >> shift], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHistBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+// Keys ((src - lo) << b | dst) of the directed entries whose source, after
+// the optional renumbering `map`, lies in [lo, hi); positions from one
+// warp-aggregated atomic per direction. Entries past `cap` are counted, not
+// written (the caller sizes chunks so that this does not happen).
+__global__ void __launch_bounds__(kThreads) k_keys_rmat_range(int64_t m, int scale, uint32_t ta, uint32_t tab,
+                                                              uint32_t tabc, uint64_t kp, uint64_t kq,
+                                                              const int32_t* __restrict__ map, int64_t lo,
+                                                              int64_t hi, int b, int64_t cap,
+                                                              uint64_t* __restrict__ keys,
+                                                              unsigned long long* __restrict__ count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; i0 < m; i0 += stride) {
+    const int64_t i = i0 + lane_id();
+    uint32_t u = 0, v = 0;
+    bool ok = i < m;
+    if (ok) {
+      gen_rmat_pair((uint64_t)i, scale, ta, tab, tabc, kp, kq, &u, &v);
+      ok = (u != v);
+      if (ok && map) {
+        u = (uint32_t)__ldg(map + u);
+        v = (uint32_t)__ldg(map + v);
+      }
+    }
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      const uint32_t src = dir ? v : u, dst = dir ? u : v;
+      const bool in = ok && (int64_t)src >= lo && (int64_t)src < hi;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (!bal) continue;
+      unsigned long long base = 0;
+      if (lane_id() == 0) base = atomicAdd(count, (unsigned long long)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const unsigned long long pos = base + (unsigned)__popc(bal & lanemask_lt());
+      if (in && (int64_t)pos < cap) keys[pos] = ((uint64_t)((int64_t)src - lo) << b) | (uint64_t)dst;
+    }
+  }
+}
+
+// raw[r] = first position of row r in the sorted chunk keys (r in [0, rows]).
+__global__ void k_row_starts(const uint64_t* __restrict__ keys, int64_t m, int b, int64_t rows,
+                             int64_t* __restrict__ raw) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t want = (uint64_t)r << b;
+    int64_t a = 0, z = m;
+    while (a < z) {
+      const int64_t mid = a + ((z - a) >> 1);
+      if (keys[mid] < want) a = mid + 1; else z = mid;
+    }
+    raw[r] = a;
+  }
+}
+
+// Degree (entries kept) and raw entry count of the chunk's rows.
+__global__ void k_chunk_degrees(const int64_t* __restrict__ off, const int64_t* __restrict__ raw, int64_t rows,
+                                int64_t lo, int32_t* __restrict__ deg, int32_t* __restrict__ rawdeg) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    deg[lo + r] = (int32_t)(off[r + 1] - off[r]);
+    rawdeg[lo + r] = (int32_t)(raw[r + 1] - raw[r]);
+  }
+}
+
+__global__ void k_vertex_keys_deg(const int32_t* __restrict__ deg, int64_t n, int b, int cls_bits, int exact,
+                                  uint64_t* __restrict__ keys) {
+  const uint64_t cmax = (1ull << cls_bits) - 1ull;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    keys[u] = ((cmax - degree_class((uint64_t)deg[u], exact != 0)) << b) | (uint64_t)u;
+}
+
+// In final order: d[i] = degree, r[i] = raw count of vertex n2o[i] (or i).
+__global__ void k_gather_counts(const int32_t* __restrict__ n2o, const int32_t* __restrict__ deg,
+                                const int32_t* __restrict__ rawdeg, int64_t n, int64_t* __restrict__ d,
+                                int64_t* __restrict__ r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = n2o ? n2o[i] : i;
+    d[i] = deg[o];
+    r[i] = rawdeg[o];
+  }
+}
+
+// Exclusive scan of x[0, n) in place with x[n] = total: tile sums, a scan of
+// the tile sums by one block, then each tile's scan plus its base.
+constexpr int kScanTile = kThreads * 16;
+
+__global__ void __launch_bounds__(kThreads) k_scan_tiles(const int64_t* __restrict__ x, int64_t n,
+                                                         unsigned long long* __restrict__ tsum) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+  unsigned long long acc = 0;
+  for (int64_t i = t0 + threadIdx.x; i < min(n, t0 + kScanTile); i += blockDim.x) acc += (unsigned long long)x[i];
+  acc = block_sum_u64(acc, sh);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(unsigned long long* __restrict__ tsum, int64_t tiles) {
+  __shared__ unsigned long long part[1024];
+  const int64_t per = ceil_div(tiles, (int64_t)blockDim.x);
+  const int64_t a = threadIdx.x * per, z = min(tiles, a + per);
+  unsigned long long s = 0;
+  for (int64_t i = a; i < z; ++i) s += tsum[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      const unsigned long long c = part[i];
+      part[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = part[threadIdx.x];
+  for (int64_t i = a; i < z; ++i) {
+    const unsigned long long c = tsum[i];
+    tsum[i] = run;
+    run += c;
+  }
+}
+
+template <class OutT>
+__global__ void __launch_bounds__(kThreads) k_scan_apply(const int64_t* __restrict__ x, int64_t n,
+                                                         const unsigned long long* __restrict__ tsum,
+                                                         OutT* __restrict__ out) {
+  __shared__ unsigned long long s_part[kThreads];
+  const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+  const int64_t t1 = min(n, t0 + kScanTile);
+  // each thread scans a contiguous run of 16, then a block scan of the runs
+  const int64_t a = t0 + (int64_t)threadIdx.x * 16, z = min(t1, a + 16);
+  unsigned long long local = 0;
+  for (int64_t i = a; i < z; ++i) local += (unsigned long long)x[i];
+  s_part[threadIdx.x] = local;
+  __syncthreads();
+  for (int o = 1; o < kThreads; o <<= 1) {
+    const unsigned long long y = (threadIdx.x >= (unsigned)o) ? s_part[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    s_part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  unsigned long long run = tsum[blockIdx.x] + s_part[threadIdx.x] - local;
+  for (int64_t i = a; i < z; ++i) {
+    const unsigned long long c = (unsigned long long)x[i];
+    out[i] = (OutT)run;
+    run += c;
+  }
+  if (z == n && a < z) out[n] = (OutT)run;  // the thread holding the last element writes the total
+}
+
+// out[0, n] = exclusive scan of x[0, n), out[n] = total. Returns the total.
+template <class OutT>
+int exclusive_scan(const int64_t* x, int64_t n, OutT* out, cudaStream_t s, int64_t* total) {
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, (int64_t)kScanTile));
+  DevBuf tsum;
+  DOBFS_TRY(tsum.alloc(sizeof(unsigned long long) * (size_t)tiles, s));
+  k_scan_tiles<<<(unsigned)tiles, kThreads, 0, s>>>(x, n, tsum.as<unsigned long long>());
+  k_scan_tile_sums<<<1, 1024, 0, s>>>(tsum.as<unsigned long long>(), tiles);
+  k_scan_apply<OutT><<<(unsigned)tiles, kThreads, 0, s>>>(x, n, tsum.as<unsigned long long>(), out);
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  OutT t = 0;
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(&t, out + n, sizeof(OutT), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  *total = (int64_t)t;
+  return DOBFS_OK;
+}
+
+struct RmatGen {
+  int scale;
+  int64_t m;  // pairs
+  uint32_t ta, tab, tabc;
+  uint64_t kp, kq;
+};
+
+// One chunk: keys of sources [lo, hi) (after `map`), sorted. *m_out = count.
+int chunk_keys(const RmatGen& G, const int32_t* map, int64_t lo, int64_t hi, int b, DevBuf& ka, DevBuf& kb,
+               int64_t cap, cudaStream_t s, uint64_t** sorted, int64_t* m_out) {
+  DevBuf cnt;
+  DOBFS_TRY(cnt.alloc(sizeof(unsigned long long), s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned long long), s));
+  k_keys_rmat_range<<<grid_for(G.m), kThreads, 0, s>>>(G.m, G.scale, G.ta, G.tab, G.tabc, G.kp, G.kq, map, lo, hi,
+                                                      b, cap, ka.as<uint64_t>(), cnt.as<unsigned long long>());
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  unsigned long long c = 0;
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(&c, cnt.ptr, sizeof(c), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  if ((int64_t)c > cap) return set_error(DOBFS_ERR_OOM, "internal: chunk of %llu keys exceeds %lld", c, (long long)cap);
+  const int rbits = std::max(1, bits_for(std::max<int64_t>(hi - lo, 2)));
+  DOBFS_TRY(radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), (int64_t)c, rbits + b, s, sorted));
+  *m_out = (int64_t)c;
+  return DOBFS_OK;
+}
+
+int read_i64(const int64_t* p, cudaStream_t s, int64_t* v) {
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(v, p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  return DOBFS_OK;
+}
+
+template <class OffT>
+int chunked_fill(dobfs_graph* g, const RmatGen& G, const int64_t* rawpre, DevBuf& ka, DevBuf& kb, int64_t cap,
+                 cudaStream_t s) {
+  const int b = g->bits;
+  const int64_t n = g->n;
+  const int32_t* map = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
+  OffT* off = g->off.as<OffT>();
+  int64_t lo = 0;
+  while (lo < n) {
+    // the longest run of rows from lo whose raw entries fit in the chunk
+    int64_t base = 0;
+    DOBFS_TRY(read_i64(rawpre + lo, s, &base));
+    int64_t a = lo + 1, z = n;  // largest hi in [lo+1, n] with rawpre[hi] - base <= cap
+    int64_t v = 0;
+    DOBFS_TRY(read_i64(rawpre + a, s, &v));
+    if (v - base > cap) return set_error(DOBFS_ERR_OOM, "a row exceeds the build chunk");
+    while (a < z) {
+      const int64_t mid = a + ((z - a + 1) >> 1);
+      DOBFS_TRY(read_i64(rawpre + mid, s, &v));
+      if (v - base <= cap) a = mid; else z = mid - 1;
+    }
+    const int64_t hi = a;
+    uint64_t* sorted = nullptr;
+    int64_t mc = 0;
+    DOBFS_TRY(chunk_keys(G, map, lo, hi, b, ka, kb, cap, s, &sorted, &mc));
+    int64_t o_lo = 0;
+    OffT t = 0;
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&t, off + lo, sizeof(OffT), cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    o_lo = (int64_t)t;
+    DevBuf offc;
+    DOBFS_TRY(offc.alloc(sizeof(int64_t) * (size_t)(hi - lo + 1), s));
+    int64_t kept = 0;
+    DOBFS_TRY(extract<int64_t>(sorted, mc, b, hi - lo, offc.as<int64_t>(), g->cols.as<int32_t>() + o_lo, s, &kept));
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&t, off + hi, sizeof(OffT), cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((int64_t)t - o_lo != kept) return set_error(DOBFS_ERR_CUDA, "internal: chunk entry count changed between passes");
+    lo = hi;
+  }
+  return DOBFS_OK;
+}
+
+int build_rmat_chunked(dobfs_graph* g, const RmatGen& G, uint32_t flags, int64_t cap, cudaStream_t s) {
+  const int b = g->bits;
+  const int64_t n = g->n;
+  DevBuf ka, kb;
+  DOBFS_TRY(ka.alloc(sizeof(uint64_t) * (size_t)cap, s));
+  DOBFS_TRY(kb.alloc(sizeof(uint64_t) * (size_t)cap, s));
+  // pass 1 (original IDs): plan chunks on a histogram of the sources
+  const int shift = std::max(0, b - 12);
+  std::vector<unsigned long long> hist(kHistBuckets, 0ull);
+  {
+    DevBuf dh;
+    DOBFS_TRY(dh.alloc(sizeof(unsigned long long) * kHistBuckets, s));
+    DOBFS_CUDA_TRY(cudaMemsetAsync(dh.ptr, 0, sizeof(unsigned long long) * kHistBuckets, s));
+    k_rmat_src_hist<<<grid_for(G.m), kThreads, 0, s>>>(G.m, G.scale, G.ta, G.tab, G.tabc, G.kp, G.kq, shift,
+                                                      dh.as<unsigned long long>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(hist.data(), dh.ptr, sizeof(unsigned long long) * kHistBuckets,
+                                   cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  DevBuf deg, rawdeg;
+  DOBFS_TRY(deg.alloc(sizeof(int32_t) * (size_t)n, s));
+  DOBFS_TRY(rawdeg.alloc(sizeof(int32_t) * (size_t)n, s));
+  {
+    const int64_t buckets = std::min<int64_t>(kHistBuckets, ceil_div(n, (int64_t)1 << shift));
+    int64_t k = 0;
+    while (k < buckets) {
+      int64_t k2 = k;
+      unsigned long long sum = 0;
+      while (k2 < buckets && sum + hist[k2] <= (unsigned long long)cap) sum += hist[k2++];
+      if (k2 == k) return set_error(DOBFS_ERR_OOM, "a source bucket exceeds the build chunk");
+      const int64_t lo = k << shift, hi = std::min<int64_t>(n, k2 << shift);
+      uint64_t* sorted = nullptr;
+      int64_t mc = 0;
+      DOBFS_TRY(chunk_keys(G, nullptr, lo, hi, b, ka, kb, cap, s, &sorted, &mc));
+      DevBuf offc, rawc;
+      DOBFS_TRY(offc.alloc(sizeof(int64_t) * (size_t)(hi - lo + 1), s));
+      DOBFS_TRY(rawc.alloc(sizeof(int64_t) * (size_t)(hi - lo + 1), s));
+      int64_t kept = 0;
+      DOBFS_TRY(extract<int64_t>(sorted, mc, b, hi - lo, offc.as<int64_t>(), nullptr, s, &kept));
+      k_row_starts<<<grid_for(hi - lo + 1), kThreads, 0, s>>>(sorted, mc, b, hi - lo, rawc.as<int64_t>());
+      k_chunk_degrees<<<grid_for(hi - lo), kThreads, 0, s>>>(offc.as<int64_t>(), rawc.as<int64_t>(), hi - lo, lo,
+                                                            deg.as<int32_t>(), rawdeg.as<int32_t>());
+      DOBFS_CUDA_TRY(cudaGetLastError());
+      DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+      k = k2;
+    }
+  }
+  // renumbering from the degrees
+  if (flags & (DOBFS_GRAPH_REINDEX | DOBFS_GRAPH_REINDEX_EXACT)) {
+    DevBuf vk, vt;
+    DOBFS_TRY(vk.alloc(sizeof(uint64_t) * (size_t)n, s));
+    DOBFS_TRY(vt.alloc(sizeof(uint64_t) * (size_t)n, s));
+    const int cls_bits = std::max(b, 6) + 1;
+    const int exact = (flags & DOBFS_GRAPH_REINDEX_EXACT) ? 1 : 0;
+    k_vertex_keys_deg<<<grid_for(n), kThreads, 0, s>>>(deg.as<int32_t>(), n, b, cls_bits, exact, vk.as<uint64_t>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    uint64_t* vsorted = nullptr;
+    DOBFS_TRY(radix_sort_u64(vk.as<uint64_t>(), vt.as<uint64_t>(), n, b + cls_bits, s, &vsorted));
+    DOBFS_TRY(g->new2orig.alloc(sizeof(int32_t) * (size_t)n, s));
+    DOBFS_TRY(g->orig2new.alloc(sizeof(int32_t) * (size_t)n, s));
+    k_maps<<<grid_for(n), kThreads, 0, s>>>(vsorted, n, b, g->new2orig.as<int32_t>(), g->orig2new.as<int32_t>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    g->reindexed = true;
+  }
+  // row offsets (final order) and raw-count prefix for the chunks of pass 2
+  DevBuf dnew, rnew, rawpre;
+  DOBFS_TRY(dnew.alloc(sizeof(int64_t) * (size_t)n, s));
+  DOBFS_TRY(rnew.alloc(sizeof(int64_t) * (size_t)n, s));
+  k_gather_counts<<<grid_for(n), kThreads, 0, s>>>(g->reindexed ? g->new2orig.as<int32_t>() : nullptr,
+                                                  deg.as<int32_t>(), rawdeg.as<int32_t>(), n, dnew.as<int64_t>(),
+                                                  rnew.as<int64_t>());
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  deg.reset();
+  rawdeg.reset();
+  DOBFS_TRY(rawpre.alloc(sizeof(int64_t) * (size_t)(n + 1), s));
+  int64_t raw_total = 0, nnz = 0;
+  DOBFS_TRY(exclusive_scan<int64_t>(rnew.as<int64_t>(), n, rawpre.as<int64_t>(), s, &raw_total));
+  rnew.reset();
+  // nnz first (the offset width depends on it), then the offsets
+  {
+    DevBuf tmp;
+    DOBFS_TRY(tmp.alloc(sizeof(int64_t) * (size_t)(n + 1), s));
+    DOBFS_TRY(exclusive_scan<int64_t>(dnew.as<int64_t>(), n, tmp.as<int64_t>(), s, &nnz));
+    g->nnz = nnz;
+    g->off64 = (flags & DOBFS_GRAPH_OFFSETS64) || nnz > (int64_t)INT32_MAX;
+    if (g->off64) {
+      g->off = std::move(tmp);
+    } else {
+      DOBFS_TRY(g->off.alloc(sizeof(int32_t) * (size_t)(n + 1), s));
+      DOBFS_TRY(exclusive_scan<int32_t>(dnew.as<int64_t>(), n, g->off.as<int32_t>(), s, &nnz));
+    }
+  }
+  dnew.reset();
+  DOBFS_TRY(g->cols.alloc(sizeof(int32_t) * (size_t)(nnz + 4), s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->cols.as<int32_t>() + nnz, 0, sizeof(int32_t) * 4, s));
+  // pass 2: the columns, chunk by chunk of final row IDs
+  if (g->off64)
+    DOBFS_TRY(chunked_fill<int64_t>(g, G, rawpre.as<int64_t>(), ka, kb, cap, s));
+  else
+    DOBFS_TRY(chunked_fill<int32_t>(g, G, rawpre.as<int64_t>(), ka, kb, cap, s));
+  rawpre.reset();
+  ka.reset();
+  kb.reset();
+  return g->off64 ? finish_stats<int64_t>(g, s) : finish_stats<int32_t>(g, s);
+}
+
 }  // namespace
 
 int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t m, uint32_t flags, cudaStream_t s) {
@@ -637,8 +1012,22 @@ int dobfs_graph_create_rmat(int scale, int64_t n_pairs, uint32_t t_a, uint32_t t
   int rc = start_timer(s, &e0, &e1);
   if (rc == DOBFS_OK) {
     rc = [&]() -> int {
-      DevBuf keys;
       const int64_t m = 2 * n_pairs;
+      // one-shot build: two 64-bit key buffers; chunked when they do not fit
+      // next to the result (or when asked)
+      size_t free_b = 0, total_b = 0;
+      DOBFS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+      const int64_t result_b = (int64_t)sizeof(int32_t) * m + 24 * (int64_t)g->n;
+      const bool chunked = (flags & DOBFS_GRAPH_CHUNKED) || (16 * m + result_b > (int64_t)(0.9 * (double)free_b));
+      if (chunked && n_pairs > 0) {
+        RmatGen G{scale, n_pairs, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed)};
+        int64_t cap = ((int64_t)(0.85 * (double)free_b) - result_b) / 16;
+        if (cap < std::min<int64_t>(m, 1 << 16)) return set_error(DOBFS_ERR_OOM, "not enough device memory for a build chunk");
+        if (flags & DOBFS_GRAPH_CHUNKED) cap = std::min<int64_t>(cap, std::max<int64_t>(1024, m / 7 + 1));  // several chunks
+        cap = std::min<int64_t>(cap, m);
+        return build_rmat_chunked(g, G, flags, cap, s);
+      }
+      DevBuf keys;
       DOBFS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s));
       if (n_pairs > 0)
         k_keys_rmat<<<grid_for(n_pairs), kThreads, 0, s>>>(n_pairs, scale, t_a, t_ab, t_abc, gen_key_pairs(seed),

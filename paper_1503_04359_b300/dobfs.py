@@ -33,6 +33,7 @@ DOBFS_GRAPH_DEVICE_PTRS = 0x4
 DOBFS_GRAPH_VALIDATE = 0x8
 DOBFS_GRAPH_OFFSETS64 = 0x10
 DOBFS_GRAPH_REINDEX_EXACT = 0x20
+DOBFS_GRAPH_CHUNKED = 0x40
 
 DOBFS_DIR_AUTO, DOBFS_DIR_TOPDOWN, DOBFS_DIR_BOTTOMUP, DOBFS_DIR_RANDOM, DOBFS_DIR_STATIC = 0, 1, 2, 3, 4
 DOBFS_RUN_CANONICAL_PARENT = 0x1

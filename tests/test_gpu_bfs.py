@@ -109,6 +109,28 @@ def test_csr_build_reindex(d, scale, flags, exact):
     assert g.info.reindexed == 1
 
 
+@pytest.mark.parametrize("scale", [10, 14, 16])
+@pytest.mark.parametrize("flags", [0, 0x2, 0x2 | 0x10, 0x20])
+def test_chunked_rmat_build_matches_one_shot(d, scale, flags):
+    """The chunked build (edge stream regenerated per chunk of source rows,
+    forced here with several chunks) gives the same CSR, renumbering and
+    statistics as the one-shot build."""
+    spec = inputs.rmat(scale)
+    g1 = d.rmat_graph(spec, flags=flags)
+    g2 = d.rmat_graph(spec, flags=flags | d.DOBFS_GRAPH_CHUNKED)
+    i1, i2 = g1.info, g2.info
+    for f in ("n_vertices", "n_entries", "n_nonisolated", "max_degree", "offsets_int64", "reindexed"):
+        assert getattr(i1, f) == getattr(i2, f), f
+    for a, b in zip(g1.export(), g2.export()):
+        np.testing.assert_array_equal(a, b)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 3, og.degrees() > 0)
+    ref, _ = oracle.bfs_many(og, roots, want_parent=False)
+    for k, r in enumerate(roots):
+        lv, pa, _ = _run(d, g2, int(r))
+        _check_run(og, int(r), lv, pa, ref[k])
+
+
 def test_pairs_and_csr_inputs(d):
     rng = np.random.default_rng(11)
     n = 3000

@@ -3,8 +3,9 @@
 - R-MAT scale 22 (int64 offsets, renumbered), 64 seeded roots: levels
   bit-exact with the oracle's serial BFS on its own CSR, parents valid,
   canonical parents bit-exact.
-- R-MAT scale 28 and Chung-Lu 2^26: the oracle cannot hold a CSR within the
-  test's time, so the GPU results are checked by the streaming invariant
+- R-MAT scale 28, R-MAT scale 29 (chunked build) and Chung-Lu 2^26: the
+  oracle cannot hold a CSR within the test's time, so the GPU results are
+  checked by the streaming invariant
   checker over the regenerated (R-MAT) or host-generated (Chung-Lu) pairs.
   The invariants characterise BFS levels exactly (level = distance), and the
   checker computes the canonical parent by its definition, compared
@@ -92,6 +93,30 @@ def test_config3a_rmat28_streaming_check(d):
     assert rc.tolist() == [0, 0, 0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
     np.testing.assert_array_equal(parents[2:], canon[2:])
     assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(4))
+
+
+def test_rmat29_chunked_build_streaming_check(d):
+    """Scale 29 (17 G stored entries): too large for the one-shot build's key
+    buffers, so the graph is built in chunks of source rows; one root with
+    any parents, one with canonical parents, checked over the regenerated
+    pair stream."""
+    spec = inputs.rmat(29)
+    src, dst = inputs.rmat_pairs(spec, count=1 << 20)
+    roots = _pair_roots(src, dst, inputs.root_seed(spec.seed), 2)
+    del src, dst
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    assert g.info.offsets_int64 == 1 and g.info.n_entries > (1 << 33)
+    lv, pa = _gpu_runs(d, g, roots[:1])
+    lv_c, pa_c = _gpu_runs(d, g, roots[1:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    g.close()
+    torch.cuda.empty_cache()
+    levels = np.concatenate([lv, lv_c])
+    parents = np.concatenate([pa, pa_c])
+    del lv, pa, lv_c, pa_c
+    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, levels, parents, want_canon=True)
+    assert rc.tolist() == [0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
+    np.testing.assert_array_equal(parents[1:], canon[1:])
+    assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(2))
 
 
 def test_config3b_chunglu26_streaming_check(d):
