@@ -243,6 +243,7 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
  * alpha/beta rule on the union of the lanes' frontiers. level_out[n_roots][n]
  * (int32, row r for roots[r], original IDs) receives the levels, identical
  * to n_roots separate dobfs_run calls. Levels only: parent_out must be NULL.
+ * n_roots = 0 does nothing (roots and level_out may then be NULL).
  * roots and level_out may be host or device memory. A lane runs at most 65535
  * levels. opts: direction auto, top-down, bottom-up or random; alpha, beta,
  * td_chunk, bu_scan, schedule_seed, stream; with opts NULL, the defaults of

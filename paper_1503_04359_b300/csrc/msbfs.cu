@@ -862,7 +862,7 @@ using namespace dobfs;
 extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out,
                                int32_t* parent_out, const dobfs_run_opts* opts, dobfs_run_stats* stats) {
   clear_error();
-  if (!g || !roots || !level_out || n_roots < 0)
+  if (!g || n_roots < 0 || (n_roots > 0 && (!roots || !level_out)))
     return set_error(DOBFS_ERR_INVALID, "graph, roots and level_out are required");
   if (parent_out)
     return set_error(DOBFS_ERR_INVALID,
@@ -875,6 +875,10 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     return set_error(DOBFS_ERR_INVALID, "bad run options for a batch (direction must be auto, top-down, "
                                         "bottom-up or random)");
   if (!cutoffs_valid(o)) return set_error(DOBFS_ERR_INVALID, "bad degree-bin cutoffs");
+  if (n_roots == 0) {  // nothing to run (roots and level_out may be NULL)
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return DOBFS_OK;
+  }
   std::vector<int32_t> hroots((size_t)n_roots);
   if (n_roots > 0) {
     if (is_device_ptr(roots))
