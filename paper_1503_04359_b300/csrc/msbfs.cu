@@ -35,6 +35,7 @@ constexpr int kThreads = 256;
 constexpr int kMsChunk = 1024;  // top-down chunk record length (default; a run may set another)
 constexpr int kMsT = 32;        // bottom-up entries per thread before a row continues warp-wide (default)
 constexpr int kMsChunkMin = 256;
+constexpr int kMsLongChunk = 4096;  // entries of a long bottom-up row per warp (chunk record)
 constexpr int kMsCases = 2;
 constexpr int kMsCaseNone = 7;
 constexpr unsigned kIterMask = (1u << kMsPlanes) - 1u;
@@ -336,8 +337,16 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
     k.ex += (unsigned long long)j;
     const unsigned long long nw = acc & need;
     if (nw != need && fd.y > scan) {
-      next[v] = nw;  // partial: k_ms_bu_long finishes the row
+      // partial: k_ms_bu_long scans the rest of the row in chunk records,
+      // k_ms_bu_fin then records the vertex
+      next[v] = nw;
       enqueue_ms(&c->n_def, A.def, (int32_t)v);
+      if ((int64_t)fd.y - scan > kMsLongChunk) {  // chunks after the first go to chunk records
+        const unsigned nch = (unsigned)ceil_div((int64_t)fd.y - scan, (int64_t)kMsLongChunk);
+        const unsigned base = atomicAdd(&c->n_rec, nch - 1);
+        for (unsigned r = 1; r < nch; ++r)
+          if ((int64_t)base + r - 1 < A.rec_cap) A.rec[base + r - 1] = make_int2((int32_t)v, (int32_t)r);
+      }
       continue;
     }
     next[v] = nw;
@@ -363,8 +372,13 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
   }
 }
 
-// Bottom-up, part 2: the rest of long rows, one warp per row, with the
-// early-exit test after every 32 entries.
+// Bottom-up, part 2: the rest of the deferred rows, one warp per row for its
+// first kMsLongChunk entries, then one warp per chunk record for the further
+// chunks of longer rows (a hub row is spread over many warps). The records
+// come after the rows in the work order, so a record usually starts once its
+// row's first chunk is done: it skips if the lanes found so far (next[v],
+// OR-ed in by every warp of the row) already cover the row, and re-checks
+// every 1024 entries. Early-exit test after every 128 entries.
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
@@ -372,59 +386,90 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
   const unsigned long long live = c->live;
-  const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
-  const int np = c->n_planes;
+  const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
   const int64_t nd = c->n_def;
+  const int64_t scan = c->bu_scan;
   const unsigned lane = lane_id();
-  MsCount k;
+  unsigned long long ex = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
-    const int32_t v = A.def[i];
-    const unsigned long long s = A.seen[v];
-    const unsigned long long need = live & ~s;
-    unsigned long long acc = next[v];
-    const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
-    const int64_t s0 = o + c->bu_scan;
-    // 128 entries per warp step: one 16-byte column load and four frontier
-    // masks per lane, then one test for the early exit
-    for (int64_t base = s0 & ~3ll; base < e && (acc & need) != need; base += 128) {
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd + nrec; i += warps) {
+    int32_t v;
+    int64_t s0, e0;
+    if (i < nd) {  // a deferred row: the first chunk of the rest
+      v = A.def[i];
+      const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      s0 = o + scan;
+      e0 = min(e, s0 + kMsLongChunk);
+    } else {
+      const int2 rc = A.rec[i - nd];
+      v = rc.x;
+      const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      s0 = o + scan + (int64_t)rc.y * kMsLongChunk;
+      e0 = min(e, s0 + kMsLongChunk);
+    }
+    const unsigned long long need = live & ~A.seen[v];
+    unsigned long long acc = __ldcg(next + v);
+    int step = 0;
+    for (int64_t base = s0 & ~3ll; base < e0 && (acc & need) != need; base += 128, ++step) {
+      if (i >= nd && (step & 7) == 7) {
+        acc |= __ldcg(next + v);  // what the row's other warps found
+        if ((acc & need) == need) break;
+      }
       const int64_t p = base + 4 * (int64_t)lane;
       unsigned long long x = 0;
-      if (p < e) {
+      if (p < e0) {
         const int4 c4 = *reinterpret_cast<const int4*>(A.cols + p);
         const int32_t us[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (p + t >= s0 && p + t < e) x |= __ldg(front + us[t]);
+          if (p + t >= s0 && p + t < e0) x |= __ldg(front + us[t]);
       }
       acc |= warp_or64(x);
-      if (lane == 0) k.ex += (unsigned long long)(min(e, base + 128) - max(s0, base));
+      if (lane == 0) ex += (unsigned long long)(min(e0, base + 128) - max(s0, base));
     }
     const unsigned long long nw = acc & need;
-    if (lane == 0) {
-      next[v] = nw;
-      if (nw) {
-        A.seen[v] = s | nw;
-        set_planes(A, v, nw, T, np);
-        const int64_t d = e - o;
-        k.n += 1;
-        k.m += (unsigned long long)d;
-        if (!s) k.mu += (unsigned long long)d;
-        k.live |= nw;
-      }
-    }
+    if (lane == 0 && nw) atomicOr(reinterpret_cast<unsigned long long*>(next + v), nw);
+  }
+  if (lane != 0) ex = 0;
+  ex = block_sum_u64(ex, sh);
+  if (threadIdx.x == 0 && ex) atomicAdd(&c->nx_examined, ex);
+}
+
+// Bottom-up, part 3: the deferred vertices, once every chunk of their rows
+// has been scanned: record the lanes found.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_ms_bu_fin(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
+  MsCtl* c = A.ctl;
+  uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
+  const unsigned long long live = c->live;
+  const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
+  const int np = c->n_planes;
+  const int64_t nd = c->n_def;
+  MsCount k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = A.def[i];
+    const unsigned long long s = A.seen[v];
+    const unsigned long long nw = next[v] & live & ~s;
+    next[v] = nw;
+    if (!nw) continue;
+    A.seen[v] = s | nw;
+    set_planes(A, v, nw, T, np);
+    const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
+    k.n += 1;
+    k.m += (unsigned long long)d;
+    if (!s) k.mu += (unsigned long long)d;
+    k.live |= nw;
   }
   const unsigned long long lv = warp_or64(k.live);
-  if (lane == 0 && lv) atomicOr(&c->nx_live, lv);
+  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
   k.n = block_sum_u64(k.n, sh);
   k.m = block_sum_u64(k.m, sh);
   k.mu = block_sum_u64(k.mu, sh);
-  k.ex = block_sum_u64(k.ex, sh);
   if (threadIdx.x == 0) {
     if (k.n) atomicAdd(&c->nx_n, k.n);
     if (k.m) atomicAdd(&c->nx_m, k.m);
     if (k.mu) atomicAdd(&c->nx_mu, k.mu);
-    if (k.ex) atomicAdd(&c->nx_examined, k.ex);
   }
 }
 
@@ -536,6 +581,7 @@ int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
   } else {
     k_ms_bu<OffT><<<G, kThreads, 0, s>>>(A);
     k_ms_bu_long<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu_fin<OffT><<<G, kThreads, 0, s>>>(A);
   }
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
