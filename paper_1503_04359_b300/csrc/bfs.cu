@@ -180,6 +180,7 @@ __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t
   c->m_u = A.nnz - d;
   c->nx_n = c->nx_m = c->nx_examined = c->nx_scanned = 0;
   c->q_tail = c->n_rec = c->n_def = c->conv_tail = 0;
+  c->out_next = 0;
   c->reached = 1;
   c->teps2 = d;
   c->examined = 0;
@@ -708,64 +709,75 @@ __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int3
                                                      int32_t root_orig, int32_t* __restrict__ level_out,
                                                      int32_t* __restrict__ parent_out) {
   constexpr int kQ = 2;  // quads per thread and step: eight independent gathers in flight
+  constexpr int64_t kOutChunk = 2048;  // quads per chunk (8192 original IDs)
   const int32_t root = A.o2n ? __ldg(A.o2n + root_orig) : root_orig;
   const int64_t quads = A.n >> 2;
   const bool vec = ((reinterpret_cast<uintptr_t>(level_out) | reinterpret_cast<uintptr_t>(parent_out)) & 15) == 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t q0 = tid; q0 < quads; q0 += stride * kQ) {
-    int32_t v[kQ][4];
-    bool inq[kQ];
+  // blocks take chunks of kOutChunk quads in turn (one counter): each block
+  // streams a contiguous stretch of the map and the outputs
+  __shared__ int64_t s_chunk;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = (int64_t)atomicAdd(&A.ctl->out_next, 1u);
+    __syncthreads();
+    const int64_t qlo = s_chunk * kOutChunk, qhi = min(quads, qlo + kOutChunk);
+    __syncthreads();
+    if (qlo >= quads) break;
+    for (int64_t q0 = qlo + threadIdx.x; q0 < qhi; q0 += (int64_t)blockDim.x * kQ) {
+      int32_t v[kQ][4];
+      bool inq[kQ];
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) {
-      const int64_t q = q0 + a * stride;
-      inq[a] = q < quads;
-      if (A.o2n) {
-        const int4 m = inq[a] ? __ldg(reinterpret_cast<const int4*>(A.o2n) + q) : make_int4(0, 0, 0, 0);
-        v[a][0] = m.x; v[a][1] = m.y; v[a][2] = m.z; v[a][3] = m.w;
-      } else {
+      for (int a = 0; a < kQ; ++a) {
+        const int64_t q = q0 + a * (int64_t)blockDim.x;
+        inq[a] = q < qhi;
+        if (A.o2n) {
+          const int4 m = inq[a] ? __ldg(reinterpret_cast<const int4*>(A.o2n) + q) : make_int4(0, 0, 0, 0);
+          v[a][0] = m.x; v[a][1] = m.y; v[a][2] = m.z; v[a][3] = m.w;
+        } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) v[a][t] = (int32_t)(q * 4 + t);
+          for (int t = 0; t < 4; ++t) v[a][t] = (int32_t)(q * 4 + t);
+        }
       }
-    }
-    // a vertex renumbered past the last one with an edge is isolated: only
-    // the root among them can be reached
-    bool need[kQ][4];
-    uint32_t vw[kQ][4];
-    int2 x[kQ][4];
+      // a vertex renumbered past the last one with an edge is isolated: only
+      // the root among them can be reached
+      bool need[kQ][4];
+      uint32_t vw[kQ][4];
+      int2 x[kQ][4];
 #pragma unroll
-    for (int a = 0; a < kQ; ++a)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int32_t vt = v[a][t];
-        need[a][t] = inq[a] && (!A.o2n || vt < A.n_nonisolated || vt == root);
-        // the visited word and the (level, parent) pair are loaded together;
-        // the pair is used only if the vertex was visited
-        vw[a][t] = need[a][t] ? __ldg(A.visited + (vt >> 5)) : 0u;
-        x[a][t] = need[a][t] ? A.lp[vt] : make_int2(-1, -1);
-      }
-    int32_t lev[kQ][4], par[kQ][4];
-#pragma unroll
-    for (int a = 0; a < kQ; ++a)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const bool vis = (vw[a][t] >> (v[a][t] & 31)) & 1u;
-        lev[a][t] = vis ? x[a][t].x : -1;
-        par[a][t] = vis ? (n2o ? __ldg(n2o + x[a][t].y) : x[a][t].y) : -1;
-      }
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) {
-      if (!inq[a]) continue;
-      const int64_t q = q0 + a * stride;
-      if (vec) {
-        reinterpret_cast<int4*>(level_out)[q] = make_int4(lev[a][0], lev[a][1], lev[a][2], lev[a][3]);
-        if (parent_out)
-          reinterpret_cast<int4*>(parent_out)[q] = make_int4(par[a][0], par[a][1], par[a][2], par[a][3]);
-      } else {
+      for (int a = 0; a < kQ; ++a)
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          level_out[q * 4 + t] = lev[a][t];
-          if (parent_out) parent_out[q * 4 + t] = par[a][t];
+          const int32_t vt = v[a][t];
+          need[a][t] = inq[a] && (!A.o2n || vt < A.n_nonisolated || vt == root);
+          // the visited word and the (level, parent) pair are loaded together;
+          // the pair is used only if the vertex was visited
+          vw[a][t] = need[a][t] ? __ldg(A.visited + (vt >> 5)) : 0u;
+          x[a][t] = need[a][t] ? A.lp[vt] : make_int2(-1, -1);
+        }
+      int32_t lev[kQ][4], par[kQ][4];
+#pragma unroll
+      for (int a = 0; a < kQ; ++a)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const bool vis = (vw[a][t] >> (v[a][t] & 31)) & 1u;
+          lev[a][t] = vis ? x[a][t].x : -1;
+          par[a][t] = vis ? (n2o ? __ldg(n2o + x[a][t].y) : x[a][t].y) : -1;
+        }
+#pragma unroll
+      for (int a = 0; a < kQ; ++a) {
+        if (!inq[a]) continue;
+        const int64_t q = q0 + a * (int64_t)blockDim.x;
+        if (vec) {
+          reinterpret_cast<int4*>(level_out)[q] = make_int4(lev[a][0], lev[a][1], lev[a][2], lev[a][3]);
+          if (parent_out)
+            reinterpret_cast<int4*>(parent_out)[q] = make_int4(par[a][0], par[a][1], par[a][2], par[a][3]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            level_out[q * 4 + t] = lev[a][t];
+            if (parent_out) parent_out[q * 4 + t] = par[a][t];
+          }
         }
       }
     }

@@ -45,6 +45,7 @@ struct BfsCtl {
   unsigned int n_rec;   // top-down chunk records
   unsigned int n_def;   // bottom-up deferred (long) rows
   unsigned int conv_tail;  // bitmap->queue conversion tail
+  unsigned int out_next;   // output pass: next chunk of original IDs to take
   // run totals
   int64_t reached, teps2, examined, alg_bytes;
   int32_t n_td, n_bu;
