@@ -1055,7 +1055,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   const bool host_loop_mode = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
   const bool want_stats = stats || (o.flags & DOBFS_RUN_SYNC_STATS);
   const bool dev_level = is_device_ptr(level_out);
-  const bool dev_parent = parent_out == nullptr || is_device_ptr(parent_out);
+  const bool dev_parent = parent_out ? is_device_ptr(parent_out) : dev_level;
   if (dev_level != dev_parent)
     return set_error(DOBFS_ERR_INVALID, "level_out and parent_out must both be host or both be device memory");
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));

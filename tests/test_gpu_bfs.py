@@ -286,6 +286,10 @@ def test_host_outputs_and_host_loop(d, s16):
     r = int(roots[0])
     lv, pa, st = _run(d, g, r, host=True)
     _check_run(og, r, lv, pa, ref_l[0])
+    # host levels alone (no parent array)
+    lv1 = np.full(og.n, 7, dtype=np.int32)
+    g.run(r, lv1)
+    np.testing.assert_array_equal(lv1, ref_l[0])
     lv2, pa2, st2 = _run(d, g, r, flags=d.DOBFS_RUN_HOST_LOOP)
     _check_run(og, r, lv2, pa2, ref_l[0])
     tr = g.trace()

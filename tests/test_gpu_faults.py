@@ -1,0 +1,172 @@
+"""Failure handling, injected on the host: device allocations that fail.
+
+The library takes every device allocation through the allocator hook
+(dobfs_set_allocator). A counting allocator that delegates to PyTorch and
+refuses the k-th request stands in for an out-of-memory device: each entry
+point must return DOBFS_ERR_OOM, free what it had allocated (no block left
+outstanding), and leave the library usable. Nothing here faults the GPU.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import dobfs_inputs as inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def d():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1503_04359_b300 import build, dobfs
+    build.build()
+    dobfs.load()
+    dobfs.use_torch_allocator()
+    yield dobfs
+    dobfs.use_torch_allocator()
+
+
+class FailingAllocator:
+    """Delegates to PyTorch; refuses request number `fail_at` (0-based)."""
+
+    def __init__(self, d, fail_at=None):
+        self.d = d
+        self.fail_at = fail_at
+        self.calls = 0
+        self.live = {}
+        dev = torch.cuda.current_device()
+
+        @d.ALLOC_FN
+        def _alloc(nbytes, stream, ctx):
+            k = self.calls
+            self.calls += 1
+            if self.fail_at is not None and k == self.fail_at:
+                return None
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+            self.live[p] = int(nbytes)
+            return p
+
+        @d.FREE_FN
+        def _free(ptr, stream, ctx):
+            self.live.pop(ptr, None)
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._keep = (_alloc, _free)
+
+    def install(self):
+        self.d._check(self.d.load().dobfs_set_allocator(self._keep[0], self._keep[1], None))
+        return self
+
+
+def _levels(d, g, r):
+    lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    g.run(int(r), lv)
+    torch.cuda.synchronize()
+    return lv.cpu().numpy()
+
+
+def test_graph_build_fails_cleanly_at_every_allocation(d):
+    spec = inputs.rmat(12)
+    for flags in (0, d.DOBFS_GRAPH_REINDEX, d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_CHUNKED):
+        counter = FailingAllocator(d).install()
+        g = d.rmat_graph(spec, flags=flags)
+        total = counter.calls
+        g.close()
+        torch.cuda.synchronize()
+        assert total > 5 and not counter.live
+        for k in range(total):
+            fa = FailingAllocator(d, fail_at=k).install()
+            with pytest.raises(d.DobfsError) as e:
+                d.rmat_graph(spec, flags=flags)
+            assert e.value.status == d.DOBFS_ERR_OOM, (flags, k, e.value)
+            torch.cuda.synchronize()
+            assert not fa.live, "allocation %d refused: %d blocks left" % (k, len(fa.live))
+    # the library is usable afterwards
+    d.use_torch_allocator()
+    og = oracle.csr_from_rmat(spec)
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    root = int(inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 1, og.degrees() > 0)[0])
+    np.testing.assert_array_equal(_levels(d, g, root), oracle.bfs(og, root)[0])
+    g.close()
+
+
+def test_run_batch_and_serve_fail_cleanly(d):
+    spec = inputs.rmat(12)
+    og = oracle.csr_from_rmat(spec)
+    d.use_torch_allocator()
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 8, og.degrees() > 0)
+    ref, _ = oracle.bfs_many(og, roots, want_parent=False)
+    # host outputs need a staging buffer (the graph's first host-output run)
+    fa = FailingAllocator(d, fail_at=0).install()
+    host = np.empty(og.n, dtype=np.int32)
+    with pytest.raises(d.DobfsError) as e:
+        g.run(int(roots[0]), host)
+    assert e.value.status == d.DOBFS_ERR_OOM
+    assert not fa.live
+    # a graph's first batch allocates its lane group (kept for later batches):
+    # refuse each of those allocations in turn, on a fresh graph each time
+    rt = torch.from_numpy(np.ascontiguousarray(roots)).cuda()
+    out = torch.empty((8, og.n), dtype=torch.int32, device="cuda")
+    d.use_torch_allocator()
+    g2 = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    counter = FailingAllocator(d).install()
+    d.dobfs_run_batch(g2.handle, rt, out)
+    torch.cuda.synchronize()
+    total = counter.calls
+    assert total >= 3 and len(counter.live) == total
+    g2.close()
+    assert not counter.live
+    for k in range(total):
+        d.use_torch_allocator()
+        g2 = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+        fb = FailingAllocator(d, fail_at=k).install()
+        with pytest.raises(d.DobfsError) as e:
+            d.dobfs_run_batch(g2.handle, rt, out)
+        assert e.value.status == d.DOBFS_ERR_OOM
+        torch.cuda.synchronize()
+        assert not fb.live, "allocation %d refused: %d blocks left" % (k, len(fb.live))
+        # the graph is still usable once memory is back
+        d.dobfs_run_batch(g2.handle, rt, out)
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        g2.close()
+        assert not fb.live
+    # a server allocates the graph's lane groups when the graph is added: refuse
+    # each of those allocations in turn; the server then takes the graph and works
+    counter = FailingAllocator(d).install()
+    srv = d.dobfs_serve_create()
+    d.dobfs_serve_add_graph(srv, g.handle)
+    d.dobfs_serve_destroy(srv)
+    total = counter.calls
+    assert total >= 3 and not counter.live
+    for k in range(total):
+        fs = FailingAllocator(d, fail_at=k).install()
+        srv = d.dobfs_serve_create()
+        try:
+            with pytest.raises(d.DobfsError) as e:
+                d.dobfs_serve_add_graph(srv, g.handle)
+            assert e.value.status == d.DOBFS_ERR_OOM
+            torch.cuda.synchronize()
+            assert not fs.live, "allocation %d refused: %d blocks left" % (k, len(fs.live))
+            d.use_torch_allocator()
+            gid = d.dobfs_serve_add_graph(srv, g.handle)
+            out1 = torch.full((og.n,), 9, dtype=torch.int32, device="cuda")
+            t = d.dobfs_serve_submit(srv, gid, int(roots[1]), out1)
+            t0 = time.time()
+            while d.dobfs_serve_poll(srv, t) is None:
+                assert time.time() - t0 < 60, "query did not finish"
+                time.sleep(0.001)
+            np.testing.assert_array_equal(out1.cpu().numpy(), ref[1])
+        finally:
+            d.dobfs_serve_destroy(srv)
+    # after the failures: the graph still answers, single and batched
+    d.use_torch_allocator()
+    np.testing.assert_array_equal(_levels(d, g, roots[2]), ref[2])
+    out = torch.empty((8, og.n), dtype=torch.int32, device="cuda")
+    d.dobfs_run_batch(g.handle, torch.from_numpy(np.ascontiguousarray(roots)).cuda(), out)
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    g.close()
