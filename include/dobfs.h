@@ -47,7 +47,8 @@ typedef enum {
   DOBFS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   DOBFS_ERR_BAD_GRAPH = -4,   /* column out of range, or asymmetric input under VALIDATE */
   DOBFS_ERR_TIMEOUT = -5,     /* a bounded device or host wait ran out */
-  DOBFS_ERR_BUSY = -6         /* admission refused: no free slot or not enough free memory */
+  DOBFS_ERR_BUSY = -6,        /* admission refused: no free slot or not enough free memory */
+  DOBFS_ERR_IO = -7           /* graph file: cannot open, read or write, or not a valid graph file */
 } dobfs_status;
 
 typedef struct dobfs_graph dobfs_graph;
@@ -162,6 +163,35 @@ int dobfs_graph_export(const dobfs_graph* g, int64_t* offsets_out, int32_t* cols
 
 /* Degree of every vertex, indexed by original ID: deg_out[n] (int32, host or device). */
 int dobfs_graph_degrees(const dobfs_graph* g, int32_t* deg_out, void* stream);
+
+/*
+ * Graph files: a built graph saved to disk and loaded again without a
+ * rebuild. The file holds the stored CSR in the internal vertex order (row
+ * offsets at their stored width, columns) and, for a renumbered graph, the
+ * map to original IDs, after a 64-byte header with a payload checksum;
+ * sections are padded to 8 bytes. Data moves through two pinned staging
+ * buffers of 64 MB, so the host never holds the whole graph.
+ *
+ * dobfs_graph_save writes g to `path` (created or truncated) on `stream`
+ * (NULL = the graph's stream), after any run still in flight on g.
+ * Errors: DOBFS_ERR_INVALID (NULL argument), DOBFS_ERR_IO (the file cannot
+ * be written; no partial file is left), DOBFS_ERR_OOM (staging buffers),
+ * DOBFS_ERR_CUDA.
+ *
+ * dobfs_graph_load builds a graph from such a file. Before any BFS kernel
+ * sees it, the stored CSR is checked on the device for every invariant the
+ * build establishes: offsets non-decreasing from 0 to n_entries, columns in
+ * range, rows strictly increasing without self-loops, and for a renumbered
+ * graph degree classes non-increasing along the internal IDs and a map that
+ * is a permutation. flags: 0 or DOBFS_GRAPH_VALIDATE (also check symmetry).
+ * Errors: DOBFS_ERR_INVALID (NULL argument, other flags), DOBFS_ERR_IO
+ * (cannot open, truncated, wrong magic or version, bad header, trailing
+ * data, checksum mismatch), DOBFS_ERR_BAD_GRAPH (an invariant fails),
+ * DOBFS_ERR_OOM, DOBFS_ERR_CUDA. On success *out is a graph equal to the
+ * one saved (same CSR, map and results); release it with dobfs_graph_destroy.
+ */
+int dobfs_graph_save(const dobfs_graph* g, const char* path, void* stream);
+int dobfs_graph_load(const char* path, uint32_t flags, void* stream, dobfs_graph** out);
 
 /* ------------------------------------------------------------------ single-source runs */
 

@@ -830,7 +830,142 @@ int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t m, uint32_t flags, cud
   return DOBFS_OK;
 }
 
-namespace {
+// ---------------------------------------------------------------- adopting a stored CSR
+// A CSR that did not come out of this library's build (a graph file) is
+// checked for every invariant the build establishes before any kernel relies
+// on it: offsets non-decreasing from 0 to n_entries, columns in range, rows
+// strictly increasing (sorted, no duplicates) and free of self-loops, and,
+// for a renumbered graph, degree classes non-increasing along the internal
+// IDs (so the isolated vertices come last and the vertices of degree >= 2^k
+// form a prefix) with new2orig a permutation.
+
+constexpr int kErrOffsets = 1, kErrColumn = 2, kErrRowOrder = 4, kErrClassOrder = 8, kErrPerm = 16,
+              kErrAsym = 32;
+
+// One warp per row.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_check_stored(const OffT* __restrict__ off,
+                                                           const int32_t* __restrict__ cols, int64_t n, int64_t nnz,
+                                                           int check_class, int* __restrict__ err) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const unsigned lane = lane_id();
+  int bad = 0;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t s = (int64_t)off[v], e = (int64_t)off[v + 1];
+    if (s < 0 || s > e || e > nnz) {
+      bad |= kErrOffsets;
+      continue;
+    }
+    if (check_class && lane == 0 && v + 1 < n) {
+      const int64_t e2 = (int64_t)off[v + 2];
+      if (e2 >= e && degree_class((uint64_t)(e - s), false) < degree_class((uint64_t)(e2 - e), false))
+        bad |= kErrClassOrder;
+    }
+    for (int64_t p = s + lane; p < e; p += 32) {
+      const int32_t c = cols[p];
+      if (c < 0 || c >= n)
+        bad |= kErrColumn;
+      else if (c == v || (p > s && cols[p - 1] >= c))
+        bad |= kErrRowOrder;
+    }
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+// o2n = inverse of n2o; o2n must hold -1 everywhere on entry. A value out of
+// range or taken twice means n2o is not a permutation.
+__global__ void k_invert_checked(const int32_t* __restrict__ n2o, int64_t n, int32_t* __restrict__ o2n,
+                                 int* __restrict__ err) {
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = n2o[i];
+    if (x < 0 || x >= n)
+      bad |= kErrPerm;
+    else if (atomicExch(o2n + x, (int32_t)i) != -1)
+      bad |= kErrPerm;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+// Every stored u -> v has v -> u (binary search in v's sorted row); one warp
+// per row u. Runs only on a CSR that passed k_check_stored.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_check_symmetric(const OffT* __restrict__ off,
+                                                              const int32_t* __restrict__ cols, int64_t n,
+                                                              int* __restrict__ err) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int bad = 0;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t s = (int64_t)off[u], e = (int64_t)off[u + 1];
+    for (int64_t p = s + lane_id(); p < e; p += 32) {
+      const int32_t v = cols[p];
+      int64_t a = (int64_t)off[v], z = (int64_t)off[v + 1];
+      while (a < z) {
+        const int64_t mid = a + ((z - a) >> 1);
+        if (cols[mid] < (int32_t)u) a = mid + 1; else z = mid;
+      }
+      if (a == (int64_t)off[v + 1] || cols[a] != (int32_t)u) bad |= kErrAsym;
+    }
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+template <class OffT>
+int adopt_checks(dobfs_graph* g, bool symmetric, cudaStream_t s, DevBuf& err, int* h) {
+  const OffT* off = g->off.as<OffT>();
+  const int32_t* cols = g->cols.as<int32_t>();
+  const int grid = grid_for(g->n * 32);
+  k_check_stored<OffT><<<grid, kThreads, 0, s>>>(off, cols, g->n, g->nnz, g->reindexed ? 1 : 0, err.as<int>());
+  if (g->reindexed) {
+    DOBFS_CUDA_TRY(cudaMemsetAsync(g->orig2new.ptr, 0xFF, sizeof(int32_t) * (size_t)g->n, s));
+    k_invert_checked<<<grid_for(g->n), kThreads, 0, s>>>(g->new2orig.as<int32_t>(), g->n,
+                                                         g->orig2new.as<int32_t>(), err.as<int>());
+  }
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  DOBFS_TRY(read_err_flag(err, s, h));
+  if (*h == 0 && symmetric) {
+    k_check_symmetric<OffT><<<grid, kThreads, 0, s>>>(off, cols, g->n, err.as<int>());
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    DOBFS_TRY(read_err_flag(err, s, h));
+  }
+  return DOBFS_OK;
+}
+
+int adopt_csr(dobfs_graph* g, bool check_symmetric, cudaStream_t s) {
+  const int64_t n = g->n;
+  int64_t ends[2] = {0, 0};
+  if (g->off64) {
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&ends[0], g->off.as<int64_t>(), 8, cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&ends[1], g->off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    int32_t e2[2] = {0, 0};
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&e2[0], g->off.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaMemcpyAsync(&e2[1], g->off.as<int32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    ends[0] = e2[0];
+    ends[1] = e2[1];
+  }
+  if (ends[0] != 0 || ends[1] != g->nnz)
+    return set_error(DOBFS_ERR_BAD_GRAPH, "stored row offsets must start at 0 and end at n_entries");
+  DevBuf err;
+  DOBFS_TRY(err.alloc(sizeof(int), s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+  int h = 0;
+  if (g->off64)
+    DOBFS_TRY(adopt_checks<int64_t>(g, check_symmetric, s, err, &h));
+  else
+    DOBFS_TRY(adopt_checks<int32_t>(g, check_symmetric, s, err, &h));
+  if (h & kErrOffsets) return set_error(DOBFS_ERR_BAD_GRAPH, "stored row offsets are not non-decreasing");
+  if (h & kErrColumn) return set_error(DOBFS_ERR_BAD_GRAPH, "stored column out of range [0, %lld)", (long long)n);
+  if (h & kErrRowOrder)
+    return set_error(DOBFS_ERR_BAD_GRAPH, "a stored row is not strictly increasing or holds a self-loop");
+  if (h & kErrClassOrder)
+    return set_error(DOBFS_ERR_BAD_GRAPH, "renumbered graph: degree classes increase along the internal IDs");
+  if (h & kErrPerm) return set_error(DOBFS_ERR_BAD_GRAPH, "renumbered graph: new2orig is not a permutation");
+  if (h & kErrAsym) return set_error(DOBFS_ERR_BAD_GRAPH, "stored graph is not symmetric (VALIDATE)");
+  return g->off64 ? finish_stats<int64_t>(g, s) : finish_stats<int32_t>(g, s);
+}
 
 int new_graph(int64_t n, cudaStream_t s, dobfs_graph** out) {
   if (!out) return set_error(DOBFS_ERR_INVALID, "out is NULL");
@@ -847,7 +982,7 @@ int new_graph(int64_t n, cudaStream_t s, dobfs_graph** out) {
 }
 
 // Finishes a build: workspace, timing; on failure frees the graph.
-int finish(dobfs_graph* g, int rc, cudaEvent_t e0, cudaEvent_t e1, dobfs_graph** out) {
+int finish_graph(dobfs_graph* g, int rc, cudaEvent_t e0, cudaEvent_t e1, dobfs_graph** out) {
   if (rc == DOBFS_OK) rc = graph_alloc_workspace(g);
   if (rc == DOBFS_OK && e0 && e1) {
     cudaEventRecord(e1, g->stream);
@@ -879,6 +1014,8 @@ int read_err_flag(DevBuf& err, cudaStream_t s, int* h) {
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   return DOBFS_OK;
 }
+
+namespace {
 
 // Device copy of a caller array (host or device); `dev` stays empty when the
 // caller's pointer is already device memory.
@@ -938,7 +1075,7 @@ int dobfs_graph_create_from_pairs(const int32_t* src, const int32_t* dst, int64_
       return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
     }();
   }
-  return finish(g, rc, e0, e1, out);
+  return finish_graph(g, rc, e0, e1, out);
 }
 
 int dobfs_graph_create(const void* row_offsets, int offsets_are_int64, const int32_t* col_indices,
@@ -997,7 +1134,7 @@ int dobfs_graph_create(const void* row_offsets, int offsets_are_int64, const int
       return build_from_keys(g, keys, m, flags, s);
     }();
   }
-  return finish(g, rc, e0, e1, out);
+  return finish_graph(g, rc, e0, e1, out);
 }
 
 int dobfs_graph_create_rmat(int scale, int64_t n_pairs, uint32_t t_a, uint32_t t_ab, uint32_t t_abc, uint64_t seed,
@@ -1036,7 +1173,7 @@ int dobfs_graph_create_rmat(int scale, int64_t n_pairs, uint32_t t_a, uint32_t t
       return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
     }();
   }
-  return finish(g, rc, e0, e1, out);
+  return finish_graph(g, rc, e0, e1, out);
 }
 
 int dobfs_graph_create_chunglu(const uint64_t* cdf, int64_t n_vertices, int64_t n_pairs, uint64_t seed,
@@ -1066,7 +1203,7 @@ int dobfs_graph_create_chunglu(const uint64_t* cdf, int64_t n_vertices, int64_t 
       return build_from_keys(g, keys, m, flags | DOBFS_GRAPH_SYMMETRIZE, s);
     }();
   }
-  return finish(g, rc, e0, e1, out);
+  return finish_graph(g, rc, e0, e1, out);
 }
 
 int dobfs_graph_export(const dobfs_graph* gc, int64_t* offsets_out, int32_t* cols_out, int32_t* new2orig_out,

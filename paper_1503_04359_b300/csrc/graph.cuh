@@ -128,4 +128,18 @@ void graph_release(dobfs_graph* g);
 // consuming `keys` (n_keys entries, may be reordered/overwritten)
 int build_from_keys(dobfs_graph* g, DevBuf& keys, int64_t n_keys, uint32_t flags, cudaStream_t s);
 
+// A new empty graph of n vertices (DOBFS_ERR_INVALID unless 1 <= n < 2^31).
+int new_graph(int64_t n, cudaStream_t s, dobfs_graph** out);
+// Events timing a build on s (e0 recorded now).
+int start_timer(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1);
+// Ends a build with status rc: on success allocates the BFS workspace and
+// hands g to *out; on failure releases g and sets *out = NULL.
+int finish_graph(dobfs_graph* g, int rc, cudaEvent_t e0, cudaEvent_t e1, dobfs_graph** out);
+// Reads a device error flag written on s.
+int read_err_flag(DevBuf& err, cudaStream_t s, int* h);
+// Takes over a stored CSR placed in g->off / g->cols (and g->new2orig when
+// g->reindexed; g->orig2new allocated): checks the build's invariants
+// (DOBFS_ERR_BAD_GRAPH otherwise), fills orig2new and the degree statistics.
+int adopt_csr(dobfs_graph* g, bool check_symmetric, cudaStream_t s);
+
 }  // namespace dobfs

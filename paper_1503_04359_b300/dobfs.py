@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdobfs.so")
 DOBFS_OK, DOBFS_PENDING = 0, 1
 DOBFS_ERR_INVALID, DOBFS_ERR_OOM, DOBFS_ERR_CUDA = -1, -2, -3
 DOBFS_BATCH_ALPHA = 4
-DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY = -4, -5, -6
+DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY, DOBFS_ERR_IO = -4, -5, -6, -7
 
 DOBFS_GRAPH_SYMMETRIZE = 0x1
 DOBFS_GRAPH_REINDEX = 0x2
@@ -122,6 +122,8 @@ def load() -> ctypes.CDLL:
         "dobfs_graph_get_info": (c_int, [G, ctypes.POINTER(dobfs_graph_info)]),
         "dobfs_graph_export": (c_int, [G, vp, vp, vp, vp]),
         "dobfs_graph_degrees": (c_int, [G, vp, vp]),
+        "dobfs_graph_save": (c_int, [G, ctypes.c_char_p, vp]),
+        "dobfs_graph_load": (c_int, [ctypes.c_char_p, u32, vp, ctypes.POINTER(G)]),
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
         "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
         "dobfs_last_trace": (c_int, [G, ctypes.POINTER(dobfs_level_trace), i32, ctypes.POINTER(i32)]),
@@ -262,6 +264,16 @@ def dobfs_graph_export(g: int, offsets_out=None, cols_out=None, new2orig_out=Non
 
 def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
     _check(load().dobfs_graph_degrees(g, _ptr(deg_out), _stream(stream)))
+
+
+def dobfs_graph_save(g: int, path: str, stream=None) -> None:
+    _check(load().dobfs_graph_save(g, os.fsencode(path), _stream(stream)))
+
+
+def dobfs_graph_load(path: str, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dobfs_graph_load(os.fsencode(path), flags, _stream(stream), ctypes.byref(h)))
+    return h.value
 
 
 def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: int | None = None,
@@ -465,6 +477,10 @@ class Graph:
         dobfs_graph_degrees(self.handle, out)
         return out
 
+    def save(self, path: str) -> None:
+        """Writes the graph file `path` (dobfs_graph_save)."""
+        dobfs_graph_save(self.handle, path)
+
     def run(self, root: int, level_out, parent_out=None, opts=None, want_stats: bool = False):
         return dobfs_run(self.handle, root, level_out, parent_out, opts, want_stats)
 
@@ -480,6 +496,11 @@ def rmat_graph(spec, flags: int = DOBFS_GRAPH_REINDEX, stream=None) -> Graph:
 
 def chunglu_graph(spec, cdf: np.ndarray, flags: int = DOBFS_GRAPH_REINDEX, stream=None) -> Graph:
     return Graph(dobfs_graph_create_chunglu(cdf, spec.n_pairs, spec.seed, flags, stream))
+
+
+def load_graph(path: str, validate: bool = False, stream=None) -> Graph:
+    """Device graph read from a graph file written by Graph.save (dobfs_graph_load)."""
+    return Graph(dobfs_graph_load(path, DOBFS_GRAPH_VALIDATE if validate else 0, stream))
 
 
 def pairs_graph(n_vertices: int, src, dst, flags: int = 0, stream=None) -> Graph:

@@ -170,3 +170,31 @@ def test_run_batch_and_serve_fail_cleanly(d):
     d.dobfs_run_batch(g.handle, torch.from_numpy(np.ascontiguousarray(roots)).cuda(), out)
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
     g.close()
+
+
+def test_graph_load_fails_cleanly_at_every_allocation(d, tmp_path):
+    spec = inputs.rmat(12)
+    og = oracle.csr_from_rmat(spec)
+    d.use_torch_allocator()
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    path = str(tmp_path / "g.dobfs")
+    g.save(path)
+    g.close()
+    counter = FailingAllocator(d).install()
+    h = d.load_graph(path)
+    total = counter.calls
+    h.close()
+    torch.cuda.synchronize()
+    assert total > 5 and not counter.live
+    for k in range(total):
+        fa = FailingAllocator(d, fail_at=k).install()
+        with pytest.raises(d.DobfsError) as e:
+            d.load_graph(path)
+        assert e.value.status == d.DOBFS_ERR_OOM, (k, e.value)
+        torch.cuda.synchronize()
+        assert not fa.live, "allocation %d refused: %d blocks left" % (k, len(fa.live))
+    d.use_torch_allocator()
+    h = d.load_graph(path)
+    root = int(inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 1, og.degrees() > 0)[0])
+    np.testing.assert_array_equal(_levels(d, h, root), oracle.bfs(og, root)[0])
+    h.close()
