@@ -433,6 +433,19 @@ def run_reference(args) -> None:
     }))
 
 
+def write_root_log(path: str, workload: str, rank: int, roots, ms, teps, levels, alg_bytes, peak: float,
+                   options: str) -> None:
+    """One JSON line per timed root: device time, TEPS, levels, algorithmic
+    bytes, and the whole-BFS fraction of the HBM peak they imply."""
+    with open(path, "w") as f:
+        for r, t, e, lv, b in zip(roots, ms, teps, levels, alg_bytes):
+            gbs = b / (t * 1e-3) / 1e9
+            f.write(json.dumps({"workload": workload, "rank": rank, "root": int(r), "device_ms": t,
+                                "gteps": e / (t * 1e-3) / 1e9, "teps_edges": int(e), "levels": int(lv),
+                                "alg_bytes": int(b), "alg_gbs": gbs, "roofline_frac": gbs / peak,
+                                "options": options}) + "\n")
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,6 +461,8 @@ def main() -> None:
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
     ap.add_argument("--tune", action="store_true", help="tune the run options on 8 other roots first")
+    ap.add_argument("--jsonl", default=None,
+                    help="also write one JSON line per timed root to this file (rank r > 0: file.r)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -552,9 +567,14 @@ def main() -> None:
     if dist:
         job_value, job_ms = aggregate_ranks(dist, "cuda", total_ms, total_edges)
 
+    peak, peak_kind = _peaks()
+    workload = "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex")
+    if args.jsonl:
+        write_root_log(args.jsonl if rank == 0 else "%s.%d" % (args.jsonl, rank), workload, rank, roots, ms, teps,
+                       levels, alg_bytes, peak, "tuned" if tuning is not None else "defaults")
+
     # roofline of the dominant kernel: per-level events in host-driven mode on
     # a fixed root sample with the default options
-    peak, peak_kind = _peaks()
     hl = dobfs.make_opts(stream=stream, flags=dobfs.DOBFS_RUN_HOST_LOOP)
     per_kind = {0: [0.0, 0], 1: [0.0, 0], 2: [0.0, 0]}  # direction (top-down, bottom-up, mixed) -> [ms, bytes]
     n_launch = {0: 0, 1: 0, 2: 0}
@@ -607,7 +627,6 @@ def main() -> None:
 
     if rank != 0:
         return
-    workload = "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex")
     prof = profiled_traffic(workload) if dom == 1 else None
     result = {
         "metric": METRIC,

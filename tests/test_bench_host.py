@@ -85,3 +85,17 @@ def test_ncu_summary_groups_bottom_up_levels(tmp_path):
     assert [x["launches"] for x in lv] == [2, 2, 2]
     table = {k: (c, t) for k, c, t, _ in ncu_summary.launch_table(launches)}
     assert table["k_bu<long, 0>"] == (4, 40.0) and table["k_bu_long<long>"] == (4, 40.0)
+
+
+def test_per_root_jsonl(tmp_path):
+    p = tmp_path / "roots.jsonl"
+    bench.write_root_log(str(p), "rmat-s10-ef16-reindex", 0, [5, 9], [2.0, 4.0], [4_000_000, 2_000_000], [6, 7],
+                         [6_400_000_000, 3_200_000_000], 6400.0, "defaults")
+    rows = [json.loads(x) for x in p.read_text().splitlines()]
+    assert [r["root"] for r in rows] == [5, 9]
+    assert rows[0]["gteps"] == pytest.approx(4e6 / 2e-3 / 1e9)
+    assert rows[1]["levels"] == 7 and rows[1]["teps_edges"] == 2_000_000
+    # 6.4e9 bytes in 2 ms = 3200 GB/s = half of the 6400 GB/s peak
+    assert rows[0]["alg_gbs"] == pytest.approx(3200.0)
+    assert rows[0]["roofline_frac"] == pytest.approx(0.5)
+    assert all(r["workload"] == "rmat-s10-ef16-reindex" and r["options"] == "defaults" for r in rows)
