@@ -48,7 +48,8 @@ typedef enum {
   DOBFS_ERR_BAD_GRAPH = -4,   /* column out of range, or asymmetric input under VALIDATE */
   DOBFS_ERR_TIMEOUT = -5,     /* a bounded device or host wait ran out */
   DOBFS_ERR_BUSY = -6,        /* admission refused: no free slot or not enough free memory */
-  DOBFS_ERR_IO = -7           /* graph file: cannot open, read or write, or not a valid graph file */
+  DOBFS_ERR_IO = -7,          /* graph file: cannot open, read or write, or not a valid graph file */
+  DOBFS_ERR_BOUNDS = -8       /* bounds-check builds only: a device index check failed (see below) */
 } dobfs_status;
 
 typedef struct dobfs_graph dobfs_graph;
@@ -434,6 +435,26 @@ int dobfs_last_trace(const dobfs_graph* g, dobfs_level_trace* out, int32_t max_l
 #define DOBFS_STATIC_MAX_VERTICES (1 << 20)
 int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int32_t n_vertices, int32_t root,
                      int32_t* level_out, int32_t* parent_out, void* stream);
+
+/* ------------------------------------------------------------------ bounds-check builds */
+
+/*
+ * libdobfs_bc.so is this library compiled with -DDOBFS_BOUNDS_CHECK. Every
+ * index its kernels read from memory (a vertex ID from a column, queue,
+ * record or map; a row's offsets; a write position taken from a counter) is
+ * checked on the device before use. A failing check records where it
+ * failed and substitutes a safe value, so the access stays in bounds; the
+ * call then returns DOBFS_ERR_BOUNDS with the place named in
+ * dobfs_last_error() (a server fails its queries with that status). Every
+ * device buffer is over-allocated by 64 KB, room for 1024 vertex IDs past
+ * n in any per-vertex array. The normal build compiles the checks away.
+ *
+ * dobfs_debug_set_column (bounds-check builds only; DOBFS_ERR_INVALID
+ * otherwise) overwrites stored entry `pos` (internal order, [0, n_entries))
+ * with `value`, which must lie in [0, n + 1024): a corrupted graph for
+ * testing the checks. The graph's first-neighbour table is refreshed.
+ */
+int dobfs_debug_set_column(dobfs_graph* g, int64_t pos, int32_t value);
 
 #ifdef __cplusplus
 }

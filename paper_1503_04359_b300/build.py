@@ -1,6 +1,11 @@
 """Builds libdobfs.so (the C-ABI library) from csrc/*.cu for sm_103a.
 
-    python -m paper_1503_04359_b300.build [--force] [--verbose]
+    python -m paper_1503_04359_b300.build [--force] [--verbose] [--bounds-check]
+
+With --bounds-check the same sources are compiled with -DDOBFS_BOUNDS_CHECK
+into ``_lib/libdobfs_bc.so``: every index the kernels read from memory is
+checked on the device and a failure is reported as DOBFS_ERR_BOUNDS (the
+binding loads this variant when DOBFS_BOUNDS_CHECK=1 is set).
 
 Every .cu is compiled to an object with nvcc (in parallel) and linked into
 ``_lib/libdobfs.so`` with the shared CUDA runtime, so the library shares the
@@ -20,6 +25,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(REPO, "_build", "dobfs")
 LIB = os.path.join(OUT_DIR, "libdobfs.so")
+LIB_BC = os.path.join(OUT_DIR, "libdobfs_bc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -46,18 +52,22 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile (if stale) and return the path of libdobfs.so."""
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          bounds_check: bool = False) -> str:
+    """Compile (if stale) and return the path of libdobfs.so (libdobfs_bc.so
+    with bounds_check)."""
+    lib = LIB_BC if bounds_check else LIB
+    build_dir = BUILD_DIR + ("_bc" if bounds_check else "")
     newest = max(os.path.getmtime(f) for f in _deps() + [__file__])
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra_flags:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest and not extra_flags:
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DDOBFS_BOUNDS_CHECK"] if bounds_check else []) + (extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -70,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     if verbose:
@@ -78,11 +88,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
     print(build(force="--force" in sys.argv or extra is not None, verbose="--verbose" in sys.argv or extra is not None,
-                extra_flags=extra))
+                extra_flags=extra, bounds_check="--bounds-check" in sys.argv))

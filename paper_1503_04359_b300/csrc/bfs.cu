@@ -94,12 +94,13 @@ __device__ __forceinline__ int64_t lower_bound_col(const int32_t* __restrict__ c
 
 // Appends v to q at an index taken from *tail, one atomic per group of
 // converged threads.
-__device__ __forceinline__ void enqueue(unsigned int* tail, int32_t* q, int32_t v) {
+__device__ __forceinline__ void enqueue(unsigned int* tail, int32_t* q, int32_t v, int64_t cap, int32_t* bc,
+                                        int site) {
   cg::coalesced_group g = cg::coalesced_threads();
   unsigned int base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
   base = g.shfl(base, 0);
-  q[base + g.thread_rank()] = v;
+  if (bc_pos((int64_t)base + g.thread_rank(), cap, bc, site)) q[base + g.thread_rank()] = v;
 }
 
 // Four top-down claims at once: the visited words are read first, then the
@@ -187,6 +188,7 @@ __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t
   c->alg_bytes = 0;
   c->n_td = c->n_bu = 0;
   c->overflow = 0;
+  c->bc_site = 0;
   c->mode = mode;
   c->alpha = alpha;
   c->beta = beta;
@@ -326,9 +328,10 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
   const int32_t x = BM ? (int32_t)(c->split_w << 5) : 0;
   unsigned long long m_new = 0, ex = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = cur[i];
+    const int32_t u = bc_vid(cur[i], A.n, &A.ctl->bc_site, kBcTdFrontier);
     int64_t s = (int64_t)A.off[u];
-    const int64_t e = (int64_t)A.off[u + 1];
+    int64_t e = (int64_t)A.off[u + 1];
+    bc_row(s, e, A.nnz, &A.ctl->bc_site, kBcTdRow);
     if (BM && x > 0 && e - s > small) s = lower_bound_col(A.cols, s, e, x);
     ex += (unsigned long long)(e - s);
     if (e - s <= small) {
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
         unsigned valid = 0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          v[t] = (j + t < e) ? A.cols[j + t] : 0;
+          v[t] = (j + t < e) ? bc_vid(A.cols[j + t], A.n, &A.ctl->bc_site, kBcTdColumn) : 0;
           if (j + t < e && v[t] >= x) valid |= 1u << t;
         }
         if (BM) {
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
           while (won) {
             const int t = __ffs(won) - 1;
             won &= won - 1;
-            enqueue(&A.ctl->q_tail, nxt, v[t]);
+            enqueue(&A.ctl->q_tail, nxt, v[t], A.n, &A.ctl->bc_site, kBcTdQueue);
           }
         }
       }
@@ -401,11 +404,13 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
       const unsigned long long rc = reinterpret_cast<const unsigned long long*>(A.rec)[r];
       lo = (int64_t)(rc >> 16);
       hi = lo + (int64_t)((rc >> 2) & 0x3FFFu);
+      bc_row(lo, hi, A.nnz, &A.ctl->bc_site, kBcTdRecord);
       lo_ok = lo + (int64_t)(rc & 3u);
     } else {
       const int2 rc = A.rec[r];
-      u = rc.x;
-      const int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+      u = bc_vid(rc.x, A.n, &A.ctl->bc_site, kBcTdRecord);
+      int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
+      bc_row(s, e, A.nnz, &A.ctl->bc_site, kBcTdRow);
       lo = (s & ~3ll) + (int64_t)rc.y * chunk;
       hi = min(e, lo + chunk);
       lo_ok = max(s, lo);
@@ -416,10 +421,10 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
       unsigned valid = 0;
       if (p < hi) {
         const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
-        v[0] = x.x;
-        v[1] = x.y;
-        v[2] = x.z;
-        v[3] = x.w;
+        v[0] = bc_vid(x.x, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[1] = bc_vid(x.y, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[2] = bc_vid(x.z, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[3] = bc_vid(x.w, A.n, &A.ctl->bc_site, kBcTdColumn);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
@@ -444,7 +449,10 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
         unsigned pos = qb + incl - cnt;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if ((won >> t) & 1u) nxt[pos++] = v[t];
+          if ((won >> t) & 1u) {
+            if (bc_pos(pos, A.n, &A.ctl->bc_site, kBcTdQueue)) nxt[pos] = v[t];
+            ++pos;
+          }
       }
     }
   }
@@ -478,7 +486,8 @@ __global__ void __launch_bounds__(kThreads) k_bitmap_to_queue(BfsArgs<OffT> A) {
     while (x) {
       const int b = __ffs(x) - 1;
       x &= x - 1;
-      q[pos++] = (int32_t)(w * 32 + b);
+      if (bc_pos(pos, A.n, &A.ctl->bc_site, kBcConvert)) q[pos] = (int32_t)(w * 32 + b);
+      ++pos;
     }
   }
 }
@@ -492,7 +501,7 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
   uint32_t* bm = (L & 1) ? A.fbm1 : A.fbm0;
   const int32_t* q = (L & 1) ? A.q1 : A.q0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = q[i];
+    const int32_t v = bc_vid(q[i], A.n, &A.ctl->bc_site, kBcConvert);
     atomicOr(bm + (v >> 5), 1u << (v & 31));
   }
 }
@@ -576,7 +585,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
       }
       int2 fd[2];
 #pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) fd[c2] = act[c2] ? __ldg(A.firstdeg + vv[c2]) : make_int2(0, 0);
+      for (int c2 = 0; c2 < 2; ++c2) {
+        fd[c2] = act[c2] ? __ldg(A.firstdeg + vv[c2]) : make_int2(0, 0);
+        if (act[c2]) fd[c2].x = bc_vid(fd[c2].x, A.n, &A.ctl->bc_site, kBcBuFirst);
+      }
       bool hit0[2];
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2) hit0[c2] = act[c2] && test_bit(front, fd[c2].x);
@@ -587,12 +599,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
         int32_t parent = hit0[c2] ? fd[c2].x : -1;
         unsigned long long exv = 1;
         if (!hit0[c2] && fd[c2].y > 1) {
-          const int64_t s0 = (int64_t)A.off[v];
-          const int64_t lim = s0 + min(fd[c2].y, scan);
+          int64_t s0 = (int64_t)A.off[v], e0 = s0 + fd[c2].y;
+          bc_row(s0, e0, A.nnz, &A.ctl->bc_site, kBcBuRow);
+          const int64_t lim = s0 + min(e0 - s0, (int64_t)scan);
           for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
             int32_t u[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) u[t] = (p + t < lim) ? A.cols[p + t] : -1;
+            for (int t = 0; t < 4; ++t)
+              u[t] = (p + t < lim) ? bc_vid(A.cols[p + t], A.n, &A.ctl->bc_site, kBcBuColumn) : -1;
             bool h[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
               if (h[t]) parent = u[t];
             exv += (unsigned long long)min((int64_t)4, lim - p);
           }
-          if (parent < 0 && fd[c2].y > scan) enqueue(&A.ctl->n_def, A.def, v);
+          if (parent < 0 && fd[c2].y > scan) enqueue(&A.ctl->n_def, A.def, v, A.n, &A.ctl->bc_site, kBcBuDeferred);
         }
         ex += exv;
         if (parent >= 0) {
@@ -657,8 +671,9 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
   unsigned long long n_new = 0, m_new = 0, ex = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
-    const int32_t v = A.def[i];
-    const int64_t s0 = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    const int32_t v = bc_vid(A.def[i], A.n, &A.ctl->bc_site, kBcBuDeferred);
+    int64_t s0 = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    bc_row(s0, e, A.nnz, &A.ctl->bc_site, kBcBuRow);
     const int64_t s = s0 + c->bu_scan;
     int32_t parent = -1;
     for (int64_t base = s & ~3ll; base < e; base += 128) {
@@ -666,7 +681,10 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
       int32_t hit = -1;
       if (p < e) {
         const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
-        const int32_t us[4] = {x.x, x.y, x.z, x.w};
+        const int32_t us[4] = {bc_vid(x.x, A.n, &A.ctl->bc_site, kBcBuColumn),
+                               bc_vid(x.y, A.n, &A.ctl->bc_site, kBcBuColumn),
+                               bc_vid(x.z, A.n, &A.ctl->bc_site, kBcBuColumn),
+                               bc_vid(x.w, A.n, &A.ctl->bc_site, kBcBuColumn)};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int64_t idx = p + t;
@@ -733,7 +751,10 @@ __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int3
         inq[a] = q < qhi;
         if (A.o2n) {
           const int4 m = inq[a] ? __ldg(reinterpret_cast<const int4*>(A.o2n) + q) : make_int4(0, 0, 0, 0);
-          v[a][0] = m.x; v[a][1] = m.y; v[a][2] = m.z; v[a][3] = m.w;
+          v[a][0] = bc_vid(m.x, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][1] = bc_vid(m.y, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][2] = bc_vid(m.z, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][3] = bc_vid(m.w, A.n, &A.ctl->bc_site, kBcOutput);
         } else {
 #pragma unroll
           for (int t = 0; t < 4; ++t) v[a][t] = (int32_t)(q * 4 + t);
@@ -762,7 +783,8 @@ __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int3
         for (int t = 0; t < 4; ++t) {
           const bool vis = (vw[a][t] >> (v[a][t] & 31)) & 1u;
           lev[a][t] = vis ? x[a][t].x : -1;
-          par[a][t] = vis ? (n2o ? __ldg(n2o + x[a][t].y) : x[a][t].y) : -1;
+          const int32_t py = vis ? bc_vid(x[a][t].y, A.n, &A.ctl->bc_site, kBcOutput) : 0;
+          par[a][t] = vis ? (n2o ? __ldg(n2o + py) : py) : -1;
         }
 #pragma unroll
       for (int a = 0; a < kQ; ++a) {
@@ -783,12 +805,13 @@ __global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int3
     }
   }
   for (int64_t o = quads * 4 + tid; o < A.n; o += stride) {  // ragged tail
-    const int32_t vt = A.o2n ? __ldg(A.o2n + o) : (int32_t)o;
+    const int32_t vt = A.o2n ? bc_vid(__ldg(A.o2n + o), A.n, &A.ctl->bc_site, kBcOutput) : (int32_t)o;
     int32_t lev = -1, par = -1;
     if ((__ldg(A.visited + (vt >> 5)) >> (vt & 31)) & 1u) {
       const int2 y = A.lp[vt];
       lev = y.x;
-      par = n2o ? __ldg(n2o + y.y) : y.y;
+      const int32_t py = bc_vid(y.y, A.n, &A.ctl->bc_site, kBcOutput);
+      par = n2o ? __ldg(n2o + py) : py;
     }
     level_out[o] = lev;
     if (parent_out) parent_out[o] = par;
@@ -806,10 +829,11 @@ __global__ void __launch_bounds__(kThreads) k_canonical_parent(BfsArgs<OffT> A, 
     if (!((__ldg(A.visited + (v >> 5)) >> (v & 31)) & 1u)) continue;
     const int32_t lev = A.lp[v].x;
     if (lev <= 0) continue;
-    const int64_t s = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    int64_t s = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+    bc_row(s, e, A.nnz, &A.ctl->bc_site, kBcOutput);
     int32_t best = INT32_MAX;
     for (int64_t j = s + lane; j < e; j += 32) {
-      const int32_t u = A.cols[j];
+      const int32_t u = bc_vid(A.cols[j], A.n, &A.ctl->bc_site, kBcOutput);
       if (((__ldg(A.visited + (u >> 5)) >> (u & 31)) & 1u) && A.lp[u].x == lev - 1) {
         const int32_t o = n2o ? n2o[u] : u;
         best = min(best, o);
@@ -1053,7 +1077,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   cudaStream_t s = (cudaStream_t)o.stream;
   if (!s) s = g->stream;
   const bool host_loop_mode = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
-  const bool want_stats = stats || (o.flags & DOBFS_RUN_SYNC_STATS);
+  const bool want_stats = stats || (o.flags & DOBFS_RUN_SYNC_STATS) || kBoundsCheck;
   const bool dev_level = is_device_ptr(level_out);
   const bool dev_parent = parent_out ? is_device_ptr(parent_out) : dev_level;
   if (dev_level != dev_parent)
@@ -1101,6 +1125,8 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_t1));
     BfsCtl c;
     DOBFS_CUDA_TRY(cudaMemcpy(&c, g->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.bc_site)
+      return set_error(DOBFS_ERR_BOUNDS, "device bounds check failed: %s", bounds_site_name(c.bc_site));
     if (c.overflow) return set_error(DOBFS_ERR_CUDA, "internal: top-down record buffer overflow");
     if (stats) {
       float ms = 0.f;
@@ -1266,6 +1292,30 @@ int dobfs_graph_destroy(dobfs_graph* g) {
     graph_release(g);
   }
   delete g;
+  return DOBFS_OK;
+}
+
+int dobfs_debug_set_column(dobfs_graph* g, int64_t pos, int32_t value) {
+  clear_error();
+  if (!kBoundsCheck) return set_error(DOBFS_ERR_INVALID, "dobfs_debug_set_column: bounds-check builds only");
+  if (!g) return set_error(DOBFS_ERR_INVALID, "graph is NULL");
+  if (pos < 0 || pos >= g->nnz)
+    return set_error(DOBFS_ERR_INVALID, "entry %lld out of range [0, %lld)", (long long)pos, (long long)g->nnz);
+  if (value < 0 || (int64_t)value >= g->n + kBoundsSlackVertices)
+    return set_error(DOBFS_ERR_INVALID, "value %d outside [0, n + %lld)", value, (long long)kBoundsSlackVertices);
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t s = g->stream;
+  if (g->last_stream) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(g->cols.as<int32_t>() + pos, &value, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  const int grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
+  if (g->off64)
+    k_firstdeg<int64_t><<<grid, kThreads, 0, s>>>(g->off.as<int64_t>(), g->cols.as<int32_t>(), g->n,
+                                                 g->firstdeg.as<int2>());
+  else
+    k_firstdeg<int32_t><<<grid, kThreads, 0, s>>>(g->off.as<int32_t>(), g->cols.as<int32_t>(), g->n,
+                                                 g->firstdeg.as<int2>());
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   return DOBFS_OK;
 }
 

@@ -26,6 +26,7 @@ void clear_error() { t_last_error[0] = '\0'; }
 
 void* dev_alloc(size_t bytes, cudaStream_t stream) {
   if (bytes == 0) bytes = 16;
+  if (kBoundsCheck) bytes += kBoundsSlackBytes;
   dobfs_alloc_fn fa;
   void* ctx;
   {
@@ -92,6 +93,15 @@ int sm_count() {
     n = c > 0 ? c : 148;
   }
   return n;
+}
+
+const char* bounds_site_name(int site) {
+  static const char* const names[kBcSiteCount] = {
+      "none", "top-down frontier entry", "top-down row offsets", "top-down neighbour ID",
+      "top-down next-queue position", "top-down chunk record", "queue/bitmap conversion",
+      "bottom-up first neighbour", "bottom-up row offsets", "bottom-up neighbour ID", "bottom-up deferred row",
+      "output parent or map entry", "batched row offsets", "batched neighbour ID", "batched chunk record"};
+  return site > 0 && site < kBcSiteCount ? names[site] : "unknown site";
 }
 
 }  // namespace dobfs

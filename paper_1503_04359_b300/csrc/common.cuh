@@ -102,4 +102,74 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
   return t;
 }
 
+// ------------------------------------------------------------------ bounds-check builds
+// Built with -DDOBFS_BOUNDS_CHECK, every index the kernels read from memory
+// (a vertex ID from a column, queue, record or map; a row's offsets; a write
+// position from a counter) is checked before use. A failing check records
+// its site in the run's control block (the first site wins) and substitutes
+// a safe value, so the access that follows stays in bounds; the host then
+// fails the call with DOBFS_ERR_BOUNDS. In normal builds the checks compile
+// away. Site numbers are listed in bounds_site_name().
+#ifdef DOBFS_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+// Bounds-check builds also over-allocate every device buffer by
+// kBoundsSlackBytes, enough for kBoundsSlackVertices vertices past n in any
+// per-vertex array, so that a corrupted vertex ID below n +
+// kBoundsSlackVertices stays inside the allocation even at an access the
+// checks would miss.
+constexpr size_t kBoundsSlackBytes = size_t(1) << 16;
+constexpr int64_t kBoundsSlackVertices = 1024;
+
+__device__ __forceinline__ void bc_fail(int32_t* site_flag, int site) { atomicCAS(site_flag, 0, site); }
+
+// v if it is a vertex ID in [0, n), else 0 (and the site is recorded).
+__device__ __forceinline__ int32_t bc_vid(int32_t v, int64_t n, int32_t* site_flag, int site) {
+  if (kBoundsCheck && (v < 0 || (int64_t)v >= n)) {
+    bc_fail(site_flag, site);
+    return 0;
+  }
+  return v;
+}
+
+// true if i is in [0, cap); otherwise records the site (the caller skips the access).
+__device__ __forceinline__ bool bc_pos(int64_t i, int64_t cap, int32_t* site_flag, int site) {
+  if (kBoundsCheck && (i < 0 || i >= cap)) {
+    bc_fail(site_flag, site);
+    return false;
+  }
+  return true;
+}
+
+// Clamps a row range to 0 <= s <= e <= nnz.
+__device__ __forceinline__ void bc_row(int64_t& s, int64_t& e, int64_t nnz, int32_t* site_flag, int site) {
+  if (kBoundsCheck && (s < 0 || s > e || e > nnz)) {
+    bc_fail(site_flag, site);
+    s = e = 0;
+  }
+}
+
+enum BoundsSite {
+  kBcTdFrontier = 1,  // top-down: frontier queue entry
+  kBcTdRow,           // top-down: row offsets of a frontier vertex
+  kBcTdColumn,        // top-down: neighbour ID
+  kBcTdQueue,         // top-down: next-queue position
+  kBcTdRecord,        // top-down: chunk record
+  kBcConvert,         // queue <-> bitmap conversion
+  kBcBuFirst,         // bottom-up: first neighbour
+  kBcBuRow,           // bottom-up: row offsets
+  kBcBuColumn,        // bottom-up: neighbour ID
+  kBcBuDeferred,      // bottom-up: deferred-row list
+  kBcOutput,          // output pass: parent or map entry
+  kBcMsRow,           // batched: row offsets
+  kBcMsColumn,        // batched: neighbour ID
+  kBcMsRecord,        // batched: chunk record or deferred row
+  kBcSiteCount
+};
+
+const char* bounds_site_name(int site);
+
 }  // namespace dobfs

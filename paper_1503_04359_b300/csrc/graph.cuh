@@ -50,7 +50,7 @@ struct BfsCtl {
   int64_t reached, teps2, examined, alg_bytes;
   int32_t n_td, n_bu;
   int32_t overflow;     // top-down record buffer overflow (never expected)
-  int32_t pad2;
+  int32_t bc_site;      // bounds-check builds: first failing check (0: none)
   // parameters
   int32_t mode, alpha, beta, static_pct, bu_steps, td_bm_div;
   int32_t td_small, td_chunk, bu_scan, td_split_pct;  // degree-bin cutoffs; mixed-level threshold

@@ -77,12 +77,12 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
   return ((unsigned long long)hi << 32) | lo;
 }
 
-__device__ __forceinline__ void enqueue_ms(unsigned int* tail, int32_t* q, int32_t v) {
+__device__ __forceinline__ void enqueue_ms(unsigned int* tail, int32_t* q, int32_t v, int64_t cap, int32_t* bc) {
   cg::coalesced_group g = cg::coalesced_threads();
   unsigned int base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
   base = g.shfl(base, 0);
-  q[base + g.thread_rank()] = v;
+  if (bc_pos((int64_t)base + g.thread_rank(), cap, bc, kBcMsRecord)) q[base + g.thread_rank()] = v;
 }
 
 // Records the lanes `nw` found at vertex v at iteration T in the planes.
@@ -237,13 +237,15 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
     const int2 rc = A.rec[r];
-    const int32_t u = rc.x;
+    const int32_t u = bc_vid(rc.x, A.n, &A.ctl->bc_site, kBcMsRecord);
     const unsigned long long fu = front[u];
-    const int64_t s = (int64_t)A.off[u] + (int64_t)rc.y * chunk;
-    const int64_t e = min((int64_t)A.off[u + 1], s + chunk);
-    if (lane == 0) ex += (unsigned long long)(e - s);
+    int64_t ro = (int64_t)A.off[u], re = (int64_t)A.off[u + 1];
+    bc_row(ro, re, A.nnz, &A.ctl->bc_site, kBcMsRow);
+    const int64_t s = ro + (int64_t)rc.y * chunk;
+    const int64_t e = min(re, s + chunk);
+    if (lane == 0 && e > s) ex += (unsigned long long)(e - s);
     for (int64_t j = s + lane; j < e; j += 32) {
-      const int32_t v = A.cols[j];
+      const int32_t v = bc_vid(A.cols[j], A.n, &A.ctl->bc_site, kBcMsColumn);
       const unsigned long long m = fu & ~__ldg(A.seen + v);
       if (m && (m & ~__ldcg(next + v))) atomicOr(reinterpret_cast<unsigned long long*>(next + v), m);
     }
@@ -320,14 +322,16 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
     unsigned long long acc = 0;
     int64_t j = 0;
     if (fd.y > 0) {
-      acc = __ldg(front + fd.x);
+      acc = __ldg(front + bc_vid(fd.x, A.n, &A.ctl->bc_site, kBcMsColumn));
       j = 1;
-      const int64_t o = (int64_t)A.off[v];
-      const int64_t lim = min((int64_t)fd.y, scan);
+      int64_t o = (int64_t)A.off[v], oe = o + fd.y;
+      bc_row(o, oe, A.nnz, &A.ctl->bc_site, kBcMsRow);
+      const int64_t lim = min(oe - o, scan);
       while (j < lim && (acc & need) != need) {
         int32_t u[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) u[t] = (j + t < lim) ? A.cols[o + j + t] : -1;
+        for (int t = 0; t < 4; ++t)
+          u[t] = (j + t < lim) ? bc_vid(A.cols[o + j + t], A.n, &A.ctl->bc_site, kBcMsColumn) : -1;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (u[t] >= 0) acc |= __ldg(front + u[t]);
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
       // partial: k_ms_bu_long scans the rest of the row in chunk records,
       // k_ms_bu_fin then records the vertex
       next[v] = nw;
-      enqueue_ms(&c->n_def, A.def, (int32_t)v);
+      enqueue_ms(&c->n_def, A.def, (int32_t)v, A.n, &c->bc_site);
       if ((int64_t)fd.y - scan > kMsLongChunk) {  // chunks after the first go to chunk records
         const unsigned nch = (unsigned)ceil_div((int64_t)fd.y - scan, (int64_t)kMsLongChunk);
         const unsigned base = atomicAdd(&c->n_rec, nch - 1);
@@ -396,14 +400,16 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
     int32_t v;
     int64_t s0, e0;
     if (i < nd) {  // a deferred row: the first chunk of the rest
-      v = A.def[i];
-      const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      v = bc_vid(A.def[i], A.n, &c->bc_site, kBcMsRecord);
+      int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      bc_row(o, e, A.nnz, &c->bc_site, kBcMsRow);
       s0 = o + scan;
       e0 = min(e, s0 + kMsLongChunk);
     } else {
       const int2 rc = A.rec[i - nd];
-      v = rc.x;
-      const int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      v = bc_vid(rc.x, A.n, &c->bc_site, kBcMsRecord);
+      int64_t o = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
+      bc_row(o, e, A.nnz, &c->bc_site, kBcMsRow);
       s0 = o + scan + (int64_t)rc.y * kMsLongChunk;
       e0 = min(e, s0 + kMsLongChunk);
     }
@@ -419,7 +425,8 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
       unsigned long long x = 0;
       if (p < e0) {
         const int4 c4 = *reinterpret_cast<const int4*>(A.cols + p);
-        const int32_t us[4] = {c4.x, c4.y, c4.z, c4.w};
+        const int32_t us[4] = {bc_vid(c4.x, A.n, &c->bc_site, kBcMsColumn), bc_vid(c4.y, A.n, &c->bc_site, kBcMsColumn),
+                               bc_vid(c4.z, A.n, &c->bc_site, kBcMsColumn), bc_vid(c4.w, A.n, &c->bc_site, kBcMsColumn)};
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (p + t >= s0 && p + t < e0) x |= __ldg(front + us[t]);
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_fin(MsArgs<OffT> A) {
   const int64_t nd = c->n_def;
   MsCount k;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = A.def[i];
+    const int32_t v = bc_vid(A.def[i], A.n, &c->bc_site, kBcMsRecord);
     const unsigned long long s = A.seen[v];
     const unsigned long long nw = next[v] & live & ~s;
     next[v] = nw;
@@ -1002,9 +1009,11 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     if (!dev_out)
       DOBFS_CUDA_TRY(cudaMemcpyAsync(level_out + (int64_t)b0 * g->n, g->ms_stage.ptr,
                                      sizeof(int32_t) * (size_t)cnt * (size_t)g->n, cudaMemcpyDeviceToHost, s));
-    if (stats) {
+    if (stats || kBoundsCheck) {
       MsCtl c;
       DOBFS_TRY(ms_group_read_ctl(m, &c));
+      if (c.bc_site)
+        return set_error(DOBFS_ERR_BOUNDS, "device bounds check failed: %s", bounds_site_name(c.bc_site));
       max_levels = std::max(max_levels, c.levels_run);
       examined += c.examined;
     }

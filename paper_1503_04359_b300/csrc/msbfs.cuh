@@ -31,7 +31,8 @@ struct MsCtl {
   unsigned long long nx_n, nx_m, nx_mu, nx_live, nx_examined;
   unsigned int n_rec, n_def;
   // parameters
-  int32_t mode, alpha, beta, td_chunk, bu_scan, pad;  // policy and degree-bin cutoffs
+  int32_t mode, alpha, beta, td_chunk, bu_scan;  // policy and degree-bin cutoffs
+  int32_t bc_site;       // bounds-check builds: first failing check (0: none)
   uint64_t sched_seed;
   int64_t examined;
 };

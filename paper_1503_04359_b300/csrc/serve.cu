@@ -248,6 +248,10 @@ bool schedule_once(dobfs_server* S) {
       G->in_flight = false;
       work = true;
       MsCtl c = *G->hctl;
+      if (c.bc_site) {
+        fail_all(S, DOBFS_ERR_BOUNDS, bounds_site_name(c.bc_site));
+        return false;
+      }
       // lanes whose frontier emptied; each flush is a pass over the whole
       // graph, so finished lanes are flushed together: when the group has no
       // live lane left, or once the oldest has waited flush_delay levels

@@ -21,11 +21,14 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libdobfs.so")
+# DOBFS_BOUNDS_CHECK=1 selects the bounds-check build (device index checks)
+if os.environ.get("DOBFS_BOUNDS_CHECK", "0") not in ("", "0"):
+    LIB_PATH = os.path.join(_HERE, "_lib", "libdobfs_bc.so")
 
 DOBFS_OK, DOBFS_PENDING = 0, 1
 DOBFS_ERR_INVALID, DOBFS_ERR_OOM, DOBFS_ERR_CUDA = -1, -2, -3
 DOBFS_BATCH_ALPHA = 4
-DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY, DOBFS_ERR_IO = -4, -5, -6, -7
+DOBFS_ERR_BAD_GRAPH, DOBFS_ERR_TIMEOUT, DOBFS_ERR_BUSY, DOBFS_ERR_IO, DOBFS_ERR_BOUNDS = -4, -5, -6, -7, -8
 
 DOBFS_GRAPH_SYMMETRIZE = 0x1
 DOBFS_GRAPH_REINDEX = 0x2
@@ -123,6 +126,7 @@ def load() -> ctypes.CDLL:
         "dobfs_graph_export": (c_int, [G, vp, vp, vp, vp]),
         "dobfs_graph_degrees": (c_int, [G, vp, vp]),
         "dobfs_graph_save": (c_int, [G, ctypes.c_char_p, vp]),
+        "dobfs_debug_set_column": (c_int, [G, i64, i32]),
         "dobfs_graph_load": (c_int, [ctypes.c_char_p, u32, vp, ctypes.POINTER(G)]),
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
         "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
@@ -264,6 +268,10 @@ def dobfs_graph_export(g: int, offsets_out=None, cols_out=None, new2orig_out=Non
 
 def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
     _check(load().dobfs_graph_degrees(g, _ptr(deg_out), _stream(stream)))
+
+
+def dobfs_debug_set_column(g: int, pos: int, value: int) -> None:
+    _check(load().dobfs_debug_set_column(g, pos, value))
 
 
 def dobfs_graph_save(g: int, path: str, stream=None) -> None:
