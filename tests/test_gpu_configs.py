@@ -13,6 +13,9 @@
   (degree >= 1 by construction, degree-biased), so no root comes from the
   CUDA path.
 """
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -93,6 +96,32 @@ def test_config3a_rmat28_streaming_check(d):
     assert rc.tolist() == [0, 0, 0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
     np.testing.assert_array_equal(parents[2:], canon[2:])
     assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(4))
+
+
+@pytest.mark.skipif(os.environ.get("DOBFS_FULL_VALIDATION", "0") in ("", "0"),
+                    reason="set DOBFS_FULL_VALIDATION=1 (64 roots at scale 28: about 45 GB of host memory, minutes)")
+def test_rmat28_all_64_roots_validated(d):
+    """Graph500-style validation of every one of 64 roots at scale 28: levels
+    and parents of each run pass the streaming invariant checker (level =
+    distance, every parent a neighbour one level up), in four batches of 16
+    roots per pass over the regenerated pairs."""
+    spec = inputs.rmat(28)
+    src, dst = inputs.rmat_pairs(spec, count=1 << 20)
+    roots = _pair_roots(src, dst, inputs.root_seed(spec.seed), 64)
+    del src, dst
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    for b in range(4):
+        batch = roots[16 * b:16 * (b + 1)]
+        lv, pa = _gpu_runs(d, g, batch)
+        t0 = time.time()
+        rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, batch, lv, pa)
+        reached = [int((lv[i] >= 0).sum()) for i in range(len(batch))]
+        print("batch %d: roots %s, reached min %d max %d, depth max %d, checked in %.0f s" %
+              (b, batch.tolist(), min(reached), max(reached), int(lv.max()), time.time() - t0), flush=True)
+        assert rc.tolist() == [0] * len(batch), [(oracle.RULES[int(r)], int(x)) for r, x in zip(rc, bad)]
+        assert min(reached) > 1000
+        del lv, pa
+    g.close()
 
 
 def test_rmat29_chunked_build_streaming_check(d):
