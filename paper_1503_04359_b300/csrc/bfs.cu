@@ -257,7 +257,11 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
   }
   const int prev_dir = c->fresh ? 0 : c->dir;
   c->fresh = 0;
-  if (c->n_f == 0) {
+  // a BFS has fewer than n levels: a frontier still non-empty past level n
+  // can only come from a fault in the step kernels, and ends the loop with
+  // an error instead of running on
+  if (c->n_f != 0 && (int64_t)c->level > A.n) c->overflow = 2;
+  if (c->n_f == 0 || c->overflow == 2) {
     c->done = 1;
     c->n_levels = c->level;
     if (in_graph) {
@@ -1127,6 +1131,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     DOBFS_CUDA_TRY(cudaMemcpy(&c, g->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost));
     if (c.bc_site)
       return set_error(DOBFS_ERR_BOUNDS, "device bounds check failed: %s", bounds_site_name(c.bc_site));
+    if (c.overflow == 2) return set_error(DOBFS_ERR_CUDA, "internal: the level loop ran past n levels");
     if (c.overflow) return set_error(DOBFS_ERR_CUDA, "internal: top-down record buffer overflow");
     if (stats) {
       float ms = 0.f;

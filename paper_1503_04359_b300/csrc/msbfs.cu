@@ -141,7 +141,11 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   c->fresh = 0;
   // done: no lane can discover anything; the server may still seed new lanes
   // and run the step, so the direction is picked in any case
-  const bool done = (c->live == 0 || c->n_f == 0);
+  // a graph-driven batch has fewer than n iterations: more can only come
+  // from a fault in the step kernels, and ends the loop instead of running on
+  const bool runaway = in_graph && (int64_t)c->levels_run > A.n;
+  if (runaway) c->runaway = 1;
+  const bool done = (c->live == 0 || c->n_f == 0 || runaway);
   if (done) c->live = 0;
   int dir;
   switch (c->mode) {
@@ -1014,6 +1018,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
       DOBFS_TRY(ms_group_read_ctl(m, &c));
       if (c.bc_site)
         return set_error(DOBFS_ERR_BOUNDS, "device bounds check failed: %s", bounds_site_name(c.bc_site));
+      if (c.runaway) return set_error(DOBFS_ERR_CUDA, "internal: the batch loop ran past n iterations");
       max_levels = std::max(max_levels, c.levels_run);
       examined += c.examined;
     }

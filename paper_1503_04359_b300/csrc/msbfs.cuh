@@ -33,6 +33,7 @@ struct MsCtl {
   // parameters
   int32_t mode, alpha, beta, td_chunk, bu_scan;  // policy and degree-bin cutoffs
   int32_t bc_site;       // bounds-check builds: first failing check (0: none)
+  int32_t runaway;       // graph-driven loop stopped after n iterations (a fault; never expected)
   uint64_t sched_seed;
   int64_t examined;
 };
