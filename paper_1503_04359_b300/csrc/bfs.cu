@@ -66,6 +66,8 @@ struct BfsArgs {
   const int32_t* o2n;  // NULL when not reindexed
   const int2* firstdeg;  // (first neighbour, degree) per vertex; first = -1 for isolated vertices
   const int64_t* deg_ge;  // [33]: vertices of degree >= 2^k
+  const int64_t* small_tab;  // [2 * kSmallDeg]: row offset and first ID of each small degree (renumbered graphs)
+  int32_t small_deg;         // degrees below this use small_tab for the row start (0: none)
   uint32_t* visited;
   uint32_t* fbm0;
   uint32_t* fbm1;
@@ -527,6 +529,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ uint32_t s_found[kThreads / 32][32];
   __shared__ uint16_t s_cand[kThreads / 32][1024];
+  __shared__ int64_t s_tab[2 * kSmallDeg];
+  if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
+  __syncthreads();
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
@@ -603,7 +608,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
         int32_t parent = hit0[c2] ? fd[c2].x : -1;
         unsigned long long exv = 1;
         if (!hit0[c2] && fd[c2].y > 1) {
-          int64_t s0 = (int64_t)A.off[v], e0 = s0 + fd[c2].y;
+          // small degrees: the row start follows from the ID (no offset load)
+          const int32_t dv = fd[c2].y;
+          int64_t s0 = dv < A.small_deg ? s_tab[dv] + (int64_t)(v - (int32_t)s_tab[kSmallDeg + dv]) * dv
+                                        : (int64_t)A.off[v];
+          int64_t e0 = s0 + dv;
           bc_row(s0, e0, A.nnz, &A.ctl->bc_site, kBcBuRow);
           const int64_t lim = s0 + min(e0 - s0, (int64_t)scan);
           for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
@@ -869,6 +878,8 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
   A.firstdeg = g->firstdeg.as<int2>();
   A.deg_ge = g->degge.as<int64_t>();
+  A.small_tab = g->degge.as<int64_t>() + 33;
+  A.small_deg = g->small_deg;
   A.visited = g->visited.as<uint32_t>();
   A.fbm0 = g->fbm0.as<uint32_t>();
   A.fbm1 = g->fbm1.as<uint32_t>();
@@ -1168,8 +1179,10 @@ int graph_alloc_workspace(dobfs_graph* g) {
   DOBFS_TRY(g->rec.alloc(sizeof(int2) * (size_t)g->rec_cap, s));
   DOBFS_TRY(g->deferred.alloc(sizeof(int32_t) * (size_t)g->n, s));
   DOBFS_TRY(g->firstdeg.alloc(sizeof(int2) * (size_t)g->n, s));
-  DOBFS_TRY(g->degge.alloc(sizeof(g->deg_ge), s));
+  DOBFS_TRY(g->degge.alloc(sizeof(g->deg_ge) + sizeof(g->small_tab), s));
   DOBFS_CUDA_TRY(cudaMemcpyAsync(g->degge.ptr, g->deg_ge, sizeof(g->deg_ge), cudaMemcpyHostToDevice, s));
+  DOBFS_CUDA_TRY(cudaMemcpyAsync(g->degge.as<int64_t>() + 33, g->small_tab, sizeof(g->small_tab),
+                                 cudaMemcpyHostToDevice, s));
   {
     const int grid = (int)std::min<int64_t>(ceil_div(g->n, kThreads), (int64_t)grid_cap(16));
     if (g->off64)

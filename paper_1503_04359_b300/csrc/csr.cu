@@ -215,10 +215,12 @@ template <class OffT>
 __global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t words, uint32_t* __restrict__ iso,
                             unsigned long long* __restrict__ stats) {
   // stats: [0] vertices with an edge, [1] max degree, [2 + k] vertices with
-  // floor(log2(degree)) == k
+  // floor(log2(degree)) == k, [34 + d] vertices of degree d (d < kSmallDeg)
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ unsigned int s_hist[32];
+  __shared__ unsigned int s_small[kSmallDeg];
   if (threadIdx.x < 32) s_hist[threadIdx.x] = 0u;
+  if (threadIdx.x < kSmallDeg) s_small[threadIdx.x] = 0u;
   __syncthreads();
   unsigned long long nonzero = 0, mx = 0;
   const int64_t total = words * 32;
@@ -232,12 +234,15 @@ __global__ void k_deg_stats(const OffT* __restrict__ off, int64_t n, int64_t wor
       nonzero += isolated ? 0 : 1;
       mx = max(mx, (unsigned long long)d);
       if (!isolated) atomicAdd(&s_hist[63 - __clzll((unsigned long long)d)], 1u);
+      if (d < kSmallDeg) atomicAdd(&s_small[d], 1u);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, isolated);
     if (lane_id() == 0) iso[v0 >> 5] = bal;
   }
   __syncthreads();
   if (threadIdx.x < 32 && s_hist[threadIdx.x]) atomicAdd(&stats[2 + threadIdx.x], (unsigned long long)s_hist[threadIdx.x]);
+  if (threadIdx.x < kSmallDeg && s_small[threadIdx.x])
+    atomicAdd(&stats[34 + threadIdx.x], (unsigned long long)s_small[threadIdx.x]);
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if (lane_id() == 0) atomicMax(&stats[1], mx);
   nonzero = block_sum_u64(nonzero, sh);
@@ -354,13 +359,14 @@ int finish_stats(dobfs_graph* g, cudaStream_t s) {
   g->words = ceil_div(g->n, 32);
   DOBFS_TRY(g->isolated.alloc(sizeof(uint32_t) * (size_t)g->words, s));
   DevBuf st;
-  DOBFS_TRY(st.alloc(sizeof(unsigned long long) * 34, s));
-  DOBFS_CUDA_TRY(cudaMemsetAsync(st.ptr, 0, sizeof(unsigned long long) * 34, s));
+  constexpr int kStats = 34 + kSmallDeg;
+  DOBFS_TRY(st.alloc(sizeof(unsigned long long) * kStats, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(st.ptr, 0, sizeof(unsigned long long) * kStats, s));
   k_deg_stats<OffT><<<grid_for(g->words * 32), kThreads, 0, s>>>(g->off.as<OffT>(), g->n, g->words,
                                                                   g->isolated.as<uint32_t>(),
                                                                   st.as<unsigned long long>());
   DOBFS_CUDA_TRY(cudaGetLastError());
-  unsigned long long h[34];
+  unsigned long long h[kStats];
   DOBFS_CUDA_TRY(cudaMemcpyAsync(h, st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   g->n_nonisolated = (int64_t)h[0];
@@ -371,6 +377,24 @@ int finish_stats(dobfs_graph* g, cudaStream_t s) {
   for (int k = 32; k >= 0; --k) {
     if (k < 32) acc += (int64_t)h[2 + k];
     g->deg_ge[k] = acc;
+  }
+  // Renumbered graphs: each degree d below kSmallDeg is a class of its own,
+  // so its vertices are consecutive and their rows (d entries each) too:
+  // row_start(v) = base[d] + (v - first[d]) * d, with first[d] the number
+  // of vertices of degree above d and base[d] its row offset.
+  memset(g->small_tab, 0, sizeof(g->small_tab));
+  g->small_deg = 0;
+  if (g->reindexed) {
+    int64_t above = g->n_nonisolated;  // vertices of degree > d, for d = 0
+    for (int d = 1; d < kSmallDeg; ++d) {
+      above -= (int64_t)h[34 + d];
+      g->small_tab[kSmallDeg + d] = above;
+      OffT base = 0;
+      DOBFS_CUDA_TRY(cudaMemcpyAsync(&base, g->off.as<OffT>() + above, sizeof(OffT), cudaMemcpyDeviceToHost, s));
+      DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+      g->small_tab[d] = (int64_t)base;
+    }
+    g->small_deg = kSmallDeg;
   }
   return DOBFS_OK;
 }

@@ -14,6 +14,10 @@ struct MsGroup;
 // Sentinel edge key: a dropped entry (self-loop or duplicate). Sorts last.
 constexpr uint64_t kSentinelKey = ~0ull;
 
+// Degrees below kSmallDeg are classes of their own in the renumbering, so a
+// row of such a vertex starts at an offset computed from its ID.
+constexpr int kSmallDeg = 8;
+
 // Degree-bin cutoffs of a run: 0 (the path's default) or within the ranges
 // the record buffers are sized for.
 inline bool cutoffs_valid(const dobfs_run_opts& o) {
@@ -84,6 +88,10 @@ struct dobfs_graph {
   dobfs::DevBuf new2orig, orig2new;  // int32[n] each, only when reindexed
   dobfs::DevBuf isolated;            // bitmap: degree-0 vertices and bits >= n
   int64_t deg_ge[33] = {};           // vertices of degree >= 2^k (a prefix of the IDs when reindexed)
+  // renumbered graphs: [d] row offset and [kSmallDeg + d] first ID of the
+  // vertices of degree d, for 1 <= d < small_deg (small_deg = 0: not used)
+  int64_t small_tab[2 * dobfs::kSmallDeg] = {};
+  int32_t small_deg = 0;
   int64_t words = 0;                 // bitmap words = ceil(n/32)
 
   // BFS workspace
@@ -94,7 +102,7 @@ struct dobfs_graph {
   int64_t rec_cap = 0;
   dobfs::DevBuf deferred;             // int32[n]
   dobfs::DevBuf firstdeg;             // int2[n]: (first neighbour, degree)
-  dobfs::DevBuf degge;                // int64[33]: device copy of deg_ge
+  dobfs::DevBuf degge;                // int64[33 + 2 * kSmallDeg]: device copy of deg_ge, small_tab
   dobfs::DevBuf ctl;                  // BfsCtl
   dobfs::DevBuf trace;                // LevelRec[kMaxTrace]
   dobfs::DevBuf out_stage;            // int32[2n] staging for host outputs (lazy)

@@ -54,6 +54,8 @@ struct MsArgs {
   int2* rec;
   int32_t* def;
   MsCtl* ctl;
+  const int64_t* small_tab;  // [2 * kSmallDeg]: row offset and first ID of each small degree (renumbered graphs)
+  int32_t small_deg;         // degrees below this use small_tab for the row start (0: none)
   int64_t n, nnz, n_cand, rec_cap;
 };
 
@@ -307,6 +309,9 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
 template <class OffT>
 __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
+  __shared__ int64_t s_tab[2 * kSmallDeg];
+  if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
+  __syncthreads();
   MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
@@ -328,7 +333,9 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
     if (fd.y > 0) {
       acc = __ldg(front + bc_vid(fd.x, A.n, &A.ctl->bc_site, kBcMsColumn));
       j = 1;
-      int64_t o = (int64_t)A.off[v], oe = o + fd.y;
+      // small degrees: the row start follows from the ID (no offset load)
+      int64_t o = fd.y < A.small_deg ? s_tab[fd.y] + (v - s_tab[kSmallDeg + fd.y]) * fd.y : (int64_t)A.off[v];
+      int64_t oe = o + fd.y;
       bc_row(o, oe, A.nnz, &A.ctl->bc_site, kBcMsRow);
       const int64_t lim = min(oe - o, scan);
       while (j < lim && (acc & need) != need) {
@@ -570,6 +577,8 @@ MsArgs<OffT> ms_args(MsGroup* m) {
   A.rec = m->rec.as<int2>();
   A.def = m->def.as<int32_t>();
   A.ctl = m->ctl.as<MsCtl>();
+  A.small_tab = g->degge.as<int64_t>() + 33;
+  A.small_deg = g->small_deg;
   A.n = g->n;
   A.nnz = g->nnz;
   A.n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
