@@ -516,14 +516,16 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // consecutive visited words (1024 vertices) at a time: one coalesced load of
 // the visited and isolated words gives the candidates (unvisited vertices
 // with an edge), which are compacted so that every lane holds one candidate
-// per round. A candidate first tests its first neighbour, read with its
-// degree from the packed (first, degree) array: rows are sorted with the
-// highest-degree neighbour first, so most vertices that have a frontier
-// neighbour resolve with that one 8-byte load. Otherwise the lane scans the
-// rest of its first bu_scan entries, four loads at a time, and stops at the
-// first neighbour in the frontier; longer rows without a hit go to the
-// deferred list. Found vertices are collected per word in shared memory and
-// every lane writes its own next-frontier and visited word: no global atomics.
+// per round. First pass: every candidate tests its first neighbour, read
+// with its degree from the packed (first, degree) array; rows are sorted
+// with the highest-degree neighbour first, so most vertices that have a
+// frontier neighbour resolve with that one 8-byte load. Second pass, over
+// the misses only (so a long scan does not hold up the first tests of the
+// other candidates): each scans the rest of its first bu_scan entries, four
+// loads at a time, and stops at the first neighbour in the frontier; longer
+// rows without a hit go to the deferred list. Found vertices are collected
+// per word in shared memory and every lane writes its own next-frontier and
+// visited word: no global atomics.
 template <class OffT, bool RECOVER>
 __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
@@ -578,19 +580,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
       }
     }
     __syncwarp();
+    // phase 1: every candidate tests its first neighbour (two per lane per
+    // round); the misses are compacted at the front of the candidate list
+    unsigned n_miss = 0;
     for (unsigned base = 0; base < total; base += 64) {
-      // two candidates per lane per round: their load chains overlap
-      unsigned jj[2], bb[2];
+      unsigned loc[2];
       int32_t vv[2];
       bool act[2];
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2) {
         const unsigned k = base + 32 * c2 + lane;
         act[c2] = k < total;
-        const unsigned loc = act[c2] ? (unsigned)s_cand[wid][k] : 0u;
-        jj[c2] = loc >> 5;
-        bb[c2] = loc & 31u;
-        vv[c2] = (int32_t)(grp * 1024 + loc);
+        loc[c2] = act[c2] ? (unsigned)s_cand[wid][k] : 0u;
+        vv[c2] = (int32_t)(grp * 1024 + loc[c2]);
       }
       int2 fd[2];
 #pragma unroll
@@ -603,40 +605,57 @@ __global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
       for (int c2 = 0; c2 < 2; ++c2) hit0[c2] = act[c2] && test_bit(front, fd[c2].x);
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2) {
-        if (!act[c2]) continue;
-        const int32_t v = vv[c2];
-        int32_t parent = hit0[c2] ? fd[c2].x : -1;
-        unsigned long long exv = 1;
-        if (!hit0[c2] && fd[c2].y > 1) {
-          // small degrees: the row start follows from the ID (no offset load)
-          const int32_t dv = fd[c2].y;
-          int64_t s0 = dv < A.small_deg ? s_tab[dv] + (int64_t)(v - (int32_t)s_tab[kSmallDeg + dv]) * dv
-                                        : (int64_t)A.off[v];
-          int64_t e0 = s0 + dv;
-          bc_row(s0, e0, A.nnz, &A.ctl->bc_site, kBcBuRow);
-          const int64_t lim = s0 + min(e0 - s0, (int64_t)scan);
-          for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
-            int32_t u[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-              u[t] = (p + t < lim) ? bc_vid(A.cols[p + t], A.n, &A.ctl->bc_site, kBcBuColumn) : -1;
-            bool h[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
-#pragma unroll
-            for (int t = 3; t >= 0; --t)
-              if (h[t]) parent = u[t];
-            exv += (unsigned long long)min((int64_t)4, lim - p);
-          }
-          if (parent < 0 && fd[c2].y > scan) enqueue(&A.ctl->n_def, A.def, v, A.n, &A.ctl->bc_site, kBcBuDeferred);
-        }
-        ex += exv;
-        if (parent >= 0) {
-          atomicOr(&s_found[wid][jj[c2]], 1u << bb[c2]);
-          A.lp[v] = make_int2(L + 1, parent);
+        if (act[c2]) ex += 1;
+        if (hit0[c2]) {
+          atomicOr(&s_found[wid][loc[c2] >> 5], 1u << (loc[c2] & 31u));
+          A.lp[vv[c2]] = make_int2(L + 1, fd[c2].x);
           n_new += 1;
           m_new += (unsigned long long)fd[c2].y;
         }
+        // the list slots written here were read in this or an earlier round
+        const bool miss = act[c2] && !hit0[c2] && fd[c2].y > 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, miss);
+        if (miss) s_cand[wid][n_miss + __popc(bal & lanemask_lt())] = (uint16_t)loc[c2];
+        n_miss += (unsigned)__popc(bal);
+      }
+    }
+    __syncwarp();
+    // phase 2: the misses scan the rest of their first bu_scan entries, four
+    // loads at a time, and stop at the first neighbour in the frontier;
+    // longer rows without a hit go to the deferred list
+    for (unsigned base = 0; base < n_miss; base += 32) {
+      const unsigned k = base + lane;
+      if (k >= n_miss) continue;
+      const unsigned lc = (unsigned)s_cand[wid][k];
+      const int32_t v = (int32_t)(grp * 1024 + lc);
+      const int32_t dv = __ldg(&A.firstdeg[v].y);
+      // small degrees: the row start follows from the ID (no offset load)
+      int64_t s0 = dv < A.small_deg ? s_tab[dv] + (int64_t)(v - (int32_t)s_tab[kSmallDeg + dv]) * dv
+                                    : (int64_t)A.off[v];
+      int64_t e0 = s0 + dv;
+      bc_row(s0, e0, A.nnz, &A.ctl->bc_site, kBcBuRow);
+      const int64_t lim = s0 + min(e0 - s0, (int64_t)scan);
+      int32_t parent = -1;
+      for (int64_t p = s0 + 1; p < lim && parent < 0; p += 4) {
+        int32_t u[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          u[t] = (p + t < lim) ? bc_vid(A.cols[p + t], A.n, &A.ctl->bc_site, kBcBuColumn) : -1;
+        bool h[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
+#pragma unroll
+        for (int t = 3; t >= 0; --t)
+          if (h[t]) parent = u[t];
+        ex += (unsigned long long)min((int64_t)4, lim - p);
+      }
+      if (parent >= 0) {
+        atomicOr(&s_found[wid][lc >> 5], 1u << (lc & 31u));
+        A.lp[v] = make_int2(L + 1, parent);
+        n_new += 1;
+        m_new += (unsigned long long)dv;
+      } else if (dv > scan) {
+        enqueue(&A.ctl->n_def, A.def, v, A.n, &A.ctl->bc_site, kBcBuDeferred);
       }
     }
     __syncwarp();
