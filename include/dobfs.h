@@ -333,7 +333,7 @@ typedef struct {
                                    waited this long (default 2000 us; 0: at once) */
   int32_t ss_max;               /* while at most this many queries of a graph wait, they run as single-
                                    source BFS (dobfs_run) on the graph's own stream instead (device
-                                   outputs only; default 2; 0: never) */
+                                   outputs only; default 1; 0: never) */
   int32_t ss_backlog;           /* ... as long as fewer than this many are already queued there (default 4) */
 } dobfs_serve_opts;
 
