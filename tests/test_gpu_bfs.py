@@ -385,3 +385,25 @@ def test_repeated_runs_and_streams(d, s16):
     torch.cuda.synchronize()
     for i, lv, s in outs:
         np.testing.assert_array_equal(lv.cpu().numpy(), ref_l[i])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_trace_counts_match_the_oracle(d, s16, mode):
+    """Per-level frontier sizes and degree sums (the switch's inputs) against
+    the oracle's levels and degrees, renumbered and not: the new frontier's
+    degree sum is read from the degree-class ranges for small degrees."""
+    spec, og, roots, ref_l, _ = s16
+    deg = og.degrees().astype(np.int64)
+    for flags in (0, d.DOBFS_GRAPH_REINDEX, d.DOBFS_GRAPH_REINDEX_EXACT):
+        g = d.rmat_graph(spec, flags=flags)
+        for i, r in enumerate(roots[:3]):
+            _run(d, g, int(r), mode=mode)
+            tr = g.trace()
+            lv = ref_l[i]
+            assert len(tr) == int(lv.max()) + 1
+            for t in tr:
+                at = lv == t.level
+                assert t.n_frontier == int(at.sum()), (flags, t.level)
+                assert t.m_frontier == int(deg[at].sum()), (flags, t.level)
+                assert t.n_next == int((lv == t.level + 1).sum())
+        g.close()
