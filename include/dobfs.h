@@ -267,9 +267,12 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
 
 /*
  * Batched BFS from n_roots roots (original IDs) with the bit-parallel
- * multi-source traversal: roots are taken 64 at a time as the lanes of one
- * traversal in which every vertex carries 64-bit masks (lanes that reached
- * it, lanes for which it is in the frontier); each level runs top-down or
+ * multi-source traversal: roots are the lanes of traversals in which every
+ * vertex carries lane masks (lanes that reached it, lanes for which it is in
+ * the frontier): up to 64 roots run as one 64-lane traversal, more in
+ * traversals of 128 lanes (two 64-bit mask words per vertex; a wide
+ * bottom-up level scans whole rows whatever the lane count, so 128 lanes
+ * cost about what 64 do); each level runs top-down or
  * bottom-up (Algorithm 1) for all lanes at once, the direction picked by the
  * alpha/beta rule on the union of the lanes' frontiers. level_out[n_roots][n]
  * (int32, row r for roots[r], original IDs) receives the levels, identical
@@ -290,8 +293,9 @@ int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32
 
 /*
  * A query server over resident graphs with continuous batching: queries
- * (graph, root) are admitted as they arrive into free lanes of 64-lane
- * bit-parallel traversals already running on that graph (lanes join and
+ * (graph, root) are admitted as they arrive into free lanes of 128-lane
+ * (or, with lane_words = 1, 64-lane) bit-parallel traversals already running
+ * on that graph (lanes join and
  * leave at level boundaries), each graph's lane groups run on their own
  * CUDA streams so work overlaps on the device, and a scheduler thread owned
  * by the server drives the levels. Each level is a step of Algorithm 1 for
@@ -335,6 +339,8 @@ typedef struct {
                                    source BFS (dobfs_run) on the graph's own stream instead (device
                                    outputs only; default 1; 0: never) */
   int32_t ss_backlog;           /* ... as long as fewer than this many are already queued there (default 4) */
+  int32_t lane_words;           /* lanes per group: 64 * lane_words, 1 or 2 (default 2: a wide bottom-up
+                                   step scans whole rows anyway, so 128 lanes cost about what 64 do) */
 } dobfs_serve_opts;
 
 typedef struct {

@@ -1,9 +1,15 @@
-// Bit-parallel multi-source BFS: up to 64 BFS (one per lane) over the same
-// graph in one traversal, each vertex carrying 64-bit lane masks.
+// Bit-parallel multi-source BFS: up to 128 BFS (one per lane) over the same
+// graph in one traversal, each vertex carrying lane masks of one or two
+// 64-bit words (64 or 128 lanes per group), a vertex's words side by side.
 //
 //   seen[v]       lanes that have reached v
 //   front/next    lanes for which v is in the current / next frontier
 //   planes[b][v]  bit b of the iteration at which each lane reached v
+//
+// Where a step scans whole rows anyway (the wide bottom-up iterations, in
+// which some live lane is nearly always still missing), its cost does not
+// depend on the number of lanes, so a 128-lane group does the work of two
+// 64-lane groups at about the cost of one.
 //
 // A step expands the frontier of iteration t for every lane at once, in the
 // direction of Algorithm 1 picked by the same alpha/beta rule on the union of
@@ -47,10 +53,10 @@ struct MsArgs {
   const int32_t* cols;
   const int2* firstdeg;
   const int32_t* o2n;
-  uint64_t* seen;
-  uint64_t* fb0;
-  uint64_t* fb1;
-  uint64_t* planes;
+  uint64_t* seen;   // [n][W]
+  uint64_t* fb0;    // [n][W]
+  uint64_t* fb1;    // [n][W]
+  uint64_t* planes; // [kMsPlanes][n][W]
   int2* rec;
   int32_t* def;
   MsCtl* ctl;
@@ -65,13 +71,126 @@ struct SeedArgs {
   int32_t root[kMsLanes];
 };
 
+// One mask word's flush: lanes of word `word` (bit i = lane 64 * word + i).
 struct FlushArgs {
   unsigned long long lanes;
+  int32_t word;
   int32_t release;
   int32_t vec;  // n % 4 == 0 and every flushed output row 16-byte aligned
-  int32_t* out[kMsLanes];
-  int32_t start[kMsLanes];
+  int32_t* out[kMsWordLanes];
+  int32_t start[kMsWordLanes];
 };
+
+// The lane masks of one vertex: W words (64 lanes each), stored contiguously
+// so that one access moves all of a vertex's lanes.
+template <int W>
+struct Lanes {
+  unsigned long long w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Lanes<W> ld_lanes(const uint64_t* p, int64_t v) {
+  Lanes<W> m;
+  if constexpr (W == 2) {
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(p + 2 * v);
+    m.w[0] = x.x;
+    m.w[1] = x.y;
+  } else {
+    m.w[0] = p[v];
+  }
+  return m;
+}
+
+// through the read-only path (arrays not written during the kernel)
+template <int W>
+__device__ __forceinline__ Lanes<W> ldg_lanes(const uint64_t* p, int64_t v) {
+  Lanes<W> m;
+  if constexpr (W == 2) {
+    const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(p + 2 * v));
+    m.w[0] = x.x;
+    m.w[1] = x.y;
+  } else {
+    m.w[0] = __ldg(p + v);
+  }
+  return m;
+}
+
+// L2 only (words other threads update with atomics during the kernel)
+template <int W>
+__device__ __forceinline__ Lanes<W> ldcg_lanes(const uint64_t* p, int64_t v) {
+  Lanes<W> m;
+  if constexpr (W == 2) {
+    const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(p + 2 * v));
+    m.w[0] = x.x;
+    m.w[1] = x.y;
+  } else {
+    m.w[0] = __ldcg(p + v);
+  }
+  return m;
+}
+
+template <int W>
+__device__ __forceinline__ void st_lanes(uint64_t* p, int64_t v, const Lanes<W>& m) {
+  if constexpr (W == 2) {
+    *reinterpret_cast<ulonglong2*>(p + 2 * v) = make_ulonglong2(m.w[0], m.w[1]);
+  } else {
+    p[v] = m.w[0];
+  }
+}
+
+template <int W>
+__device__ __forceinline__ Lanes<W> zero_lanes() {
+  Lanes<W> m;
+#pragma unroll
+  for (int i = 0; i < W; ++i) m.w[i] = 0ull;
+  return m;
+}
+
+template <int W>
+__device__ __forceinline__ bool any(const Lanes<W>& m) {
+  unsigned long long x = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) x |= m.w[i];
+  return x != 0ull;
+}
+
+template <int W>
+__device__ __forceinline__ Lanes<W> and_not(const Lanes<W>& a, const Lanes<W>& b) {  // a & ~b
+  Lanes<W> m;
+#pragma unroll
+  for (int i = 0; i < W; ++i) m.w[i] = a.w[i] & ~b.w[i];
+  return m;
+}
+
+template <int W>
+__device__ __forceinline__ Lanes<W> and_(const Lanes<W>& a, const Lanes<W>& b) {
+  Lanes<W> m;
+#pragma unroll
+  for (int i = 0; i < W; ++i) m.w[i] = a.w[i] & b.w[i];
+  return m;
+}
+
+template <int W>
+__device__ __forceinline__ void or_into(Lanes<W>& a, const Lanes<W>& b) {
+#pragma unroll
+  for (int i = 0; i < W; ++i) a.w[i] |= b.w[i];
+}
+
+template <int W>
+__device__ __forceinline__ bool covers(const Lanes<W>& acc, const Lanes<W>& need) {  // need is a subset of acc
+  unsigned long long x = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) x |= need.w[i] & ~acc.w[i];
+  return x == 0ull;
+}
+
+template <int W>
+__device__ __forceinline__ Lanes<W> ctl_lanes(const unsigned long long* words) {
+  Lanes<W> m;
+#pragma unroll
+  for (int i = 0; i < W; ++i) m.w[i] = words[i];
+  return m;
+}
 
 __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
   const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
@@ -87,42 +206,62 @@ __device__ __forceinline__ void enqueue_ms(unsigned int* tail, int32_t* q, int32
   if (bc_pos((int64_t)base + g.thread_rank(), cap, bc, kBcMsRecord)) q[base + g.thread_rank()] = v;
 }
 
-// Records the lanes `nw` found at vertex v at iteration T in the planes.
-template <class OffT>
-__device__ __forceinline__ void set_planes(const MsArgs<OffT>& A, int64_t v, unsigned long long nw, unsigned T,
+// Records the lanes `nw` found at vertex v at iteration T in the planes (one
+// thread owns v).
+template <int W, class OffT>
+__device__ __forceinline__ void set_planes(const MsArgs<OffT>& A, int64_t v, const Lanes<W>& nw, unsigned T,
                                            int n_planes) {
   for (int b = 0; b < n_planes; ++b)
-    if ((T >> b) & 1u) A.planes[(int64_t)b * A.n + v] |= nw;
+    if ((T >> b) & 1u) {
+      Lanes<W> p = ld_lanes<W>(A.planes + (int64_t)b * A.n * W, v);
+      or_into(p, nw);
+      st_lanes<W>(A.planes + (int64_t)b * A.n * W, v, p);
+    }
 }
 
-// One thread per seeded lane; repeated roots are counted once in the
-// frontier and unvisited-edge totals (the atomics tell the first one).
-template <class OffT>
+// Seeds lanes at their roots, one thread per seeded lane. A root is counted
+// in the frontier and unvisited-edge totals once, by the first seed naming
+// it, from the state before this seeding (read before any bit is set).
+template <class OffT, int W>
 __global__ void k_ms_seed(MsArgs<OffT> A, SeedArgs S) {
   const int i = threadIdx.x;
   MsCtl* c = A.ctl;
   const unsigned T = (unsigned)c->iter & kIterMask;
   const int np = c->n_planes;
   uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
-  if (i < S.count) {
-    const int32_t r = A.o2n ? A.o2n[S.root[i]] : S.root[i];
-    const unsigned long long bit = 1ull << S.lane[i];
-    const unsigned long long s_old = atomicOr(reinterpret_cast<unsigned long long*>(A.seen + r), bit);
-    const unsigned long long f_old = atomicOr(reinterpret_cast<unsigned long long*>(front + r), bit);
+  const bool mine = i < S.count;
+  int32_t r = 0;
+  bool s_old = false, f_old = false;
+  if (mine) {
+    r = A.o2n ? A.o2n[S.root[i]] : S.root[i];
+    s_old = any(ld_lanes<W>(A.seen, r));
+    f_old = any(ld_lanes<W>(front, r));
+  }
+  __syncthreads();
+  if (mine) {
+    const int l = S.lane[i], w = l / kMsWordLanes;
+    const unsigned long long bit = 1ull << (l % kMsWordLanes);
+    atomicOr(reinterpret_cast<unsigned long long*>(A.seen + (int64_t)r * W + w), bit);
+    atomicOr(reinterpret_cast<unsigned long long*>(front + (int64_t)r * W + w), bit);
     for (int b = 0; b < np; ++b)
-      if ((T >> b) & 1u) atomicOr(reinterpret_cast<unsigned long long*>(A.planes + (int64_t)b * A.n + r), bit);
-    const long long d = (long long)A.off[r + 1] - (long long)A.off[r];
-    if (!f_old) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&c->n_f), 1ull);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_f), (unsigned long long)d);
+      if ((T >> b) & 1u)
+        atomicOr(reinterpret_cast<unsigned long long*>(A.planes + (int64_t)b * A.n * W + (int64_t)r * W + w), bit);
+    atomicOr(&c->active[w], bit);
+    atomicOr(&c->live[w], bit);
+    bool first = true;
+    for (int j = 0; j < i && first; ++j) first = S.root[j] != S.root[i];
+    if (first) {
+      const long long d = (long long)A.off[r + 1] - (long long)A.off[r];
+      if (!f_old) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&c->n_f), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_f), (unsigned long long)d);
+      }
+      if (!s_old) atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_u), (unsigned long long)(-d));
     }
-    if (!s_old) atomicAdd(reinterpret_cast<unsigned long long*>(&c->m_u), (unsigned long long)(-d));
-    atomicOr(&c->active, bit);
-    atomicOr(&c->live, bit);
   }
 }
 
-template <class OffT>
+template <class OffT, int W>
 __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
                             int in_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -132,11 +271,14 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
     c->n_f = (int64_t)c->nx_n;
     c->m_f = (int64_t)c->nx_m;
     c->m_u -= (int64_t)c->nx_mu;
-    c->live = c->nx_live & c->active;
+    for (int w = 0; w < W; ++w) {
+      c->live[w] = c->nx_live[w] & c->active[w];
+      c->nx_live[w] = 0;
+    }
     c->examined += (int64_t)c->nx_examined;
     c->iter += 1;
     c->levels_run += 1;
-    c->nx_n = c->nx_m = c->nx_mu = c->nx_live = c->nx_examined = 0;
+    c->nx_n = c->nx_m = c->nx_mu = c->nx_examined = 0;
     c->n_rec = c->n_def = 0;
   }
   const int prev_dir = c->fresh ? 0 : c->dir;
@@ -147,8 +289,11 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   // from a fault in the step kernels, and ends the loop instead of running on
   const bool runaway = in_graph && (int64_t)c->levels_run > A.n;
   if (runaway) c->runaway = 1;
-  const bool done = (c->live == 0 || c->n_f == 0 || runaway);
-  if (done) c->live = 0;
+  unsigned long long any_live = 0;
+  for (int w = 0; w < W; ++w) any_live |= c->live[w];
+  const bool done = (any_live == 0 || c->n_f == 0 || runaway);
+  if (done)
+    for (int w = 0; w < W; ++w) c->live[w] = 0;
   int dir;
   switch (c->mode) {
     case DOBFS_DIR_TOPDOWN: dir = 0; break;
@@ -187,38 +332,41 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
 // all planes are clean; planes from kFirstPlanes up are cleared again when an
 // iteration first needs them. Discovery iterations then stay small: fewer
 // plane bits to set per discovery and fewer planes per flush.
-template <class OffT>
+template <class OffT, int W>
 __global__ void k_ms_rebase(MsArgs<OffT> A) {
   MsCtl* c = A.ctl;
-  if (threadIdx.x != 0 || blockIdx.x != 0 || c->active != 0) return;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int w = 0; w < W; ++w)
+    if (c->active[w] != 0) return;
   c->iter = 0;
   if (c->n_planes > kFirstPlanes) c->n_planes = kFirstPlanes;
   c->clear_plane = -1;
 }
 
-template <class OffT>
+template <class OffT, int W>
 __global__ void k_ms_clear_plane(MsArgs<OffT> A) {
   const int b = A.ctl->clear_plane;
   if (b < 0) return;
-  uint64_t* p = A.planes + (int64_t)b * A.n;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n; v += (int64_t)gridDim.x * blockDim.x)
-    p[v] = 0ull;
+  uint64_t* p = A.planes + (int64_t)b * A.n * W;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n * W; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0ull;
 }
 
-template <class OffT>
+template <class OffT, int W>
 __global__ void k_ms_clear_next(MsArgs<OffT> A) {
   uint64_t* next = (A.ctl->iter & 1) ? A.fb0 : A.fb1;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x)
-    next[v] = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n_cand * W;
+       i += (int64_t)gridDim.x * blockDim.x)
+    next[i] = 0ull;
 }
 
 // Top-down, part 1: chunk records for the rows of the frontier vertices.
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
   const uint64_t* front = (A.ctl->iter & 1) ? A.fb1 : A.fb0;
   const int64_t chunk = A.ctl->td_chunk;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
-    if (!front[v]) continue;
+    if (!any(ld_lanes<W>(front, v))) continue;
     const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
     if (d == 0) continue;
     const unsigned nch = (unsigned)ceil_div(d, chunk);
@@ -230,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
 
 // Top-down, part 2: one warp per record pushes front[u] to the unseen lanes
 // of each neighbour.
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   const MsCtl* c = A.ctl;
@@ -244,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
     const int2 rc = A.rec[r];
     const int32_t u = bc_vid(rc.x, A.n, &A.ctl->bc_site, kBcMsRecord);
-    const unsigned long long fu = front[u];
+    const Lanes<W> fu = ld_lanes<W>(front, u);
     int64_t ro = (int64_t)A.off[u], re = (int64_t)A.off[u + 1];
     bc_row(ro, re, A.nnz, &A.ctl->bc_site, kBcMsRow);
     const int64_t s = ro + (int64_t)rc.y * chunk;
@@ -252,8 +400,12 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
     if (lane == 0 && e > s) ex += (unsigned long long)(e - s);
     for (int64_t j = s + lane; j < e; j += 32) {
       const int32_t v = bc_vid(A.cols[j], A.n, &A.ctl->bc_site, kBcMsColumn);
-      const unsigned long long m = fu & ~__ldg(A.seen + v);
-      if (m && (m & ~__ldcg(next + v))) atomicOr(reinterpret_cast<unsigned long long*>(next + v), m);
+      const Lanes<W> m = and_not(fu, ldg_lanes<W>(A.seen, v));
+      if (!any(m)) continue;
+      const Lanes<W> nx = ldcg_lanes<W>(next, v);
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        if (m.w[w] & ~nx.w[w]) atomicOr(reinterpret_cast<unsigned long long*>(next + v * W + w), m.w[w]);
     }
   }
   ex = block_sum_u64(ex, sh);
@@ -261,52 +413,72 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
 }
 
 // Folds the lanes found at vertex v into the step's counters.
+template <int W>
 struct MsCount {
-  unsigned long long n = 0, m = 0, mu = 0, live = 0, ex = 0;
+  unsigned long long n = 0, m = 0, mu = 0, ex = 0;
+  unsigned long long live[W] = {};
 };
 
+template <int W>
+__device__ __forceinline__ void ms_count_flush(MsCtl* c, MsCount<W>& k, unsigned long long* sh, bool with_ex) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const unsigned long long lv = warp_or64(k.live[w]);
+    if (lane_id() == 0 && lv) atomicOr(&c->nx_live[w], lv);
+  }
+  k.n = block_sum_u64(k.n, sh);
+  k.m = block_sum_u64(k.m, sh);
+  k.mu = block_sum_u64(k.mu, sh);
+  if (with_ex) k.ex = block_sum_u64(k.ex, sh);
+  if (threadIdx.x == 0) {
+    if (k.n) atomicAdd(&c->nx_n, k.n);
+    if (k.m) atomicAdd(&c->nx_m, k.m);
+    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
+    if (with_ex && k.ex) atomicAdd(&c->nx_examined, k.ex);
+  }
+}
+
+// Records lanes nw (non-empty) newly found at v: seen, planes, counters.
+template <int W, class OffT>
+__device__ __forceinline__ void ms_found(const MsArgs<OffT>& A, int64_t v, const Lanes<W>& s, const Lanes<W>& nw,
+                                         int64_t deg, unsigned T, int np, MsCount<W>& k) {
+  Lanes<W> s2 = s;
+  or_into(s2, nw);
+  st_lanes<W>(A.seen, v, s2);
+  set_planes<W>(A, v, nw, T, np);
+  k.n += 1;
+  k.m += (unsigned long long)deg;
+  if (!any(s)) k.mu += (unsigned long long)deg;
+#pragma unroll
+  for (int w = 0; w < W; ++w) k.live[w] |= nw.w[w];
+}
+
 // Top-down, part 3: the pushed masks become the next frontier; record them.
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   MsCtl* c = A.ctl;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
-  const int64_t scan = c->bu_scan;
-  MsCount k;
+  MsCount<W> k;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long nx = next[v];
-    if (!nx) continue;
-    const unsigned long long s = A.seen[v];
-    const unsigned long long nw = nx & ~s;
-    next[v] = nw;
-    if (!nw) continue;
-    A.seen[v] = s | nw;
-    set_planes(A, v, nw, T, np);
-    const int64_t d = A.firstdeg[v].y;
-    k.n += 1;
-    k.m += (unsigned long long)d;
-    if (!s) k.mu += (unsigned long long)d;
-    k.live |= nw;
+    const Lanes<W> nx = ld_lanes<W>(next, v);
+    if (!any(nx)) continue;
+    const Lanes<W> s = ld_lanes<W>(A.seen, v);
+    const Lanes<W> nw = and_not(nx, s);
+    st_lanes<W>(next, v, nw);
+    if (!any(nw)) continue;
+    ms_found<W>(A, v, s, nw, A.firstdeg[v].y, T, np, k);
   }
-  const unsigned long long lv = warp_or64(k.live);
-  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
-  k.n = block_sum_u64(k.n, sh);
-  k.m = block_sum_u64(k.m, sh);
-  k.mu = block_sum_u64(k.mu, sh);
-  if (threadIdx.x == 0) {
-    if (k.n) atomicAdd(&c->nx_n, k.n);
-    if (k.m) atomicAdd(&c->nx_m, k.m);
-    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
-  }
+  ms_count_flush<W>(c, k, sh, false);
 }
 
 // Bottom-up, part 1: one vertex per thread. A vertex missing live lanes ORs
 // the frontier masks of its first bu_scan neighbours and stops once every
 // missing lane is found; longer rows continue in k_ms_bu_long with the
 // partial mask kept in next[v].
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   __shared__ int64_t s_tab[2 * kSmallDeg];
@@ -315,46 +487,46 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
   MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
-  const unsigned long long live = c->live;
+  const Lanes<W> live = ctl_lanes<W>(c->live);
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
   const int64_t scan = c->bu_scan;
-  MsCount k;
+  MsCount<W> k;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long s = A.seen[v];
-    const unsigned long long need = live & ~s;
-    if (!need) {
-      next[v] = 0ull;
+    const Lanes<W> s = ld_lanes<W>(A.seen, v);
+    const Lanes<W> need = and_not(live, s);
+    if (!any(need)) {
+      st_lanes<W>(next, v, zero_lanes<W>());
       continue;
     }
     const int2 fd = A.firstdeg[v];
-    unsigned long long acc = 0;
+    Lanes<W> acc = zero_lanes<W>();
     int64_t j = 0;
     if (fd.y > 0) {
-      acc = __ldg(front + bc_vid(fd.x, A.n, &A.ctl->bc_site, kBcMsColumn));
+      acc = ldg_lanes<W>(front, bc_vid(fd.x, A.n, &A.ctl->bc_site, kBcMsColumn));
       j = 1;
       // small degrees: the row start follows from the ID (no offset load)
       int64_t o = fd.y < A.small_deg ? s_tab[fd.y] + (v - s_tab[kSmallDeg + fd.y]) * fd.y : (int64_t)A.off[v];
       int64_t oe = o + fd.y;
       bc_row(o, oe, A.nnz, &A.ctl->bc_site, kBcMsRow);
       const int64_t lim = min(oe - o, scan);
-      while (j < lim && (acc & need) != need) {
+      while (j < lim && !covers(acc, need)) {
         int32_t u[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           u[t] = (j + t < lim) ? bc_vid(A.cols[o + j + t], A.n, &A.ctl->bc_site, kBcMsColumn) : -1;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (u[t] >= 0) acc |= __ldg(front + u[t]);
+          if (u[t] >= 0) or_into(acc, ldg_lanes<W>(front, u[t]));
         j = min(j + 4, lim);
       }
     }
     k.ex += (unsigned long long)j;
-    const unsigned long long nw = acc & need;
-    if (nw != need && fd.y > scan) {
+    const Lanes<W> nw = and_(acc, need);
+    if (!covers(nw, need) && fd.y > scan) {
       // partial: k_ms_bu_long scans the rest of the row in chunk records,
       // k_ms_bu_fin then records the vertex
-      next[v] = nw;
+      st_lanes<W>(next, v, nw);
       enqueue_ms(&c->n_def, A.def, (int32_t)v, A.n, &c->bc_site);
       if ((int64_t)fd.y - scan > kMsLongChunk) {  // chunks after the first go to chunk records
         const unsigned nch = (unsigned)ceil_div((int64_t)fd.y - scan, (int64_t)kMsLongChunk);
@@ -364,27 +536,11 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
       }
       continue;
     }
-    next[v] = nw;
-    if (!nw) continue;
-    A.seen[v] = s | nw;
-    set_planes(A, v, nw, T, np);
-    k.n += 1;
-    k.m += (unsigned long long)fd.y;
-    if (!s) k.mu += (unsigned long long)fd.y;
-    k.live |= nw;
+    st_lanes<W>(next, v, nw);
+    if (!any(nw)) continue;
+    ms_found<W>(A, v, s, nw, fd.y, T, np, k);
   }
-  const unsigned long long lv = warp_or64(k.live);
-  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
-  k.n = block_sum_u64(k.n, sh);
-  k.m = block_sum_u64(k.m, sh);
-  k.mu = block_sum_u64(k.mu, sh);
-  k.ex = block_sum_u64(k.ex, sh);
-  if (threadIdx.x == 0) {
-    if (k.n) atomicAdd(&c->nx_n, k.n);
-    if (k.m) atomicAdd(&c->nx_m, k.m);
-    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
-    if (k.ex) atomicAdd(&c->nx_examined, k.ex);
-  }
+  ms_count_flush<W>(c, k, sh, true);
 }
 
 // Bottom-up, part 2: the rest of the deferred rows, one warp per row for its
@@ -394,13 +550,13 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
 // row's first chunk is done: it skips if the lanes found so far (next[v],
 // OR-ed in by every warp of the row) already cover the row, and re-checks
 // every 1024 entries. Early-exit test after every 128 entries.
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
-  const unsigned long long live = c->live;
+  const Lanes<W> live = ctl_lanes<W>(c->live);
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
   const int64_t nd = c->n_def;
   const int64_t scan = c->bu_scan;
@@ -424,29 +580,33 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
       s0 = o + scan + (int64_t)rc.y * kMsLongChunk;
       e0 = min(e, s0 + kMsLongChunk);
     }
-    const unsigned long long need = live & ~A.seen[v];
-    unsigned long long acc = __ldcg(next + v);
+    const Lanes<W> need = and_not(live, ld_lanes<W>(A.seen, v));
+    Lanes<W> acc = ldcg_lanes<W>(next, v);
     int step = 0;
-    for (int64_t base = s0 & ~3ll; base < e0 && (acc & need) != need; base += 128, ++step) {
+    for (int64_t base = s0 & ~3ll; base < e0 && !covers(acc, need); base += 128, ++step) {
       if (i >= nd && (step & 7) == 7) {
-        acc |= __ldcg(next + v);  // what the row's other warps found
-        if ((acc & need) == need) break;
+        or_into(acc, ldcg_lanes<W>(next, v));  // what the row's other warps found
+        if (covers(acc, need)) break;
       }
       const int64_t p = base + 4 * (int64_t)lane;
-      unsigned long long x = 0;
+      Lanes<W> x = zero_lanes<W>();
       if (p < e0) {
         const int4 c4 = *reinterpret_cast<const int4*>(A.cols + p);
         const int32_t us[4] = {bc_vid(c4.x, A.n, &c->bc_site, kBcMsColumn), bc_vid(c4.y, A.n, &c->bc_site, kBcMsColumn),
                                bc_vid(c4.z, A.n, &c->bc_site, kBcMsColumn), bc_vid(c4.w, A.n, &c->bc_site, kBcMsColumn)};
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (p + t >= s0 && p + t < e0) x |= __ldg(front + us[t]);
+          if (p + t >= s0 && p + t < e0) or_into(x, ldg_lanes<W>(front, us[t]));
       }
-      acc |= warp_or64(x);
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc.w[w] |= warp_or64(x.w[w]);
       if (lane == 0) ex += (unsigned long long)(min(e0, base + 128) - max(s0, base));
     }
-    const unsigned long long nw = acc & need;
-    if (lane == 0 && nw) atomicOr(reinterpret_cast<unsigned long long*>(next + v), nw);
+    const Lanes<W> nw = and_(acc, need);
+    if (lane == 0)
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        if (nw.w[w]) atomicOr(reinterpret_cast<unsigned long long*>(next + (int64_t)v * W + w), nw.w[w]);
   }
   if (lane != 0) ex = 0;
   ex = block_sum_u64(ex, sh);
@@ -455,72 +615,63 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
 
 // Bottom-up, part 3: the deferred vertices, once every chunk of their rows
 // has been scanned: record the lanes found.
-template <class OffT>
+template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_bu_fin(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[kThreads / 32];
   MsCtl* c = A.ctl;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
-  const unsigned long long live = c->live;
+  const Lanes<W> live = ctl_lanes<W>(c->live);
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
   const int64_t nd = c->n_def;
-  MsCount k;
+  MsCount<W> k;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = bc_vid(A.def[i], A.n, &c->bc_site, kBcMsRecord);
-    const unsigned long long s = A.seen[v];
-    const unsigned long long nw = next[v] & live & ~s;
-    next[v] = nw;
-    if (!nw) continue;
-    A.seen[v] = s | nw;
-    set_planes(A, v, nw, T, np);
+    const Lanes<W> s = ld_lanes<W>(A.seen, v);
+    const Lanes<W> nw = and_not(and_(ld_lanes<W>(next, v), live), s);
+    st_lanes<W>(next, v, nw);
+    if (!any(nw)) continue;
     const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
-    k.n += 1;
-    k.m += (unsigned long long)d;
-    if (!s) k.mu += (unsigned long long)d;
-    k.live |= nw;
+    ms_found<W>(A, v, s, nw, d, T, np, k);
   }
-  const unsigned long long lv = warp_or64(k.live);
-  if (lane_id() == 0 && lv) atomicOr(&c->nx_live, lv);
-  k.n = block_sum_u64(k.n, sh);
-  k.m = block_sum_u64(k.m, sh);
-  k.mu = block_sum_u64(k.mu, sh);
-  if (threadIdx.x == 0) {
-    if (k.n) atomicAdd(&c->nx_n, k.n);
-    if (k.m) atomicAdd(&c->nx_m, k.m);
-    if (k.mu) atomicAdd(&c->nx_mu, k.mu);
-  }
+  ms_count_flush<W>(c, k, sh, false);
 }
 
-// Writes the levels of the lanes in F.lanes for every original ID, and with
-// F.release clears those lanes' bits.
+// Writes the levels of the lanes in F.lanes (of mask word F.word) for every
+// original ID, and with F.release clears those lanes' bits.
 // Levels of vertex v (original ID o) for the lanes in F.lanes, with at most
 // NP planes in use: the plane words are shifted right one lane at a time, so
 // every lane costs a few constant-shift operations per plane.
-template <int NP, class OffT>
+template <int NP, int W, class OffT>
 __device__ __forceinline__ void flush_vertex(const MsArgs<OffT>& A, const FlushArgs& F, int np, int64_t o, int64_t v,
                                              int32_t* const* s_out, const int32_t* s_start,
                                              unsigned long long& mu_back) {
-  const unsigned long long s = A.seen[v];
+  const int64_t vw = v * W + F.word;
+  const unsigned long long s = A.seen[vw];
   const unsigned long long hit = s & F.lanes;
   unsigned long long q[NP];
 #pragma unroll
-  for (int b = 0; b < NP; ++b) q[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n + v] : 0ull;
+  for (int b = 0; b < NP; ++b) q[b] = (hit && b < np) ? A.planes[(int64_t)b * A.n * W + vw] : 0ull;
   if (F.release && hit) {
     // a frontier bit of a lane only sits on a vertex that lane reached: clear
     // the released lanes in both frontier buffers too, so a lane reused later
     // starts from a clean frontier even if no step ran in between
-    A.fb0[v] &= ~F.lanes;
-    A.fb1[v] &= ~F.lanes;
-    A.seen[v] = s & ~F.lanes;
+    A.fb0[vw] &= ~F.lanes;
+    A.fb1[vw] &= ~F.lanes;
+    A.seen[vw] = s & ~F.lanes;
 #pragma unroll
     for (int b = 0; b < NP; ++b)
-      if (b < np) A.planes[(int64_t)b * A.n + v] = q[b] & ~F.lanes;
-    if (!(s & ~F.lanes)) mu_back += (unsigned long long)A.firstdeg[v].y;  // unseen by every lane again
+      if (b < np) A.planes[(int64_t)b * A.n * W + vw] = q[b] & ~F.lanes;
+    bool unseen = !(s & ~F.lanes);  // unseen by every lane again (the other words flush in their own launch)
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (w != F.word && A.seen[v * W + w]) unseen = false;
+    if (unseen) mu_back += (unsigned long long)A.firstdeg[v].y;
   }
   // lanes unrolled: every bit position is a compile-time constant, and the
   // lane test is uniform across the warp (F.lanes is the same for all threads)
 #pragma unroll
-  for (int i = 0; i < kMsLanes; ++i) {
+  for (int i = 0; i < kMsWordLanes; ++i) {
     if (!((F.lanes >> i) & 1ull)) continue;
     int32_t lev = -1;
     if ((hit >> i) & 1ull) {
@@ -536,13 +687,13 @@ __device__ __forceinline__ void flush_vertex(const MsArgs<OffT>& A, const FlushA
 // One kernel per plane-count class (NP = 4, 8, 16 planes at most): all three
 // are launched and the ones that do not match the planes in use return at
 // once, so the common case keeps a small register footprint.
-template <class OffT, int NP>
+template <class OffT, int W, int NP>
 __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs F) {
   const int np = A.ctl->n_planes;
   if (np > NP || (NP > 4 && np <= NP / 2)) return;
-  __shared__ int32_t* s_out[kMsLanes];
-  __shared__ int32_t s_start[kMsLanes];
-  if (threadIdx.x < kMsLanes) {
+  __shared__ int32_t* s_out[kMsWordLanes];
+  __shared__ int32_t s_start[kMsWordLanes];
+  if (threadIdx.x < kMsWordLanes) {
     s_out[threadIdx.x] = F.out[threadIdx.x];
     s_start[threadIdx.x] = F.start[threadIdx.x];
   }
@@ -550,14 +701,96 @@ __global__ void __launch_bounds__(kThreads) k_ms_flush(MsArgs<OffT> A, FlushArgs
   unsigned long long mu_back = 0;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < A.n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = A.o2n ? A.o2n[o] : o;
-    flush_vertex<NP>(A, F, np, o, v, s_out, s_start, mu_back);
+    flush_vertex<NP, W>(A, F, np, o, v, s_out, s_start, mu_back);
   }
   if (F.release) {
     __shared__ unsigned long long sh[kThreads / 32];
     mu_back = block_sum_u64(mu_back, sh);
     if (threadIdx.x == 0) {
       if (mu_back) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctl->m_u), mu_back);
-      if (blockIdx.x == 0) atomicAnd(&A.ctl->active, ~F.lanes);  // the lanes are free again
+      if (blockIdx.x == 0) atomicAnd(&A.ctl->active[F.word], ~F.lanes);  // the lanes are free again
+    }
+  }
+}
+
+// The flush for up to four discovery planes (iterations below 16, the usual
+// case) with four consecutive original IDs per thread: one 16-byte map load
+// and one 16-byte store per lane row instead of four of each.
+template <class OffT, int W>
+__global__ void __launch_bounds__(kThreads) k_ms_flush4v(MsArgs<OffT> A, FlushArgs F) {
+  const int np = A.ctl->n_planes;
+  if (np > 4) return;
+  __shared__ int32_t* s_out[kMsWordLanes];
+  __shared__ int32_t s_start[kMsWordLanes];
+  if (threadIdx.x < kMsWordLanes) {
+    s_out[threadIdx.x] = F.out[threadIdx.x];
+    s_start[threadIdx.x] = F.start[threadIdx.x];
+  }
+  __syncthreads();
+  unsigned long long mu_back = 0;
+  const int64_t quads = A.n >> 2;
+  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < quads; qd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = qd * 4;
+    int64_t v[4];
+    if (A.o2n) {
+      const int4 m4 = __ldg(reinterpret_cast<const int4*>(A.o2n) + qd);
+      v[0] = m4.x;
+      v[1] = m4.y;
+      v[2] = m4.z;
+      v[3] = m4.w;
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = o + t;
+    }
+    unsigned long long sv[4], hit[4], q[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      sv[t] = A.seen[v[t] * W + F.word];
+      hit[t] = sv[t] & F.lanes;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        q[t][b] = (hit[t] && b < np) ? A.planes[(int64_t)b * A.n * W + v[t] * W + F.word] : 0ull;
+    if (F.release) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (!hit[t]) continue;
+        const int64_t vw = v[t] * W + F.word;
+        A.fb0[vw] &= ~F.lanes;
+        A.fb1[vw] &= ~F.lanes;
+        A.seen[vw] = sv[t] & ~F.lanes;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (b < np) A.planes[(int64_t)b * A.n * W + vw] = q[t][b] & ~F.lanes;
+        bool unseen = !(sv[t] & ~F.lanes);  // the other words flush in their own launch
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+          if (w != F.word && A.seen[v[t] * W + w]) unseen = false;
+        if (unseen) mu_back += (unsigned long long)A.firstdeg[v[t]].y;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMsWordLanes; ++i) {
+      if (!((F.lanes >> i) & 1ull)) continue;
+      int32_t lev[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        unsigned T = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) T |= (unsigned)((q[t][b] >> i) & 1ull) << b;
+        lev[t] = ((hit[t] >> i) & 1ull) ? (int32_t)((T - (unsigned)s_start[i]) & kIterMask) : -1;
+      }
+      *reinterpret_cast<int4*>(s_out[i] + o) = make_int4(lev[0], lev[1], lev[2], lev[3]);
+    }
+  }
+  if (F.release) {
+    __shared__ unsigned long long sh[kThreads / 32];
+    mu_back = block_sum_u64(mu_back, sh);
+    if (threadIdx.x == 0) {
+      if (mu_back) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctl->m_u), mu_back);
+      if (blockIdx.x == 0) atomicAnd(&A.ctl->active[F.word], ~F.lanes);
     }
   }
 }
@@ -588,26 +821,26 @@ MsArgs<OffT> ms_args(MsGroup* m) {
 
 int ms_grid(int per_sm = 8) { return sm_count() * per_sm; }
 
-template <class OffT>
+template <class OffT, int W>
 int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   const int G = ms_grid();
-  k_ms_clear_plane<OffT><<<G, kThreads, 0, s>>>(A);
+  k_ms_clear_plane<OffT, W><<<G, kThreads, 0, s>>>(A);
   if (kase == 0) {
-    k_ms_clear_next<OffT><<<G, kThreads, 0, s>>>(A);
-    k_ms_td_list<OffT><<<G, kThreads, 0, s>>>(A);
-    k_ms_td<OffT><<<G, kThreads, 0, s>>>(A);
-    k_ms_td_post<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_clear_next<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_td_list<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_td<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_td_post<OffT, W><<<G, kThreads, 0, s>>>(A);
   } else {
-    k_ms_bu<OffT><<<G, kThreads, 0, s>>>(A);
-    k_ms_bu_long<OffT><<<G, kThreads, 0, s>>>(A);
-    k_ms_bu_fin<OffT><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu_long<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu_fin<OffT, W><<<G, kThreads, 0, s>>>(A);
   }
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
 
-template <class OffT>
+template <class OffT, int W>
 int ms_build_graph(MsGroup* m) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   cudaStream_t cs = nullptr;
@@ -635,7 +868,7 @@ int ms_build_graph(MsGroup* m) {
     return fail(set_error(DOBFS_ERR_CUDA, "conditional handle failed"));
   if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return fail(set_error(DOBFS_ERR_CUDA, "capture failed"));
-  k_ms_switch<OffT><<<1, 32, 0, cs>>>(A, h_while, h_case, 1);
+  k_ms_switch<OffT, W><<<1, 32, 0, cs>>>(A, h_while, h_case, 1);
   cudaGraph_t captured = nullptr;
   if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture failed"));
   size_t nn = 0;
@@ -655,7 +888,7 @@ int ms_build_graph(MsGroup* m) {
     if (cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return fail(set_error(DOBFS_ERR_CUDA, "capture case failed"));
-    const int rc = ms_launch_case<OffT>(m, k, cs);
+    const int rc = ms_launch_case<OffT, W>(m, k, cs);
     cudaGraph_t cap = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &cap);
     if (rc != DOBFS_OK) return fail(rc);
@@ -667,17 +900,17 @@ int ms_build_graph(MsGroup* m) {
   return DOBFS_OK;
 }
 
-template <class OffT>
+template <class OffT, int W>
 int ms_seed_impl(MsGroup* m, const SeedArgs& S) {
-  k_ms_seed<OffT><<<1, kMsLanes, 0, m->stream>>>(ms_args<OffT>(m), S);
+  k_ms_seed<OffT, W><<<1, kMsLanes, 0, m->stream>>>(ms_args<OffT>(m), S);
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
 
-template <class OffT>
+template <class OffT, int W>
 int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
-  k_ms_switch<OffT><<<1, 32, 0, m->stream>>>(A, 0, 0, 0);
+  k_ms_switch<OffT, W><<<1, 32, 0, m->stream>>>(A, 0, 0, 0);
   MsCtl c;
   DOBFS_CUDA_TRY(cudaMemcpyAsync(&c, m->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost, m->stream));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -689,7 +922,7 @@ int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, m->stream);
   }
-  const int rc = ms_launch_case<OffT>(m, c.step_case, m->stream);
+  const int rc = ms_launch_case<OffT, W>(m, c.step_case, m->stream);
   if (case_ms) {
     cudaEventRecord(e1, m->stream);
     cudaEventSynchronize(e1);
@@ -700,126 +933,61 @@ int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
   return rc;
 }
 
-// The flush for up to four discovery planes (iterations below 16, the usual
-// case) with four consecutive original IDs per thread: one 16-byte map load
-// and one 16-byte store per lane row instead of four of each.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_ms_flush4v(MsArgs<OffT> A, FlushArgs F) {
-  const int np = A.ctl->n_planes;
-  if (np > 4) return;
-  __shared__ int32_t* s_out[kMsLanes];
-  __shared__ int32_t s_start[kMsLanes];
-  if (threadIdx.x < kMsLanes) {
-    s_out[threadIdx.x] = F.out[threadIdx.x];
-    s_start[threadIdx.x] = F.start[threadIdx.x];
-  }
-  __syncthreads();
-  unsigned long long mu_back = 0;
-  const int64_t quads = A.n >> 2;
-  for (int64_t qd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qd < quads; qd += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = qd * 4;
-    int64_t v[4];
-    if (A.o2n) {
-      const int4 m4 = __ldg(reinterpret_cast<const int4*>(A.o2n) + qd);
-      v[0] = m4.x;
-      v[1] = m4.y;
-      v[2] = m4.z;
-      v[3] = m4.w;
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) v[t] = o + t;
-    }
-    unsigned long long sv[4], hit[4], q[4][4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      sv[t] = A.seen[v[t]];
-      hit[t] = sv[t] & F.lanes;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) q[t][b] = (hit[t] && b < np) ? A.planes[(int64_t)b * A.n + v[t]] : 0ull;
-    if (F.release) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (!hit[t]) continue;
-        A.fb0[v[t]] &= ~F.lanes;
-        A.fb1[v[t]] &= ~F.lanes;
-        A.seen[v[t]] = sv[t] & ~F.lanes;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (b < np) A.planes[(int64_t)b * A.n + v[t]] = q[t][b] & ~F.lanes;
-        if (!(sv[t] & ~F.lanes)) mu_back += (unsigned long long)A.firstdeg[v[t]].y;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kMsLanes; ++i) {
-      if (!((F.lanes >> i) & 1ull)) continue;
-      int32_t lev[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        unsigned T = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) T |= (unsigned)((q[t][b] >> i) & 1ull) << b;
-        lev[t] = ((hit[t] >> i) & 1ull) ? (int32_t)((T - (unsigned)s_start[i]) & kIterMask) : -1;
-      }
-      *reinterpret_cast<int4*>(s_out[i] + o) = make_int4(lev[0], lev[1], lev[2], lev[3]);
-    }
-  }
-  if (F.release) {
-    __shared__ unsigned long long sh[kThreads / 32];
-    mu_back = block_sum_u64(mu_back, sh);
-    if (threadIdx.x == 0) {
-      if (mu_back) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctl->m_u), mu_back);
-      if (blockIdx.x == 0) atomicAnd(&A.ctl->active, ~F.lanes);
-    }
-  }
-}
-
-template <class OffT>
+template <class OffT, int W>
 int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
   const int G = (int)std::min<int64_t>(ceil_div(m->g->n, kThreads), (int64_t)ms_grid(16));
   const MsArgs<OffT> A = ms_args<OffT>(m);
   if (F.vec)
-    k_ms_flush4v<OffT><<<G, kThreads, 0, m->stream>>>(A, F);
+    k_ms_flush4v<OffT, W><<<G, kThreads, 0, m->stream>>>(A, F);
   else
-    k_ms_flush<OffT, 4><<<G, kThreads, 0, m->stream>>>(A, F);
-  k_ms_flush<OffT, 8><<<G, kThreads, 0, m->stream>>>(A, F);
-  k_ms_flush<OffT, 16><<<G, kThreads, 0, m->stream>>>(A, F);
+    k_ms_flush<OffT, W, 4><<<G, kThreads, 0, m->stream>>>(A, F);
+  k_ms_flush<OffT, W, 8><<<G, kThreads, 0, m->stream>>>(A, F);
+  k_ms_flush<OffT, W, 16><<<G, kThreads, 0, m->stream>>>(A, F);
   DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
 
-template <class OffT>
+template <class OffT, int W>
 int ms_switch_async_impl(MsGroup* m, MsCtl* dst) {
-  k_ms_switch<OffT><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), 0, 0, 0);
+  k_ms_switch<OffT, W><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), 0, 0, 0);
   DOBFS_CUDA_TRY(cudaGetLastError());
   DOBFS_CUDA_TRY(cudaMemcpyAsync(dst, m->ctl.ptr, sizeof(MsCtl), cudaMemcpyDeviceToHost, m->stream));
   return DOBFS_OK;
 }
 
+template <class OffT, int W>
+int ms_rebase_impl(MsGroup* m) {
+  k_ms_rebase<OffT, W><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m));
+  DOBFS_CUDA_TRY(cudaGetLastError());
+  return DOBFS_OK;
+}
+
+// Calls F<OffT, W>(args...) for the group's offset type and mask words.
+#define MS_DISPATCH(m, F, ...)                                                            \
+  ((m)->g->off64 ? ((m)->words == 2 ? F<int64_t, 2>(__VA_ARGS__) : F<int64_t, 1>(__VA_ARGS__)) \
+                 : ((m)->words == 2 ? F<int32_t, 2>(__VA_ARGS__) : F<int32_t, 1>(__VA_ARGS__)))
+
 }  // namespace
 
-int ms_group_switch_async(MsGroup* m, MsCtl* dst) {
-  return m->g->off64 ? ms_switch_async_impl<int64_t>(m, dst) : ms_switch_async_impl<int32_t>(m, dst);
-}
+int ms_group_switch_async(MsGroup* m, MsCtl* dst) { return MS_DISPATCH(m, ms_switch_async_impl, m, dst); }
 
-int ms_group_case_async(MsGroup* m, int kase) {
-  return m->g->off64 ? ms_launch_case<int64_t>(m, kase, m->stream) : ms_launch_case<int32_t>(m, kase, m->stream);
-}
+int ms_group_case_async(MsGroup* m, int kase) { return MS_DISPATCH(m, ms_launch_case, m, kase, m->stream); }
 
-int64_t ms_group_bytes(const dobfs_graph* g) {
+int64_t ms_group_bytes(const dobfs_graph* g, int words) {
   const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
-  return (int64_t)sizeof(uint64_t) * g->n * (3 + kMsPlanes) + (int64_t)sizeof(int2) * (n_cand + g->nnz / kMsChunkMin + 64) +
-         (int64_t)sizeof(int32_t) * g->n + (int64_t)sizeof(MsCtl);
+  return (int64_t)sizeof(uint64_t) * g->n * words * (3 + kMsPlanes) +
+         (int64_t)sizeof(int2) * (n_cand + g->nnz / kMsChunkMin + 64) + (int64_t)sizeof(int32_t) * g->n +
+         (int64_t)sizeof(MsCtl);
 }
 
-int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out) {
+int ms_group_create(dobfs_graph* g, cudaStream_t s, int words, MsGroup** out) {
+  if (words < 1 || words > kMsMaxWords) return set_error(DOBFS_ERR_INVALID, "lane groups hold 1 or 2 mask words");
   MsGroup* m = new (std::nothrow) MsGroup();
   if (!m) return set_error(DOBFS_ERR_OOM, "host allocation failed");
   m->g = g;
   m->stream = s;
-  const size_t vb = sizeof(uint64_t) * (size_t)g->n;
+  m->words = words;
+  const size_t vb = sizeof(uint64_t) * (size_t)g->n * (size_t)words;
   int rc = m->seen.alloc(vb, s);
   if (rc == DOBFS_OK) rc = m->fb0.alloc(vb, s);
   if (rc == DOBFS_OK) rc = m->fb1.alloc(vb, s);
@@ -847,7 +1015,7 @@ void ms_group_destroy(MsGroup* m) {
 
 int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   cudaStream_t s = m->stream;
-  const size_t vb = sizeof(uint64_t) * (size_t)m->g->n;
+  const size_t vb = sizeof(uint64_t) * (size_t)m->g->n * (size_t)m->words;
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->seen.ptr, 0, vb, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb0.ptr, 0, vb, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb1.ptr, 0, vb, s));
@@ -871,49 +1039,49 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
 }
 
 int ms_group_seed(MsGroup* m, int count, const int32_t* lane, const int32_t* root) {
-  if (count < 0 || count > kMsLanes) return set_error(DOBFS_ERR_INVALID, "at most 64 lanes per seeding");
+  if (count < 0 || count > kMsWordLanes * m->words) return set_error(DOBFS_ERR_INVALID, "more lanes than the group has");
   SeedArgs S;
   S.count = count;
   for (int i = 0; i < count; ++i) {
+    if (lane[i] < 0 || lane[i] >= kMsWordLanes * m->words) return set_error(DOBFS_ERR_INVALID, "lane out of range");
     S.lane[i] = lane[i];
     S.root[i] = root[i];
   }
-  return m->g->off64 ? ms_seed_impl<int64_t>(m, S) : ms_seed_impl<int32_t>(m, S);
+  return MS_DISPATCH(m, ms_seed_impl, m, S);
 }
 
 int ms_group_step(MsGroup* m, MsCtl* after_switch, float* case_ms) {
-  return m->g->off64 ? ms_step_impl<int64_t>(m, after_switch, case_ms)
-                     : ms_step_impl<int32_t>(m, after_switch, case_ms);
+  return MS_DISPATCH(m, ms_step_impl, m, after_switch, case_ms);
 }
 
 int ms_group_run_to_end(MsGroup* m) {
-  if (!m->exec) DOBFS_TRY(m->g->off64 ? ms_build_graph<int64_t>(m) : ms_build_graph<int32_t>(m));
+  if (!m->exec) DOBFS_TRY(MS_DISPATCH(m, ms_build_graph, m));
   DOBFS_CUDA_TRY(cudaGraphLaunch(m->exec, m->stream));
   return DOBFS_OK;
 }
 
-int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_t* start, bool release) {
-  FlushArgs F;
-  memset(&F, 0, sizeof(F));
-  F.lanes = lanes;
-  F.release = release ? 1 : 0;
-  F.vec = (m->g->n % 4 == 0) ? 1 : 0;
-  for (int i = 0; i < kMsLanes; ++i) {
-    F.out[i] = ((lanes >> i) & 1ull) ? out[i] : nullptr;
-    F.start[i] = start ? start[i] : 0;
-    if (F.out[i] && (reinterpret_cast<uintptr_t>(F.out[i]) & 15)) F.vec = 0;
+int ms_group_flush(MsGroup* m, LaneMask lanes, int32_t* const* out, const int32_t* start, bool release) {
+  for (int w = 0; w < m->words; ++w) {
+    const uint64_t lw = lane_word(lanes, w);
+    if (!lw) continue;
+    FlushArgs F;
+    memset(&F, 0, sizeof(F));
+    F.lanes = lw;
+    F.word = w;
+    F.release = release ? 1 : 0;
+    F.vec = (m->g->n % 4 == 0) ? 1 : 0;
+    for (int i = 0; i < kMsWordLanes; ++i) {
+      const int l = kMsWordLanes * w + i;
+      F.out[i] = ((lw >> i) & 1ull) ? out[l] : nullptr;
+      F.start[i] = start ? start[l] : 0;
+      if (F.out[i] && (reinterpret_cast<uintptr_t>(F.out[i]) & 15)) F.vec = 0;
+    }
+    DOBFS_TRY(MS_DISPATCH(m, ms_flush_impl, m, F));
   }
-  return m->g->off64 ? ms_flush_impl<int64_t>(m, F) : ms_flush_impl<int32_t>(m, F);
-}
-
-int ms_group_rebase(MsGroup* m) {
-  if (m->g->off64)
-    k_ms_rebase<int64_t><<<1, 32, 0, m->stream>>>(ms_args<int64_t>(m));
-  else
-    k_ms_rebase<int32_t><<<1, 32, 0, m->stream>>>(ms_args<int32_t>(m));
-  DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
+
+int ms_group_rebase(MsGroup* m) { return MS_DISPATCH(m, ms_rebase_impl, m); }
 
 int ms_group_read_ctl(MsGroup* m, MsCtl* c) {
   DOBFS_CUDA_TRY(cudaMemcpyAsync(c, m->ctl.ptr, sizeof(MsCtl), cudaMemcpyDeviceToHost, m->stream));
@@ -958,20 +1126,28 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t s = o.stream ? (cudaStream_t)o.stream : g->stream;
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
-  if (!g->ms) DOBFS_TRY(ms_group_create(g, s, &g->ms));
+  // more than 64 roots run in 128-lane groups: a wide bottom-up step costs
+  // about the same for 128 lanes as for 64
+  const int words = n_roots > kMsWordLanes ? 2 : 1;
+  const int group_lanes = kMsWordLanes * words;
+  if (g->ms && g->ms->words != words) {
+    ms_group_destroy(g->ms);
+    g->ms = nullptr;
+  }
+  if (!g->ms) DOBFS_TRY(ms_group_create(g, s, words, &g->ms));
   MsGroup* m = g->ms;
   m->stream = s;
   const bool dev_out = is_device_ptr(level_out);
-  if (!dev_out && !g->ms_stage.ptr)
-    DOBFS_TRY(g->ms_stage.alloc(sizeof(int32_t) * (size_t)kMsLanes * (size_t)g->n, g->stream));
+  const size_t stage_bytes = sizeof(int32_t) * (size_t)group_lanes * (size_t)g->n;
+  if (!dev_out && g->ms_stage.bytes < stage_bytes) DOBFS_TRY(g->ms_stage.alloc(stage_bytes, g->stream));
   const bool host_loop = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
   g->batch_trace.clear();
   g->last_trace_batch = host_loop;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
   int32_t max_levels = 0;
   int64_t examined = 0;
-  for (int32_t b0 = 0; b0 < n_roots; b0 += kMsLanes) {
-    const int cnt = (int)std::min<int32_t>(kMsLanes, n_roots - b0);
+  for (int32_t b0 = 0; b0 < n_roots; b0 += group_lanes) {
+    const int cnt = (int)std::min<int32_t>(group_lanes, n_roots - b0);
     DOBFS_TRY(ms_group_reset(m, o));
     int32_t lanes[kMsLanes];
     for (int i = 0; i < cnt; ++i) lanes[i] = i;
@@ -1017,7 +1193,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     for (int i = 0; i < kMsLanes; ++i)
       outp[i] = i < cnt ? (dev_out ? level_out + (int64_t)(b0 + i) * g->n : g->ms_stage.as<int32_t>() + (int64_t)i * g->n)
                         : nullptr;
-    const uint64_t lm = cnt == 64 ? ~0ull : ((1ull << cnt) - 1ull);
+    const LaneMask lm = cnt == kMsLanes ? ~(LaneMask)0 : (lane_bit(cnt) - 1);
     DOBFS_TRY(ms_group_flush(m, lm, outp, nullptr, false));
     if (!dev_out)
       DOBFS_CUDA_TRY(cudaMemcpyAsync(level_out + (int64_t)b0 * g->n, g->ms_stage.ptr,

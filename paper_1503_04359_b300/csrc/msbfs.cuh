@@ -1,6 +1,6 @@
-// Bit-parallel multi-source BFS (64 roots per lane group) on a dobfs_graph.
+// Bit-parallel multi-source BFS (64 or 128 roots per lane group) on a dobfs_graph.
 //
-// Used by dobfs_run_batch (a group runs a batch of up to 64 roots to the end)
+// Used by dobfs_run_batch (a group runs a batch of up to 128 roots to the end)
 // and by the query server (lanes join and leave a running group at level
 // boundaries). A group owns its per-vertex lane masks and its control block;
 // the graph's CSR is shared read-only.
@@ -11,8 +11,24 @@
 
 namespace dobfs {
 
-constexpr int kMsLanes = 64;
+constexpr int kMsWordLanes = 64;                 // lanes per 64-bit mask word
+constexpr int kMsMaxWords = 2;                   // mask words per vertex: 64 or 128 lanes per group
+constexpr int kMsLanes = kMsWordLanes * kMsMaxWords;  // most lanes of a group
 constexpr int kMsPlanes = 16;  // discovery iterations are kept mod 2^16
+
+// Host-side set of up to kMsLanes lanes (bit l = lane l).
+using LaneMask = unsigned __int128;
+inline LaneMask lane_bit(int l) { return (LaneMask)1 << l; }
+inline uint64_t lane_word(LaneMask m, int w) { return (uint64_t)(m >> (kMsWordLanes * w)); }
+inline LaneMask lanes_of(const unsigned long long* words, int n_words) {
+  LaneMask m = 0;
+  for (int w = 0; w < n_words; ++w) m |= (LaneMask)words[w] << (kMsWordLanes * w);
+  return m;
+}
+inline int first_lane(LaneMask m) {  // m != 0
+  const uint64_t lo = (uint64_t)m;
+  return lo ? __builtin_ctzll(lo) : kMsWordLanes + __builtin_ctzll((uint64_t)(m >> kMsWordLanes));
+}
 
 // Device control block of a lane group.
 struct MsCtl {
@@ -24,11 +40,12 @@ struct MsCtl {
   int32_t n_planes;      // planes cleared so far (planes >= n_planes hold stale bits)
   int32_t clear_plane;   // plane the running step clears first (-1: none)
   int32_t levels_run;    // steps since the last reset
-  unsigned long long active;  // lanes holding a query
-  unsigned long long live;    // lanes with a non-empty frontier
+  unsigned long long active[kMsMaxWords];  // lanes holding a query
+  unsigned long long live[kMsMaxWords];    // lanes with a non-empty frontier
   int64_t n_f, m_f, m_u, n_f_prev;
   // accumulators of the running step
-  unsigned long long nx_n, nx_m, nx_mu, nx_live, nx_examined;
+  unsigned long long nx_n, nx_m, nx_mu, nx_examined;
+  unsigned long long nx_live[kMsMaxWords];
   unsigned int n_rec, n_def;
   // parameters
   int32_t mode, alpha, beta, td_chunk, bu_scan;  // policy and degree-bin cutoffs
@@ -41,8 +58,10 @@ struct MsCtl {
 struct MsGroup {
   dobfs_graph* g = nullptr;
   cudaStream_t stream = nullptr;
-  DevBuf seen, fb0, fb1;  // uint64[n]: lanes that reached v; frontier masks by iteration parity
-  DevBuf planes;          // uint64[kMsPlanes][n]: bit b of the discovery iteration, per lane
+  int words = 1;          // mask words per vertex: lanes = 64 * words
+  // per vertex v, words [v * words, (v + 1) * words) of each mask array
+  DevBuf seen, fb0, fb1;  // uint64[n][words]: lanes that reached v; frontier masks by iteration parity
+  DevBuf planes;          // uint64[kMsPlanes][n][words]: bit b of the discovery iteration, per lane
   DevBuf rec;             // int2[]: top-down chunk records
   int64_t rec_cap = 0;
   DevBuf def;             // int32[n]: bottom-up rows continued warp-wide
@@ -52,10 +71,11 @@ struct MsGroup {
   cudaGraphExec_t exec = nullptr;
 };
 
-// Device bytes of one lane group on g (what ms_group_create allocates).
-int64_t ms_group_bytes(const dobfs_graph* g);
-// Creates a group on g (allocates its masks); *out owned by the caller.
-int ms_group_create(dobfs_graph* g, cudaStream_t s, MsGroup** out);
+// Device bytes of one lane group of `words` mask words on g (what ms_group_create allocates).
+int64_t ms_group_bytes(const dobfs_graph* g, int words);
+// Creates a group of 64 * words lanes (words 1 or 2) on g (allocates its
+// masks); *out owned by the caller.
+int ms_group_create(dobfs_graph* g, cudaStream_t s, int words, MsGroup** out);
 void ms_group_destroy(MsGroup* m);
 
 // Clears every mask and counter (all lanes free).
@@ -73,7 +93,7 @@ int ms_group_run_to_end(MsGroup* m);
 // Writes levels of the lanes in `lanes` into out[i][n] (original IDs; -1 if
 // unreached), levels counted from start[i]; with `release` the lanes' bits
 // are cleared and the lanes freed.
-int ms_group_flush(MsGroup* m, uint64_t lanes, int32_t* const* out, const int32_t* start, bool release);
+int ms_group_flush(MsGroup* m, LaneMask lanes, int32_t* const* out, const int32_t* start, bool release);
 
 // Server loop pieces, all asynchronous on the group's stream: the direction
 // switch followed by a copy of the control block into `dst` (pinned host

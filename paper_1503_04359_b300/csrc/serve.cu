@@ -1,8 +1,8 @@
 // Query server: continuous batching of single-root BFS queries over several
 // resident graphs.
 //
-// Every added graph gets lane groups (64-lane bit-parallel traversals, see
-// msbfs.cu), each on its own CUDA stream, so the work of different graphs
+// Every added graph gets lane groups (64- or 128-lane bit-parallel
+// traversals, see msbfs.cu), each on its own CUDA stream, so the work of different graphs
 // and groups overlaps on the device. A scheduler thread runs the loop:
 //   1. launch the direction switch of every group that holds or awaits
 //      queries, with an asynchronous copy of its control block;
@@ -68,11 +68,12 @@ struct Group {
   cudaStream_t stream = nullptr;
   MsCtl* hctl = nullptr;  // pinned
   Query* lane_q[kMsLanes] = {};
-  uint64_t busy = 0;  // lanes holding a query
+  LaneMask all = 0;   // the group's lanes (64 per mask word)
+  LaneMask busy = 0;  // lanes holding a query
   bool in_flight = false;  // a switch and its control-block copy are queued
   cudaEvent_t ctl_ev = nullptr;
   int32_t cohort_iter = 0;  // iteration at which the group last went from idle to busy
-  uint64_t finished = 0;    // lanes done but not yet flushed
+  LaneMask finished = 0;    // lanes done but not yet flushed
   int32_t finish_iter[kMsLanes] = {};
   int64_t bytes = 0;
 };
@@ -119,7 +120,7 @@ struct dobfs_server {
 namespace dobfs {
 namespace {
 
-int64_t group_bytes(const dobfs_graph* g) { return ms_group_bytes(g); }
+int64_t group_bytes(const dobfs_server* S, const dobfs_graph* g) { return ms_group_bytes(g, S->opts.lane_words); }
 
 // Creates a lane group on engine e (scheduler thread, or add_graph).
 int add_group(dobfs_server* S, Engine* e) {
@@ -131,7 +132,8 @@ int add_group(dobfs_server* S, Engine* e) {
       cudaEventCreateWithFlags(&G->ctl_ev, cudaEventDisableTiming) != cudaSuccess) {
     rc = set_error(DOBFS_ERR_CUDA, "stream or pinned allocation failed");
   }
-  if (rc == DOBFS_OK) rc = ms_group_create(e->g, G->stream, &G->ms);
+  if (rc == DOBFS_OK) rc = ms_group_create(e->g, G->stream, S->opts.lane_words, &G->ms);
+  G->all = S->opts.lane_words == 2 ? ~(LaneMask)0 : (lane_bit(kMsWordLanes) - 1);
   if (rc == DOBFS_OK) {
     dobfs_run_opts o;
     dobfs_run_opts_init(&o);
@@ -148,7 +150,7 @@ int add_group(dobfs_server* S, Engine* e) {
     delete G;
     return rc;
   }
-  G->bytes = group_bytes(e->g);
+  G->bytes = group_bytes(S, e->g);
   e->groups.push_back(G);
   return DOBFS_OK;
 }
@@ -220,7 +222,7 @@ bool schedule_once(dobfs_server* S) {
           // an idle group starts a cohort once a full group of queries waits or
           // the oldest waiting query has waited gather_us
           if (e->pending.empty()) continue;
-          const bool full = e->pending.size() >= (size_t)kMsLanes;
+          const bool full = e->pending.size() >= (size_t)(kMsWordLanes * S->opts.lane_words);
           const bool old = now_ns() - e->pending.front()->t_submit >= (int64_t)S->opts.gather_us * 1000;
           if (!full && !old) {
             S->waiting_gpu = true;  // poll again shortly
@@ -255,26 +257,27 @@ bool schedule_once(dobfs_server* S) {
       // lanes whose frontier emptied; each flush is a pass over the whole
       // graph, so finished lanes are flushed together: when the group has no
       // live lane left, or once the oldest has waited flush_delay levels
-      const uint64_t done_now = G->busy & ~c.live & ~G->finished;
+      const LaneMask live = lanes_of(c.live, G->ms->words);
+      const LaneMask done_now = G->busy & ~live & ~G->finished;
       for (int i = 0; i < kMsLanes; ++i)
-        if ((done_now >> i) & 1ull) G->finish_iter[i] = c.iter;
+        if ((done_now >> i) & 1) G->finish_iter[i] = c.iter;
       G->finished |= done_now;
-      bool flush_now = G->finished && (c.live == 0 || S->opts.flush_delay <= 0);
+      bool flush_now = G->finished && (live == 0 || S->opts.flush_delay <= 0);
       for (int i = 0; i < kMsLanes && G->finished && !flush_now; ++i)
-        if (((G->finished >> i) & 1ull) && c.iter - G->finish_iter[i] >= S->opts.flush_delay) flush_now = true;
-      const uint64_t finished = flush_now ? G->finished : 0ull;
+        if (((G->finished >> i) & 1) && c.iter - G->finish_iter[i] >= S->opts.flush_delay) flush_now = true;
+      const LaneMask finished = flush_now ? G->finished : 0;
       if (finished) {
         int32_t* outs[kMsLanes] = {};
         int32_t starts[kMsLanes] = {};
         for (int i = 0; i < kMsLanes; ++i)
-          if ((finished >> i) & 1ull) {
+          if ((finished >> i) & 1) {
             Query* q = G->lane_q[i];
             outs[i] = q->host_out ? q->stage.as<int32_t>() : q->out;
             starts[i] = q->start_iter;
           }
         int rc = ms_group_flush(G->ms, finished, outs, starts, true);
         for (int i = 0; i < kMsLanes && rc == DOBFS_OK; ++i)
-          if ((finished >> i) & 1ull) {
+          if ((finished >> i) & 1) {
             Query* q = G->lane_q[i];
             if (q->host_out && cudaMemcpyAsync(q->out, q->stage.ptr, sizeof(int32_t) * (size_t)g->n,
                                                cudaMemcpyDeviceToHost, G->stream) != cudaSuccess)
@@ -315,7 +318,7 @@ bool schedule_once(dobfs_server* S) {
       if (idle) G->cohort_iter = c.iter;
       const bool light = S->opts.admit_div <= 0 || c.n_f * (int64_t)S->opts.admit_div < g->n;
       const bool can_join = (G->busy == 0) || (light && c.iter - G->cohort_iter <= S->opts.join_window);
-      uint64_t freel = can_join ? ~G->busy : 0ull;
+      LaneMask freel = can_join ? (G->all & ~G->busy) : 0;
       while (freel && !e->pending.empty()) {
         Query* q = e->pending.front();
         const int64_t need = q->host_out ? (int64_t)sizeof(int32_t) * g->n : 0;
@@ -330,13 +333,13 @@ bool schedule_once(dobfs_server* S) {
           break;
         }
         e->pending.pop_front();
-        const int lane = __builtin_ctzll(freel);
+        const int lane = first_lane(freel);
         freel &= freel - 1;
         q->start_iter = c.iter;
         q->t_admit = now_ns();
         q->state = kRunning;
         G->lane_q[lane] = q;
-        G->busy |= 1ull << lane;
+        G->busy |= lane_bit(lane);
         lanes[k] = lane;
         roots[k] = q->root;
         ++k;
@@ -350,7 +353,7 @@ bool schedule_once(dobfs_server* S) {
         fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
         return false;
       }
-      if (c.live || k) {
+      if (live || k) {
         S->group_steps += 1;
         if (ms_group_case_async(G->ms, c.step_case) != DOBFS_OK) {
           fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
@@ -371,11 +374,11 @@ bool schedule_once(dobfs_server* S) {
     for (Group* G : e->groups) {
       const bool light = S->opts.admit_div <= 0 || G->hctl->n_f * (int64_t)S->opts.admit_div < g->n;
       const bool can_join =
-          (G->busy == 0) || (light && G->hctl->iter - G->cohort_iter <= S->opts.join_window && ~G->busy != 0);
+          (G->busy == 0) || (light && G->hctl->iter - G->cohort_iter <= S->opts.join_window && (G->all & ~G->busy) != 0);
       all_full = all_full && !can_join;
     }
     if (!e->pending.empty() && all_full && (int)e->groups.size() < S->opts.max_groups_per_graph) {
-      const int64_t gb = group_bytes(g);
+      const int64_t gb = group_bytes(S, g);
       bool ok;
       {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -470,6 +473,7 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   o->gather_us = 2000;
   o->ss_max = 1;
   o->ss_backlog = 4;
+  o->lane_words = 2;
   return DOBFS_OK;
 }
 
@@ -482,7 +486,8 @@ int dobfs_serve_create(const dobfs_serve_opts* opts, dobfs_server** out) {
   if (opts) o = *opts;
   if (o.groups_per_graph < 1 || o.max_groups_per_graph < o.groups_per_graph || o.alpha < 1 || o.beta < 1 ||
       o.direction < 0 || o.direction > DOBFS_DIR_RANDOM || o.max_device_bytes < 0 || o.admit_div < 0 ||
-      o.join_window < 0 || o.flush_delay < 0 || o.gather_us < 0 || o.ss_max < 0 || o.ss_backlog < 0)
+      o.join_window < 0 || o.flush_delay < 0 || o.gather_us < 0 || o.ss_max < 0 || o.ss_backlog < 0 ||
+      o.lane_words < 1 || o.lane_words > kMsMaxWords)
     return set_error(DOBFS_ERR_INVALID, "bad server options");
   dobfs_server* S = new (std::nothrow) dobfs_server();
   if (!S) return set_error(DOBFS_ERR_OOM, "host allocation failed");
@@ -515,7 +520,7 @@ int dobfs_serve_add_graph(dobfs_server* S, dobfs_graph* g, int32_t* gid) {
     delete e;
     return set_error(DOBFS_ERR_CUDA, "stream or pinned allocation failed");
   }
-  const int64_t gb = group_bytes(g) * S->opts.groups_per_graph;
+  const int64_t gb = group_bytes(S, g) * S->opts.groups_per_graph;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->reserved + gb > S->budget) {

@@ -83,7 +83,7 @@ class dobfs_serve_opts(ctypes.Structure):
                 ("max_groups_per_graph", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("admit_div", ctypes.c_int32), ("join_window", ctypes.c_int32),
                 ("flush_delay", ctypes.c_int32), ("gather_us", ctypes.c_int32), ("ss_max", ctypes.c_int32),
-                ("ss_backlog", ctypes.c_int32)]
+                ("ss_backlog", ctypes.c_int32), ("lane_words", ctypes.c_int32)]
 
 
 class dobfs_query_result(ctypes.Structure):
@@ -353,7 +353,7 @@ def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_gr
                     alpha: int | None = None, beta: int | None = None, direction: int = DOBFS_DIR_AUTO,
                     admit_div: int | None = None, join_window: int | None = None,
                     flush_delay: int | None = None, gather_us: int | None = None, ss_max: int | None = None,
-                    ss_backlog: int | None = None) -> dobfs_serve_opts:
+                    ss_backlog: int | None = None, lane_words: int | None = None) -> dobfs_serve_opts:
     o = dobfs_serve_opts()
     _check(load().dobfs_serve_opts_init(ctypes.byref(o)))
     if admit_div is not None:
@@ -364,6 +364,8 @@ def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_gr
         o.flush_delay = flush_delay
     if gather_us is not None:
         o.gather_us = gather_us
+    if lane_words is not None:
+        o.lane_words = lane_words
     if ss_max is not None:
         o.ss_max = ss_max
     if ss_backlog is not None:

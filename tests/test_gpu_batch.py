@@ -2,7 +2,7 @@
 
 Every row of the batch output must equal the oracle's level array for that
 root bit-exact, whatever the direction schedule, the batch size (full and
-partial lane groups, several groups) or repeated roots.
+partial lane groups, several groups, 64- and 128-lane groups) or repeated roots.
 """
 import numpy as np
 import pytest
@@ -29,7 +29,7 @@ def d():
 def s14():
     spec = inputs.rmat(14)
     og = oracle.csr_from_rmat(spec)
-    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 100, og.degrees() > 0)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 300, og.degrees() > 0)
     lv, _ = oracle.bfs_many(og, roots, want_parent=False)
     return spec, og, roots, lv
 
@@ -53,7 +53,7 @@ def _batch(d, g, roots, mode=0, seed=0, host=False, **kw):
 def test_batch_levels_bit_exact(d, s14, mode, seed, flags):
     spec, og, roots, ref = s14
     g = d.rmat_graph(spec, flags=flags)
-    out = _batch(d, g, roots, mode, seed)          # one full group of 64 and a partial one of 36
+    out = _batch(d, g, roots, mode, seed)          # two full 128-lane groups and a partial one of 44
     np.testing.assert_array_equal(out, ref)
 
 
@@ -71,11 +71,14 @@ def test_batch_degree_bin_cutoffs(d, s14, cut):
 def test_batch_sizes_duplicates_host(d, s14):
     spec, og, roots, ref = s14
     g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64)
-    for k in (1, 3, 63, 64, 65):
+    # 64 roots or fewer: one 64-lane group; more: 128-lane groups, full and partial
+    for k in (1, 3, 63, 64, 65, 127, 128, 129, 300):
         np.testing.assert_array_equal(_batch(d, g, roots[:k]), ref[:k])
+    np.testing.assert_array_equal(_batch(d, g, roots[:40]), ref[:40])  # back to 64 lanes
     dup = np.array([roots[0], roots[1], roots[0], roots[0]], dtype=np.int32)
     np.testing.assert_array_equal(_batch(d, g, dup), ref[[0, 1, 0, 0]])
     np.testing.assert_array_equal(_batch(d, g, roots[:70], host=True), ref[:70])
+    np.testing.assert_array_equal(_batch(d, g, roots[:200], host=True), ref[:200])
     # same as single-source runs of the same graph
     lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
     g.run(int(roots[5]), lv)

@@ -34,7 +34,7 @@ def graphs(d):
     for scale, flags in ((11, 0), (13, 0x2), (15, 0x2)):
         spec = inputs.rmat(scale)
         og = oracle.csr_from_rmat(spec)
-        roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 80, og.degrees() > 0)
+        roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 160, og.degrees() > 0)
         ref, _ = oracle.bfs_many(og, roots, want_parent=False)
         out.append((d.rmat_graph(spec, flags=flags), og, roots, ref))
     return out
@@ -50,11 +50,13 @@ def _wait(d, srv, ticket, timeout=60.0):
         time.sleep(0.0005)
 
 
-@pytest.mark.parametrize("ss_max", [0, 2])
-def test_alone_and_in_the_mix(d, graphs, ss_max):
+@pytest.mark.parametrize("ss_max,lane_words", [(0, 1), (2, 1), (0, 2), (2, 2)])
+def test_alone_and_in_the_mix(d, graphs, ss_max, lane_words):
     """ss_max = 0: every query runs in a lane group; 2: lone queries take the
-    single-source path and bursts the lane groups."""
-    srv = d.dobfs_serve_create(d.make_serve_opts(max_groups_per_graph=2, ss_max=ss_max))
+    single-source path and bursts the lane groups. Groups of 64 lanes
+    (lane_words 1) or 128 (2); the mix holds more queries per graph than a
+    group has lanes."""
+    srv = d.dobfs_serve_create(d.make_serve_opts(max_groups_per_graph=2, ss_max=ss_max, lane_words=lane_words))
     try:
         gids = [d.dobfs_serve_add_graph(srv, g.handle) for g, _, _, _ in graphs]
         # alone: one query at a time
@@ -70,7 +72,8 @@ def test_alone_and_in_the_mix(d, graphs, ss_max):
         # the mix: every query of every graph submitted at once (more than a lane group holds
         # per graph, so queries may wait for lanes or a second group); host outputs for some
         outs, tickets = {}, {}
-        for k in range(80):
+        n_mix = 160 if lane_words == 2 else 80
+        for k in range(n_mix):
             for gi, (g, og, roots, ref) in enumerate(graphs):
                 if k % 7 == 3:
                     out = np.full(og.n, 9, dtype=np.int32)
@@ -87,7 +90,7 @@ def test_alone_and_in_the_mix(d, graphs, ss_max):
             if (gi, k) in alone:
                 np.testing.assert_array_equal(got, alone[(gi, k)])
         st = d.dobfs_serve_get_stats(srv)
-        assert st.completed == 9 + 240 and st.in_flight == 0
+        assert st.completed == 9 + 3 * n_mix and st.in_flight == 0
     finally:
         d.dobfs_serve_destroy(srv)
 
