@@ -337,7 +337,7 @@ typedef struct {
                                    waited this long (default 2000 us; 0: at once) */
   int32_t ss_max;               /* while at most this many queries of a graph wait, they run as single-
                                    source BFS (dobfs_run) on the graph's own stream instead (device
-                                   outputs only; default 1; 0: never) */
+                                   outputs only; default 2; 0: never) */
   int32_t ss_backlog;           /* ... as long as fewer than this many are already queued there (default 4) */
   int32_t lane_words;           /* lanes per group: 64 * lane_words, 1 or 2 (default 2: a wide bottom-up
                                    step scans whole rows anyway, so 128 lanes cost about what 64 do) */

@@ -471,7 +471,7 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   o->join_window = 1;
   o->flush_delay = 3;
   o->gather_us = 2000;
-  o->ss_max = 1;
+  o->ss_max = 2;
   o->ss_backlog = 4;
   o->lane_words = 2;
   return DOBFS_OK;
