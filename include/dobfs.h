@@ -322,7 +322,8 @@ typedef struct dobfs_server dobfs_server;
 typedef struct {
   int64_t max_device_bytes;     /* device-memory budget for lane groups and staging (0: 90% of free memory) */
   int32_t groups_per_graph;     /* lane groups created per graph up front (default 1) */
-  int32_t max_groups_per_graph; /* upper bound on groups per graph (default 2) */
+  int32_t max_groups_per_graph; /* upper bound on groups per graph (default 1: one full cohort at a time
+                                   beats two half-full ones, since a wide step costs the same either way) */
   int32_t alpha, beta;          /* direction rule of the lane groups (defaults DOBFS_BATCH_ALPHA, 24);
                                    the single-source path uses dobfs_run_opts_init's */
   int32_t direction;            /* DOBFS_DIR_AUTO / TOPDOWN / BOTTOMUP / RANDOM */

@@ -463,7 +463,7 @@ int dobfs_serve_opts_init(dobfs_serve_opts* o) {
   memset(o, 0, sizeof(*o));
   o->max_device_bytes = 0;
   o->groups_per_graph = 1;
-  o->max_groups_per_graph = 2;
+  o->max_groups_per_graph = 1;
   o->alpha = DOBFS_BATCH_ALPHA;
   o->beta = 24;
   o->direction = DOBFS_DIR_AUTO;

@@ -349,7 +349,8 @@ def dobfs_serve_opts_init() -> dobfs_serve_opts:
     return o
 
 
-def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_groups_per_graph: int = 2,
+def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int | None = None,
+                    max_groups_per_graph: int | None = None,
                     alpha: int | None = None, beta: int | None = None, direction: int = DOBFS_DIR_AUTO,
                     admit_div: int | None = None, join_window: int | None = None,
                     flush_delay: int | None = None, gather_us: int | None = None, ss_max: int | None = None,
@@ -371,8 +372,10 @@ def make_serve_opts(max_device_bytes: int = 0, groups_per_graph: int = 1, max_gr
     if ss_backlog is not None:
         o.ss_backlog = ss_backlog
     o.max_device_bytes = max_device_bytes
-    o.groups_per_graph = groups_per_graph
-    o.max_groups_per_graph = max_groups_per_graph
+    if groups_per_graph is not None:
+        o.groups_per_graph = groups_per_graph
+    if max_groups_per_graph is not None:
+        o.max_groups_per_graph = max_groups_per_graph
     if alpha is not None:
         o.alpha = alpha
     if beta is not None:
