@@ -251,7 +251,7 @@ def cpu_baseline(scale: int = 22, n_roots: int = 4) -> dict:
 
 
 def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps: int = 3) -> dict:
-    """Batched BFS (64-lane bit-parallel groups) against one-at-a-time runs on
+    """Batched BFS (bit-parallel lane groups of 64 or 128 roots) against one-at-a-time runs on
     the same R-MAT graph: roots/s for batches of 64/256/1024 seeded roots and
     for 64 sequential single-source runs (levels only in both), with device
     time from CUDA events. Outputs stay on the device (1024 x n int32)."""

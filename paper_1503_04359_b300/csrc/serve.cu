@@ -190,7 +190,7 @@ bool schedule_once(dobfs_server* S) {
       Query* q = e->pending.front();
       e->pending.pop_front();
       dobfs_run_opts o;
-      dobfs_run_opts_init(&o);  // single-source defaults (the lane groups' alpha suits 64 lanes)
+      dobfs_run_opts_init(&o);  // single-source defaults (the lane groups' alpha suits many lanes)
       o.stream = (void*)e->ss_stream;
       int rc = dobfs_run(e->g, q->root, q->out, nullptr, &o, nullptr);
       q->levels_h = e->ss_levels + (e->ss_next++ % kSsRing);

@@ -1,4 +1,4 @@
-"""GPU parity of batched (64-lane bit-parallel) BFS against the CPU oracle.
+"""GPU parity of batched (bit-parallel lane groups) BFS against the CPU oracle.
 
 Every row of the batch output must equal the oracle's level array for that
 root bit-exact, whatever the direction schedule, the batch size (full and
