@@ -53,6 +53,7 @@ constexpr int kThreads = 256;
 constexpr int kTdSmall = 16;     // top-down rows up to this length: one thread
 constexpr int kChunk = 512;      // top-down chunk record length (entries)
 constexpr int kBuT = 32;         // bottom-up entries scanned per thread before deferring
+constexpr int kTdClaimPer = 8;   // top-down chunk entries claimed per lane per step (4: 0.5 % slower at scale 28)
 constexpr int kTdSmallMin = 8;   // smallest allowed cutoffs (they size the record buffer)
 constexpr int kChunkMin = 256;
 constexpr int kCases = 6;      // step kinds of the level loop's switch node
@@ -110,33 +111,41 @@ __device__ __forceinline__ void enqueue(unsigned int* tail, int32_t* q, int32_t 
 // winners write (level, parent) and read their degree. Keeping the four
 // chains independent overlaps their memory latencies. Returns the winners
 // as a 4-bit mask; `m_new` accumulates their degrees.
-template <class OffT>
-__device__ __forceinline__ unsigned td_claim4(const BfsArgs<OffT>& A, const int32_t (&v)[4], unsigned valid,
+template <int N, class OffT>
+__device__ __forceinline__ unsigned td_claimN(const BfsArgs<OffT>& A, const int32_t (&v)[N], unsigned valid,
                                               int32_t u, int32_t next_level, unsigned long long& m_new) {
-  uint32_t w[4];
+  uint32_t w[N];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) w[t] = ((valid >> t) & 1u) ? __ldcg(A.visited + (v[t] >> 5)) : ~0u;
+  for (int t = 0; t < N; ++t) w[t] = ((valid >> t) & 1u) ? __ldcg(A.visited + (v[t] >> 5)) : ~0u;
   unsigned cand = 0;
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < N; ++t)
     if (!((w[t] >> (v[t] & 31)) & 1u)) cand |= 1u << t;
   unsigned won = 0;
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < N; ++t)
     if ((cand >> t) & 1u) {
       const uint32_t bit = 1u << (v[t] & 31);
       if (!(atomicOr(A.visited + (v[t] >> 5), bit) & bit)) won |= 1u << t;
     }
-  int32_t d[4] = {0, 0, 0, 0};
+  int32_t d[N];
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < N; ++t) {
+    d[t] = 0;
     if ((won >> t) & 1u) {
       A.lp[v[t]] = make_int2(next_level, u);
       d[t] = __ldg(&A.firstdeg[v[t]].y);
     }
+  }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) m_new += (unsigned long long)d[t];
+  for (int t = 0; t < N; ++t) m_new += (unsigned long long)d[t];
   return won;
+}
+
+template <class OffT>
+__device__ __forceinline__ unsigned td_claim4(const BfsArgs<OffT>& A, const int32_t (&v)[4], unsigned valid,
+                                              int32_t u, int32_t next_level, unsigned long long& m_new) {
+  return td_claimN<4>(A, v, valid, u, next_level, m_new);
 }
 
 // Top-down marking without claims (bitmap-output top-down steps): a
@@ -341,18 +350,19 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
     if (BM && x > 0 && e - s > small) s = lower_bound_col(A.cols, s, e, x);
     ex += (unsigned long long)(e - s);
     if (e - s <= small) {
-      for (int64_t j = s; j < e; j += 4) {
-        int32_t v[4];
+      constexpr int kE = 4;  // entries per step (short rows: wider steps measured no faster)
+      for (int64_t j = s; j < e; j += kE) {
+        int32_t v[kE];
         unsigned valid = 0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kE; ++t) {
           v[t] = (j + t < e) ? bc_vid(A.cols[j + t], A.n, &A.ctl->bc_site, kBcTdColumn) : 0;
           if (j + t < e && v[t] >= x) valid |= 1u << t;
         }
-        if (BM) {
+        if constexpr (BM) {
           td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
         } else {
-          unsigned won = td_claim4(A, v, valid, u, L + 1, m_new);
+          unsigned won = td_claimN<kE>(A, v, valid, u, L + 1, m_new);
           while (won) {
             const int t = __ffs(won) - 1;
             won &= won - 1;
@@ -421,25 +431,28 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
       hi = min(e, lo + chunk);
       lo_ok = max(s, lo);
     }
-    for (int64_t pb = lo; pb < hi; pb += 128) {  // uniform trip count: the warp enqueues together
-      const int64_t p = pb + 4 * (int64_t)lane;
-      int32_t v[4] = {0, 0, 0, 0};
+    constexpr int kE = BM ? 4 : kTdClaimPer;  // entries per lane per step
+    for (int64_t pb = lo; pb < hi; pb += 32 * kE) {  // uniform trip count: the warp enqueues together
+      const int64_t p = pb + kE * (int64_t)lane;
+      int32_t v[kE];
       unsigned valid = 0;
-      if (p < hi) {
-        const int4 x = *reinterpret_cast<const int4*>(A.cols + p);
-        v[0] = bc_vid(x.x, A.n, &A.ctl->bc_site, kBcTdColumn);
-        v[1] = bc_vid(x.y, A.n, &A.ctl->bc_site, kBcTdColumn);
-        v[2] = bc_vid(x.z, A.n, &A.ctl->bc_site, kBcTdColumn);
-        v[3] = bc_vid(x.w, A.n, &A.ctl->bc_site, kBcTdColumn);
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
+      for (int h = 0; h < kE; h += 4) {
+        int4 x = make_int4(0, 0, 0, 0);
+        if (p + h < hi) x = *reinterpret_cast<const int4*>(A.cols + p + h);
+        v[h] = bc_vid(x.x, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[h + 1] = bc_vid(x.y, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[h + 2] = bc_vid(x.z, A.n, &A.ctl->bc_site, kBcTdColumn);
+        v[h + 3] = bc_vid(x.w, A.n, &A.ctl->bc_site, kBcTdColumn);
       }
-      if (BM) {
+#pragma unroll
+      for (int t = 0; t < kE; ++t)
+        if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
+      if constexpr (BM) {
         if (valid) td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
         continue;
       }
-      const unsigned won = valid ? td_claim4(A, v, valid, u, L + 1, m_new) : 0u;
+      const unsigned won = valid ? td_claimN<kE>(A, v, valid, u, L + 1, m_new) : 0u;
       const unsigned cnt = (unsigned)__popc(won);
       unsigned incl = cnt;
 #pragma unroll
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
         qb = __shfl_sync(0xffffffffu, qb, 31);
         unsigned pos = qb + incl - cnt;
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < kE; ++t)
           if ((won >> t) & 1u) {
             if (bc_pos(pos, A.n, &A.ctl->bc_site, kBcTdQueue)) nxt[pos] = v[t];
             ++pos;
