@@ -164,3 +164,23 @@ def test_config3b_chunglu26_streaming_check(d):
     assert rc.tolist() == [0, 0, 0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
     np.testing.assert_array_equal(parents[2:], canon[2:])
     assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(4))
+
+
+def test_config2_rmat22_batched_256_roots(d):
+    """Batched BFS at scale 22 in 128-lane groups (256 roots = two full
+    groups): every 16th row bit-exact with the oracle's serial BFS, the rest
+    through the streaming invariant checker."""
+    spec = inputs.rmat(22)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0x256, og.n, 256, og.degrees() > 0)
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    out = torch.empty((256, og.n), dtype=torch.int32, device="cuda")
+    d.dobfs_run_batch(g.handle, torch.from_numpy(np.ascontiguousarray(roots)).cuda(), out)
+    lv = out.cpu().numpy()
+    del out
+    g.close()
+    ref, _ = oracle.bfs_many(og, roots[::16], want_parent=False)
+    np.testing.assert_array_equal(lv[::16], ref)
+    for b in range(0, 256, 64):
+        rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, roots[b:b + 64], lv[b:b + 64])
+        assert rc.tolist() == [0] * 64, [(oracle.RULES[int(r)], int(x)) for r, x in zip(rc, bad)]
