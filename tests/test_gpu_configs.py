@@ -184,3 +184,39 @@ def test_config2_rmat22_batched_256_roots(d):
     for b in range(0, 256, 64):
         rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, roots[b:b + 64], lv[b:b + 64])
         assert rc.tolist() == [0] * 64, [(oracle.RULES[int(r)], int(x)) for r, x in zip(rc, bad)]
+
+
+def test_config5_served_mix_rmat18_20(d):
+    """The server with its default options (128-lane groups, one group per
+    graph) on R-MAT scale 18 and 20 graphs, 150 queries per graph submitted at
+    once: every 10th result bit-exact with the oracle, every result through
+    the streaming invariant checker."""
+    specs = [inputs.rmat(18), inputs.rmat(20)]
+    graphs = [d.rmat_graph(s, flags=d.DOBFS_GRAPH_REINDEX) for s in specs]
+    srv = d.dobfs_serve_create()
+    try:
+        gids = [d.dobfs_serve_add_graph(srv, g.handle) for g in graphs]
+        outs, tickets, roots = {}, {}, {}
+        ogs = [oracle.csr_from_rmat(s) for s in specs]
+        for gi, og in enumerate(ogs):
+            roots[gi] = inputs.sample_roots(inputs.root_seed(specs[gi].seed) ^ 0x5E7E, og.n, 150, og.degrees() > 0)
+        for k in range(150):
+            for gi, g in enumerate(graphs):
+                out = torch.full((g.n,), 9, dtype=torch.int32, device="cuda")
+                outs[(gi, k)] = out
+                tickets[(gi, k)] = d.dobfs_serve_submit(srv, gids[gi], int(roots[gi][k]), out)
+        t0 = time.time()
+        for key, t in tickets.items():
+            while d.dobfs_serve_poll(srv, t) is None:
+                assert time.time() - t0 < 300, "queries did not finish"
+                time.sleep(0.001)
+        for gi, spec in enumerate(specs):
+            lv = np.stack([outs[(gi, k)].cpu().numpy() for k in range(150)])
+            ref, _ = oracle.bfs_many(ogs[gi], roots[gi][::10], want_parent=False)
+            np.testing.assert_array_equal(lv[::10], ref)
+            rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, roots[gi], lv)
+            assert rc.tolist() == [0] * 150, [(oracle.RULES[int(r)], int(x)) for r, x in zip(rc, bad)]
+    finally:
+        d.dobfs_serve_destroy(srv)
+        for g in graphs:
+            g.close()
