@@ -305,14 +305,17 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
 
 
 def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000, 5000, 10000, 20000, 50000),
-                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 120.0, serve_opts=None) -> dict:
+                  seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 120.0, min_slots: int = 256,
+                  serve_opts=None) -> dict:
     """Open-loop serving: R-MAT graphs of the given scales resident, Poisson
     arrivals (seeded exponential gaps) at each rate, graph ids uniform, roots
     uniform over degree >= 1 vertices. Latency runs from the scheduled arrival
     to the completion the server reports (CLOCK_MONOTONIC), so a harness that
     falls behind its schedule is charged for it. Output buffers come from a
-    per-graph pool of device slots (out_gb in all); a query whose graph has no
-    free slot waits in its graph's FIFO without holding up other graphs. The
+    per-graph pool of device slots: an even share of out_gb, at least
+    min_slots (two full 128-lane cohorts: one running while the next gathers)
+    and at most 1024 per graph; a query whose graph has no free slot waits in
+    its graph's FIFO without holding up other graphs. The
     one-at-a-time baseline is the device time of single-source runs (levels
     only) averaged over the same mix."""
     graphs, pools, slots = [], [], []
@@ -323,7 +326,7 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
         g = dobfs.rmat_graph(spec, flags=dobfs.DOBFS_GRAPH_REINDEX)
         deg = g.degrees()
         pool = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0x5E7E, g.n, 1024, deg > 0)
-        k = int(max(16, min(1024, per_graph_bytes // (4 * g.n))))
+        k = int(min(1024, max(min_slots, per_graph_bytes // (4 * g.n))))
         slots.append(torch.empty((k, g.n), dtype=torch.int32, device="cuda"))
         lv = torch.empty(g.n, dtype=torch.int32, device="cuda")
         ms = [g.run(int(r), lv, None, want_stats=True).device_ms for r in pool[:8]]
