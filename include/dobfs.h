@@ -334,8 +334,9 @@ typedef struct {
   int32_t flush_delay;          /* finished lanes of a group are written out together when no lane is
                                    left running, or once the oldest has waited this many levels
                                    (default 3; 0: at once) */
-  int32_t gather_us;            /* an idle group starts a cohort when 64 queries wait or the oldest has
-                                   waited this long (default 2000 us; 0: at once) */
+  int32_t gather_us;            /* an idle group starts a cohort when a full group of queries (64 *
+                                   lane_words) waits or the oldest has waited this long (default
+                                   2000 us; 0: at once) */
   int32_t ss_max;               /* while at most this many queries of a graph wait, they run as single-
                                    source BFS (dobfs_run) on the graph's own stream instead (device
                                    outputs only; default 2; 0: never) */
