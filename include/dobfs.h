@@ -266,6 +266,21 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
               const dobfs_run_opts* opts, dobfs_run_stats* stats);
 
 /*
+ * Waits at most timeout_ms milliseconds (< 0: no limit; 0: only test) for
+ * the work the library has queued for g: its last run or batch, on whatever
+ * stream it ran, with everything queued before it on that stream. Runs and
+ * batches with device outputs return once launched; this bounds the wait for
+ * them. Returns DOBFS_OK once that work is done (or if none was queued),
+ * DOBFS_ERR_TIMEOUT if it is still running at the limit (nothing is
+ * cancelled: it completes later, and a later wait returns DOBFS_OK),
+ * DOBFS_ERR_CUDA if it failed, DOBFS_ERR_INVALID for a NULL graph. The
+ * graph must not be destroyed during the wait. The library's kernels never
+ * wait on one another: the level loop is a CUDA graph whose conditional nodes
+ * end it on the device, so host waits are the only waits there are.
+ */
+int dobfs_graph_wait(dobfs_graph* g, int32_t timeout_ms);
+
+/*
  * Batched BFS from n_roots roots (original IDs) with the bit-parallel
  * multi-source traversal: roots are the lanes of traversals in which every
  * vertex carries lane masks (lanes that reached it, lanes for which it is in

@@ -14,6 +14,9 @@
 // neighbours by increasing new ID, i.e. by decreasing degree — the highest-
 // degree neighbour first, which shortens bottom-up scans.
 #include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../dobfs_inputs/gen.h"
@@ -1299,6 +1302,26 @@ int dobfs_graph_degrees(const dobfs_graph* gc, int32_t* deg_out, void* stream) {
   if (!dev) DOBFS_CUDA_TRY(cudaMemcpyAsync(deg_out, dst, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
   return DOBFS_OK;
+}
+
+int dobfs_graph_wait(dobfs_graph* g, int32_t timeout_ms) {
+  clear_error();
+  if (!g) return set_error(DOBFS_ERR_INVALID, "graph is NULL");
+  cudaEvent_t ev;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    ev = g->ev_done;  // created with the run workspace, never replaced
+  }
+  if (!ev) return DOBFS_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return DOBFS_OK;
+    if (e != cudaErrorNotReady) return set_error(DOBFS_ERR_CUDA, "graph work failed: %s", cudaGetErrorString(e));
+    if (timeout_ms >= 0 && std::chrono::steady_clock::now() - t0 >= std::chrono::milliseconds(timeout_ms))
+      return set_error(DOBFS_ERR_TIMEOUT, "graph work still running after %d ms", timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
 }
 
 int dobfs_graph_get_info(const dobfs_graph* g, dobfs_graph_info* info) {

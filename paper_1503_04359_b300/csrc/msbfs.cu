@@ -261,6 +261,8 @@ __global__ void k_ms_seed(MsArgs<OffT> A, SeedArgs S) {
   }
 }
 
+__global__ void k_ms_set_ctl(MsCtl* dst, MsCtl c) { *dst = c; }
+
 template <class OffT, int W>
 __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
                             int in_graph) {
@@ -1033,8 +1035,10 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   c.td_chunk = o.td_chunk ? o.td_chunk : kMsChunk;
   c.bu_scan = o.bu_scan ? o.bu_scan : kMsT;
   c.sched_seed = o.schedule_seed;
-  DOBFS_CUDA_TRY(cudaMemcpyAsync(m->ctl.ptr, &c, sizeof(c), cudaMemcpyHostToDevice, s));
-  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));  // c is on this stack
+  // written by a kernel that takes the block by value, so the host neither
+  // keeps a staging copy alive nor waits for the stream
+  k_ms_set_ctl<<<1, 1, 0, s>>>(m->ctl.as<MsCtl>(), c);
+  DOBFS_CUDA_TRY(cudaGetLastError());
   return DOBFS_OK;
 }
 

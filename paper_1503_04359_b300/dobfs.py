@@ -127,6 +127,7 @@ def load() -> ctypes.CDLL:
         "dobfs_graph_degrees": (c_int, [G, vp, vp]),
         "dobfs_graph_save": (c_int, [G, ctypes.c_char_p, vp]),
         "dobfs_debug_set_column": (c_int, [G, i64, i32]),
+        "dobfs_graph_wait": (c_int, [G, i32]),
         "dobfs_graph_load": (c_int, [ctypes.c_char_p, u32, vp, ctypes.POINTER(G)]),
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
         "dobfs_run": (c_int, [G, i32, vp, vp, ctypes.POINTER(dobfs_run_opts), ctypes.POINTER(dobfs_run_stats)]),
@@ -272,6 +273,16 @@ def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
 
 def dobfs_debug_set_column(g: int, pos: int, value: int) -> None:
     _check(load().dobfs_debug_set_column(g, pos, value))
+
+
+def dobfs_graph_wait(g: int, timeout_ms: int = -1) -> bool:
+    """True once the graph's queued work is done, False if it is still running
+    after timeout_ms (< 0: no limit); raises if it failed."""
+    st = load().dobfs_graph_wait(g, int(timeout_ms))
+    if st == DOBFS_ERR_TIMEOUT:
+        return False
+    _check(st)
+    return True
 
 
 def dobfs_graph_save(g: int, path: str, stream=None) -> None:
@@ -496,6 +507,9 @@ class Graph:
 
     def run(self, root: int, level_out, parent_out=None, opts=None, want_stats: bool = False):
         return dobfs_run(self.handle, root, level_out, parent_out, opts, want_stats)
+
+    def wait(self, timeout_ms: int = -1) -> bool:
+        return dobfs_graph_wait(self.handle, timeout_ms)
 
     def trace(self):
         return dobfs_last_trace(self.handle)

@@ -1,4 +1,5 @@
-"""Failure handling, injected on the host: device allocations that fail.
+"""Failure handling, injected on the host: device allocations that fail, and
+bounded host waits that run out.
 
 The library takes every device allocation through the allocator hook
 (dobfs_set_allocator). A counting allocator that delegates to PyTorch and
@@ -198,3 +199,48 @@ def test_graph_load_fails_cleanly_at_every_allocation(d, tmp_path):
     root = int(inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 1, og.degrees() > 0)[0])
     np.testing.assert_array_equal(_levels(d, h, root), oracle.bfs(og, root)[0])
     h.close()
+
+
+def test_bounded_wait_runs_out_then_completes(d):
+    """dobfs_graph_wait: a run and a batch queued behind a fixed-length
+    spinning kernel (torch.cuda._sleep, about half a second) are still running
+    at a 0 ms and a 20 ms limit (DOBFS_ERR_TIMEOUT; nothing is cancelled), and
+    a wait without limit then returns once they are done, with the oracle's
+    levels. No GPU wait is involved: the kernels only run late."""
+    spec = inputs.rmat(14)
+    og = oracle.csr_from_rmat(spec)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 3, og.degrees() > 0)
+    ref, _ = oracle.bfs_many(og, roots, want_parent=False)
+    g = d.rmat_graph(spec)
+    assert g.wait(0)  # nothing queued
+    s = torch.cuda.Stream()
+    lv = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+    out = torch.full((2, g.n), 7, dtype=torch.int32, device="cuda")
+    o = d.make_opts(stream=s)
+    # warm-up: the run workspace, its CUDA graph and the batch's lane group
+    # exist afterwards, so the calls below only queue work
+    g.run(int(roots[0]), lv, None, o)
+    d.dobfs_run_batch(g.handle, np.ascontiguousarray(roots[1:]), out, opts=o)
+    assert g.wait(-1)
+    for batch in (False, True):
+        lv.fill_(7)
+        out.fill_(7)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(1_000_000_000)
+        if batch:
+            d.dobfs_run_batch(g.handle, np.ascontiguousarray(roots[1:]), out, opts=o)
+        else:
+            g.run(int(roots[0]), lv, None, o)
+        assert not g.wait(0)
+        assert not g.wait(20)
+        assert "still running" in d.last_error()
+        assert g.wait(-1)
+        if batch:
+            np.testing.assert_array_equal(out.cpu().numpy(), ref[1:])
+        else:
+            np.testing.assert_array_equal(lv.cpu().numpy(), ref[0])
+    g.close()
+    with pytest.raises(d.DobfsError) as e:
+        d.dobfs_graph_wait(None, 0)
+    assert e.value.status == d.DOBFS_ERR_INVALID
