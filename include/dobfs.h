@@ -299,6 +299,9 @@ int dobfs_graph_wait(dobfs_graph* g, int32_t timeout_ms);
  * dobfs_run_opts_init except alpha = DOBFS_BATCH_ALPHA (the union frontier of
  * 64 lanes reaches a bottom-up size sooner than one lane's). stats
  * (nullable): device_ms, levels (deepest group), edges_examined.
+ * Asynchronous on the batch's stream when level_out is device memory and
+ * stats is NULL (device roots are first read back with a synchronous copy);
+ * otherwise the call returns when the levels are written.
  */
 #define DOBFS_BATCH_ALPHA 4
 int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32_t* level_out, int32_t* parent_out,
