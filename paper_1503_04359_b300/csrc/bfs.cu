@@ -946,6 +946,7 @@ int resident_grid(K kernel) {
     cudaGetLastError();
     per_sm = 4;
   }
+  fit_carveout(kernel, kThreads, per_sm);
   return grid_cap(per_sm);
 }
 

@@ -172,4 +172,32 @@ enum BoundsSite {
 
 const char* bounds_site_name(int site);
 
+// Sets a kernel's shared-memory carve-out to what min(per_sm, its occupancy)
+// resident blocks of `threads` threads need, so the rest of the SM's on-chip
+// memory serves as L1 (the default carve-out reserves more shared memory
+// than these kernels use). Reverts to the default if the smaller carve-out
+// would lower the kernel's occupancy. A hint only: results never depend on it.
+template <class K>
+void fit_carveout(K kernel, int threads, int per_sm) {
+  int occ = 0, dev = 0, smem_sm = 0, reserve = 0;
+  cudaFuncAttributes fa;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1 ||
+      cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      smem_sm <= 0) {
+    cudaGetLastError();
+    return;
+  }
+  const int want = per_sm < occ ? per_sm : occ;
+  const int64_t need = (int64_t)want * ((int64_t)fa.sharedSizeBytes + reserve);
+  const int pct = (int)((need * 100 + smem_sm - 1) / smem_sm);
+  int after = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct < 100 ? pct : 100) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&after, kernel, threads, 0) != cudaSuccess || after < want)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, -1);
+  cudaGetLastError();
+}
+
 }  // namespace dobfs
