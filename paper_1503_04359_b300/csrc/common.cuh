@@ -174,9 +174,8 @@ const char* bounds_site_name(int site);
 
 // Sets a kernel's shared-memory carve-out to what min(per_sm, its occupancy)
 // resident blocks of `threads` threads need, so the rest of the SM's on-chip
-// memory serves as L1 (the default carve-out reserves more shared memory
-// than these kernels use). Reverts to the default if the smaller carve-out
-// would lower the kernel's occupancy. A hint only: results never depend on it.
+// memory serves as L1. Reverts to the default if the smaller carve-out would
+// lower the kernel's occupancy. A hint only: results never depend on it.
 template <class K>
 void fit_carveout(K kernel, int threads, int per_sm) {
   int occ = 0, dev = 0, smem_sm = 0, reserve = 0;
