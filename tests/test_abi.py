@@ -55,6 +55,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.dobfs_run(None, 0, None, None, None, None) == dobfs.DOBFS_ERR_INVALID
     assert lib.dobfs_graph_get_info(None, None) == dobfs.DOBFS_ERR_INVALID
     assert lib.dobfs_graph_destroy(None) == dobfs.DOBFS_OK
+    assert lib.dobfs_graph_wait(None, 0) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_save(None, b"x", None) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_load(None, 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_INVALID
+    assert lib.dobfs_graph_load(b"x", 0x80, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_INVALID
     o = dobfs.dobfs_run_opts()
     assert lib.dobfs_run_opts_init(ctypes.byref(o)) == 0
     assert (o.direction, o.alpha, o.beta) == (dobfs.DOBFS_DIR_AUTO, 14, 24)
@@ -75,3 +79,23 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(dobfs, "LIB_PATH", "/nonexistent/libdobfs.so")
     with pytest.raises(ImportError):
         dobfs.load()
+
+
+def test_graph_file_header_checks_without_gpu(lib, tmp_path):
+    """dobfs_graph_load refuses missing files and bad headers before any CUDA call."""
+    h = ctypes.c_void_p()
+    assert lib.dobfs_graph_load(os.fsencode(tmp_path / "missing.dobfs"), 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_IO
+    assert "cannot open" in dobfs.last_error()
+    short = tmp_path / "short.dobfs"
+    short.write_bytes(b"DOBFSCSR")
+    assert lib.dobfs_graph_load(os.fsencode(short), 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_IO
+    assert "truncated" in dobfs.last_error()
+    other = tmp_path / "other.dobfs"
+    other.write_bytes(b"NOTAGRPH" + bytes(56))
+    assert lib.dobfs_graph_load(os.fsencode(other), 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_IO
+    assert "not a dobfs graph file" in dobfs.last_error()
+    newer = tmp_path / "newer.dobfs"
+    newer.write_bytes(b"DOBFSCSR" + (99).to_bytes(4, "little") + bytes(52))
+    assert lib.dobfs_graph_load(os.fsencode(newer), 0, None, ctypes.byref(h)) == dobfs.DOBFS_ERR_IO
+    assert "version 99" in dobfs.last_error()
+    assert not h.value
