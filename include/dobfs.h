@@ -46,7 +46,7 @@ typedef enum {
   DOBFS_ERR_OOM = -2,         /* device allocation failed */
   DOBFS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   DOBFS_ERR_BAD_GRAPH = -4,   /* column out of range, or asymmetric input under VALIDATE */
-  DOBFS_ERR_TIMEOUT = -5,     /* a bounded device or host wait ran out */
+  DOBFS_ERR_TIMEOUT = -5,     /* a bounded host wait ran out (dobfs_graph_wait) */
   DOBFS_ERR_BUSY = -6,        /* admission refused: no free slot or not enough free memory */
   DOBFS_ERR_IO = -7,          /* graph file: cannot open, read or write, or not a valid graph file */
   DOBFS_ERR_BOUNDS = -8       /* bounds-check builds only: a device index check failed (see below) */
