@@ -10,9 +10,14 @@ What it computes (see ``dobfs_oracle.c`` for the passages followed):
 * ``csr_from_pairs`` / ``csr_from_rmat`` — the undirected graph as CSR, each
   undirected edge stored as two directed edges, self-loops and duplicates
   dropped, rows sorted (Sec. 4, "Methodology").
+* ``csr_from_rmat_par`` — the same CSR built by several threads (host graphs
+  of billions of entries); equal to ``csr_from_rmat``.
 * ``bfs`` — serial FIFO-queue BFS: level = hop distance (the result every
   top-down / bottom-up schedule of Algorithm 1 reaches), canonical parent =
   smallest-ID neighbour one level up.
+* ``bfs_partial`` — the same BFS stopped after a given number of adjacency
+  entries (a bounded timing sample on graphs too large to traverse on one
+  core in the time allowed); every level it writes is the full BFS level.
 * ``check_bfs`` / ``check_bfs_rmat_stream`` — the BFS invariants (level[root]=0,
   |level(u)-level(v)| <= 1 on every edge, every reached vertex has a neighbour
   one level up, every parent a neighbour one level up, reached set = the
@@ -25,7 +30,9 @@ What it computes (see ``dobfs_oracle.c`` for the passages followed):
 Pins (tests/test_oracle.py): brute force on all roots of random tiny graphs;
 closed forms (path, cycle, star, complete graph, binary tree, grid, Petersen
 graph, disjoint unions, isolated root); planted mistakes caught by the
-invariant checker. Parity status: levels and canonical parents pinned; no
+invariant checker; the threaded CSR equal to the set-based and serial ones;
+the stopped BFS a prefix of the closed-form path levels and, with no limit,
+equal to the full BFS. Parity status: levels and canonical parents pinned; no
 numeric example is printed in the paper, so no value is taken from it.
 """
 from __future__ import annotations
@@ -86,8 +93,12 @@ def _load():
         lib.oracle_csr_from_pairs.argtypes = [i64, i64, P32, P32, P64, P32]
         lib.oracle_csr_from_rmat.restype = i64
         lib.oracle_csr_from_rmat.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, P64, P32]
+        lib.oracle_csr_from_rmat_par.restype = i64
+        lib.oracle_csr_from_rmat_par.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, P64, P32, i32]
         lib.oracle_bfs.restype = i32
         lib.oracle_bfs.argtypes = [i64, P64, P32, i32, P32, P32]
+        lib.oracle_bfs_partial.restype = i64
+        lib.oracle_bfs_partial.argtypes = [i64, P64, P32, i32, P32, i64]
         lib.oracle_bfs_many.restype = None
         lib.oracle_bfs_many.argtypes = [i64, P64, P32, i32, P32, P32, P32, i32]
         lib.oracle_components.restype = None
@@ -156,6 +167,20 @@ def csr_from_rmat(spec) -> Csr:
     return Csr(off, cols[:nnz].copy())
 
 
+def csr_from_rmat_par(spec, n_threads: int | None = None) -> Csr:
+    """The CSR of csr_from_rmat built by several threads (host graphs of
+    billions of entries). The column array is returned as a view of the
+    placement buffer (2 * n_pairs entries) to avoid a second copy."""
+    lib = _load()
+    n, m = spec.n_vertices, spec.n_pairs
+    off = np.zeros(n + 1, dtype=np.int64)
+    cols = np.empty(2 * m, dtype=np.int32)
+    ta, tab, tabc = spec.thresholds
+    nnz = lib.oracle_csr_from_rmat_par(spec.scale, m, ta, tab, tabc, spec.seed, _p(off, ctypes.c_int64),
+                                       _p(cols, ctypes.c_int32), n_threads or os.cpu_count() or 1)
+    return Csr(off, cols[:nnz])
+
+
 def bfs(g: Csr, root: int, want_parent: bool = True):
     """Serial BFS: (level, canonical parent or None, number of levels)."""
     lib = _load()
@@ -164,6 +189,16 @@ def bfs(g: Csr, root: int, want_parent: bool = True):
     nlev = lib.oracle_bfs(g.n, _p(g.off, ctypes.c_int64), _p(g.cols, ctypes.c_int32), int(root),
                           _p(level, ctypes.c_int32), _p(parent, ctypes.c_int32) if want_parent else None)
     return level, parent, nlev
+
+
+def bfs_partial(g: Csr, root: int, max_entries: int):
+    """The serial BFS stopped after reading max_entries adjacency entries:
+    (level, entries read). Every level written is the full BFS level."""
+    lib = _load()
+    level = np.empty(g.n, dtype=np.int32)
+    read = lib.oracle_bfs_partial(g.n, _p(g.off, ctypes.c_int64), _p(g.cols, ctypes.c_int32), int(root),
+                                  _p(level, ctypes.c_int32), int(max_entries))
+    return level, int(read)
 
 
 def bfs_many(g: Csr, roots, want_parent: bool = True, n_threads: int | None = None):

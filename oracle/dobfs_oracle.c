@@ -109,6 +109,67 @@ int64_t oracle_csr_from_rmat(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, 
 }
 
 /*
+ * The CSR of oracle_csr_from_rmat built by n_threads threads, for graphs of
+ * billions of entries (R-MAT scale 28: 8.6 G entries before de-duplication).
+ * Same counting placement, spread over threads: the pair stream is split
+ * into ranges, each thread counts its pairs' endpoints into the row counts
+ * with atomic increments; after the prefix sum each thread places its pairs
+ * at atomically advanced row cursors (so the order inside a row differs from
+ * the serial placement, which the row sort removes); rows are then sorted
+ * and de-duplicated in parallel, and finally moved down over the removed
+ * duplicates in row order. The result equals oracle_csr_from_rmat's.
+ */
+int64_t oracle_csr_from_rmat_par(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
+                                 uint64_t seed, int64_t* off, int32_t* cols, int32_t n_threads) {
+  const int64_t n = (int64_t)1 << scale;
+  const uint64_t kp = gen_key_pairs(seed), kq = gen_key_perm(seed);
+  const int nt = n_threads > 0 ? n_threads : 1;
+  (void)nt;
+  memset(off, 0, sizeof(int64_t) * (size_t)(n + 1));
+#pragma omp parallel for schedule(static, 1 << 16) num_threads(nt)
+  for (int64_t i = 0; i < m; ++i) {
+    uint32_t u, v;
+    gen_rmat_pair((uint64_t)i, scale, t_a, t_ab, t_abc, kp, kq, &u, &v);
+    if (u == v) continue;
+    __atomic_fetch_add(&off[u + 1], 1, __ATOMIC_RELAXED);
+    __atomic_fetch_add(&off[v + 1], 1, __ATOMIC_RELAXED);
+  }
+  for (int64_t u = 0; u < n; ++u) off[u + 1] += off[u];
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  memcpy(pos, off, sizeof(int64_t) * (size_t)n);
+#pragma omp parallel for schedule(static, 1 << 16) num_threads(nt)
+  for (int64_t i = 0; i < m; ++i) {
+    uint32_t u, v;
+    gen_rmat_pair((uint64_t)i, scale, t_a, t_ab, t_abc, kp, kq, &u, &v);
+    if (u == v) continue;
+    cols[__atomic_fetch_add(&pos[u], 1, __ATOMIC_RELAXED)] = (int32_t)v;
+    cols[__atomic_fetch_add(&pos[v], 1, __ATOMIC_RELAXED)] = (int32_t)u;
+  }
+  /* sort each row and drop its duplicates in place; pos[u] = kept length */
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nt)
+  for (int64_t u = 0; u < n; ++u) {
+    const int64_t s = off[u], e = off[u + 1];
+    qsort(cols + s, (size_t)(e - s), sizeof(int32_t), cmp_i32);
+    int64_t w = s;
+    for (int64_t j = s; j < e; ++j) {
+      if (j > s && cols[j] == cols[j - 1]) continue;
+      cols[w++] = cols[j];
+    }
+    pos[u] = w - s;
+  }
+  int64_t w = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    const int64_t s = off[u], len = pos[u];
+    if (w != s) memmove(cols + w, cols + s, sizeof(int32_t) * (size_t)len);
+    off[u] = w;
+    w += len;
+  }
+  off[n] = w;
+  free(pos);
+  return w;
+}
+
+/*
  * Serial FIFO-queue BFS from `root` (plain definition of the BFS level).
  * level[v] = hop distance from root, -1 if unreachable. If parent is not
  * NULL it receives the canonical parent: for v != root reached,
@@ -148,6 +209,39 @@ int32_t oracle_bfs(int64_t n, const int64_t* off, const int32_t* cols, int32_t r
     parent[root] = root;
   }
   return maxlev + 1;
+}
+
+/*
+ * The FIFO-queue BFS of oracle_bfs, stopped once it has read max_entries
+ * adjacency entries (a bounded sample of one BFS on a graph too large to
+ * traverse in full on one core in the time allowed). Levels are assigned
+ * when a vertex is first reached, so every level written equals the full
+ * BFS level; vertices not reached by then keep -1. Returns the number of
+ * entries read: every entry of every row started, so it may exceed
+ * max_entries by less than one row. With max_entries >= the stored entries
+ * the result is oracle_bfs's level array.
+ */
+int64_t oracle_bfs_partial(int64_t n, const int64_t* off, const int32_t* cols, int32_t root, int32_t* level,
+                           int64_t max_entries) {
+  for (int64_t v = 0; v < n; ++v) level[v] = -1;
+  if (root < 0 || root >= n) return 0;
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int64_t head = 0, tail = 0, read = 0;
+  level[root] = 0;
+  queue[tail++] = root;
+  while (head < tail && read < max_entries) {
+    const int32_t u = queue[head++];
+    for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+      const int32_t v = cols[j];
+      if (level[v] == -1) {
+        level[v] = level[u] + 1;
+        queue[tail++] = v;
+      }
+    }
+    read += off[u + 1] - off[u];
+  }
+  free(queue);
+  return read;
 }
 
 /* oracle_bfs for several roots; root r writes level[r*n ..], parent[r*n ..]. */

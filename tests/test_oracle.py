@@ -318,3 +318,52 @@ def test_stream_multi_equals_single_and_isolates_roots():
     badp[2, int(np.flatnonzero(lv[2] > 0)[0])] = -5
     rc, _, _, _ = oracle.check_bfs_pairs_multi(g.n, src, dst, roots, lv, badp)
     assert rc.tolist() == [0, 0, 5]
+
+
+def test_csr_from_rmat_par_equals_serial_and_pairs():
+    """The threaded build places entries in another order inside each row;
+    after the row sort it must give the serial CSR (itself pinned to the
+    set-based construction through csr_from_pairs) at any thread count."""
+    for scale, ef in ((9, 8), (12, 16), (15, 16)):
+        spec = inputs.rmat(scale, edgefactor=ef)
+        a = oracle.csr_from_rmat(spec)
+        src, dst = inputs.rmat_pairs(spec)
+        b = oracle.csr_from_pairs(spec.n_vertices, src, dst)
+        for nt in (1, 3, 8):
+            c = oracle.csr_from_rmat_par(spec, n_threads=nt)
+            np.testing.assert_array_equal(c.off, a.off)
+            np.testing.assert_array_equal(c.cols, a.cols)
+        np.testing.assert_array_equal(a.off, b.off)
+        np.testing.assert_array_equal(a.cols, b.cols)
+
+
+def test_bfs_partial_path_closed_form():
+    """Path 0-1-...-(n-1) from vertex 0: rows are read in queue order (degree
+    1, then 2, 2, ...); after the rows of vertices 0..k, 1 + 2k entries have
+    been read and vertices 0..k+1 carry their levels. The BFS stops at the
+    first row boundary with at least max_entries entries read."""
+    n = 41
+    _, _, g = _graph(n, _path(n))
+    for budget in range(1, 2 * n):
+        level, read = oracle.bfs_partial(g, 0, budget)
+        k = min(max(0, -(-(budget - 1) // 2)), n - 1)
+        expect_read = 1 + 2 * k if k < n - 1 else 2 * (n - 1)
+        reached = min(k + 2, n)
+        assert read == expect_read, (budget, read, expect_read)
+        assert level[:reached].tolist() == list(range(reached))
+        assert (level[reached:] == -1).all()
+
+
+def test_bfs_partial_prefix_of_full_bfs():
+    spec, g, root = _rmat_small()
+    full, _, _ = oracle.bfs(g, root, want_parent=False)
+    total = int(g.degrees()[full >= 0].sum())
+    lv, read = oracle.bfs_partial(g, root, g.nnz + 1)
+    np.testing.assert_array_equal(lv, full)
+    assert read == total
+    maxdeg = int(g.degrees().max())
+    for budget in (1, 10, 100, total // 7, total // 2, total - 1):
+        lv, read = oracle.bfs_partial(g, root, budget)
+        got = lv >= 0
+        assert np.array_equal(lv[got], full[got])
+        assert min(budget, total) <= read < budget + maxdeg
