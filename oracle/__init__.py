@@ -10,8 +10,8 @@ What it computes (see ``dobfs_oracle.c`` for the passages followed):
 * ``csr_from_pairs`` / ``csr_from_rmat`` — the undirected graph as CSR, each
   undirected edge stored as two directed edges, self-loops and duplicates
   dropped, rows sorted (Sec. 4, "Methodology").
-* ``csr_from_rmat_par`` — the same CSR built by several threads (host graphs
-  of billions of entries); equal to ``csr_from_rmat``.
+* ``csr_from_rmat_par`` / ``csr_from_pairs_par`` — the same CSRs built by
+  several threads (host graphs of billions of entries).
 * ``bfs`` — serial FIFO-queue BFS: level = hop distance (the result every
   top-down / bottom-up schedule of Algorithm 1 reaches), canonical parent =
   smallest-ID neighbour one level up.
@@ -95,6 +95,8 @@ def _load():
         lib.oracle_csr_from_rmat.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, P64, P32]
         lib.oracle_csr_from_rmat_par.restype = i64
         lib.oracle_csr_from_rmat_par.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, P64, P32, i32]
+        lib.oracle_csr_from_pairs_par.restype = i64
+        lib.oracle_csr_from_pairs_par.argtypes = [i64, i64, P32, P32, P64, P32, i32]
         lib.oracle_bfs.restype = i32
         lib.oracle_bfs.argtypes = [i64, P64, P32, i32, P32, P32]
         lib.oracle_bfs_partial.restype = i64
@@ -178,6 +180,23 @@ def csr_from_rmat_par(spec, n_threads: int | None = None) -> Csr:
     ta, tab, tabc = spec.thresholds
     nnz = lib.oracle_csr_from_rmat_par(spec.scale, m, ta, tab, tabc, spec.seed, _p(off, ctypes.c_int64),
                                        _p(cols, ctypes.c_int32), n_threads or os.cpu_count() or 1)
+    return Csr(off, cols[:nnz])
+
+
+def csr_from_pairs_par(n: int, src, dst, n_threads: int | None = None) -> Csr:
+    """The CSR of csr_from_pairs built by several threads; the column array is
+    a view of the placement buffer."""
+    lib = _load()
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = len(src)
+    off = np.zeros(n + 1, dtype=np.int64)
+    cols = np.empty(max(2 * m, 1), dtype=np.int32)
+    nnz = lib.oracle_csr_from_pairs_par(n, m, _p(src, ctypes.c_int32), _p(dst, ctypes.c_int32),
+                                        _p(off, ctypes.c_int64), _p(cols, ctypes.c_int32),
+                                        n_threads or os.cpu_count() or 1)
+    if nnz < 0:
+        raise ValueError("endpoint out of range")
     return Csr(off, cols[:nnz])
 
 

@@ -108,39 +108,56 @@ int64_t oracle_csr_from_rmat(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, 
   return sort_dedup_rows(n, off, cols);
 }
 
+/* Source of the undirected pairs of a streamed graph: regenerated R-MAT
+ * pairs (gen.h), or pairs held in two arrays. */
+typedef struct {
+  int kind; /* 0: R-MAT stream, 1: arrays */
+  int scale;
+  uint32_t t_a, t_ab, t_abc;
+  uint64_t kp, kq;
+  const int32_t* src;
+  const int32_t* dst;
+} pair_source;
+
+static inline void get_pair(const pair_source* ps, int64_t i, uint32_t* u, uint32_t* v) {
+  if (ps->kind == 0) {
+    gen_rmat_pair((uint64_t)i, ps->scale, ps->t_a, ps->t_ab, ps->t_abc, ps->kp, ps->kq, u, v);
+  } else {
+    *u = (uint32_t)ps->src[i];
+    *v = (uint32_t)ps->dst[i];
+  }
+}
+
 /*
- * The CSR of oracle_csr_from_rmat built by n_threads threads, for graphs of
- * billions of entries (R-MAT scale 28: 8.6 G entries before de-duplication).
- * Same counting placement, spread over threads: the pair stream is split
- * into ranges, each thread counts its pairs' endpoints into the row counts
- * with atomic increments; after the prefix sum each thread places its pairs
- * at atomically advanced row cursors (so the order inside a row differs from
- * the serial placement, which the row sort removes); rows are then sorted
- * and de-duplicated in parallel, and finally moved down over the removed
- * duplicates in row order. The result equals oracle_csr_from_rmat's.
+ * The CSR of oracle_csr_from_rmat / oracle_csr_from_pairs built by n_threads
+ * threads, for graphs of billions of entries (R-MAT scale 28: 8.6 G entries
+ * before de-duplication). Same counting placement, spread over threads: the
+ * pair stream is split into ranges, each thread counts its pairs' endpoints
+ * into the row counts with atomic increments; after the prefix sum each
+ * thread places its pairs at atomically advanced row cursors (so the order
+ * inside a row differs from the serial placement, which the row sort
+ * removes); rows are then sorted and de-duplicated in parallel, and finally
+ * moved down over the removed duplicates in row order. The result equals
+ * the serial builders'.
  */
-int64_t oracle_csr_from_rmat_par(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
-                                 uint64_t seed, int64_t* off, int32_t* cols, int32_t n_threads) {
-  const int64_t n = (int64_t)1 << scale;
-  const uint64_t kp = gen_key_pairs(seed), kq = gen_key_perm(seed);
-  const int nt = n_threads > 0 ? n_threads : 1;
+static int64_t csr_par_core(const pair_source* ps, int64_t n, int64_t m, int64_t* off, int32_t* cols, int nt) {
   (void)nt;
   memset(off, 0, sizeof(int64_t) * (size_t)(n + 1));
 #pragma omp parallel for schedule(static, 1 << 16) num_threads(nt)
   for (int64_t i = 0; i < m; ++i) {
     uint32_t u, v;
-    gen_rmat_pair((uint64_t)i, scale, t_a, t_ab, t_abc, kp, kq, &u, &v);
+    get_pair(ps, i, &u, &v);
     if (u == v) continue;
     __atomic_fetch_add(&off[u + 1], 1, __ATOMIC_RELAXED);
     __atomic_fetch_add(&off[v + 1], 1, __ATOMIC_RELAXED);
   }
   for (int64_t u = 0; u < n; ++u) off[u + 1] += off[u];
-  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
   memcpy(pos, off, sizeof(int64_t) * (size_t)n);
 #pragma omp parallel for schedule(static, 1 << 16) num_threads(nt)
   for (int64_t i = 0; i < m; ++i) {
     uint32_t u, v;
-    gen_rmat_pair((uint64_t)i, scale, t_a, t_ab, t_abc, kp, kq, &u, &v);
+    get_pair(ps, i, &u, &v);
     if (u == v) continue;
     cols[__atomic_fetch_add(&pos[u], 1, __ATOMIC_RELAXED)] = (int32_t)v;
     cols[__atomic_fetch_add(&pos[v], 1, __ATOMIC_RELAXED)] = (int32_t)u;
@@ -167,6 +184,24 @@ int64_t oracle_csr_from_rmat_par(int scale, int64_t m, uint32_t t_a, uint32_t t_
   off[n] = w;
   free(pos);
   return w;
+}
+
+int64_t oracle_csr_from_rmat_par(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
+                                 uint64_t seed, int64_t* off, int32_t* cols, int32_t n_threads) {
+  const pair_source ps = {0, scale, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed), NULL, NULL};
+  return csr_par_core(&ps, (int64_t)1 << scale, m, off, cols, n_threads > 0 ? n_threads : 1);
+}
+
+/* Returns -1 on an out-of-range endpoint, like oracle_csr_from_pairs. */
+int64_t oracle_csr_from_pairs_par(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* off,
+                                  int32_t* cols, int32_t n_threads) {
+  const int nt = n_threads > 0 ? n_threads : 1;
+  int64_t bad = 0;
+#pragma omp parallel for reduction(+ : bad) num_threads(nt)
+  for (int64_t i = 0; i < m; ++i) bad += (src[i] < 0 || dst[i] < 0 || src[i] >= n || dst[i] >= n) ? 1 : 0;
+  if (bad) return -1;
+  const pair_source ps = {1, 0, 0, 0, 0, 0, 0, src, dst};
+  return csr_par_core(&ps, n, m, off, cols, nt);
 }
 
 /*
@@ -346,26 +381,6 @@ int64_t oracle_teps_edges(int64_t n, const int64_t* off, const int32_t* level) {
   for (int64_t v = 0; v < n; ++v)
     if (level[v] >= 0) s += off[v + 1] - off[v];
   return s / 2;
-}
-
-/* Source of the undirected pairs of a streamed graph: regenerated R-MAT
- * pairs (gen.h), or pairs held in two arrays. */
-typedef struct {
-  int kind; /* 0: R-MAT stream, 1: arrays */
-  int scale;
-  uint32_t t_a, t_ab, t_abc;
-  uint64_t kp, kq;
-  const int32_t* src;
-  const int32_t* dst;
-} pair_source;
-
-static inline void get_pair(const pair_source* ps, int64_t i, uint32_t* u, uint32_t* v) {
-  if (ps->kind == 0) {
-    gen_rmat_pair((uint64_t)i, ps->scale, ps->t_a, ps->t_ab, ps->t_abc, ps->kp, ps->kq, u, v);
-  } else {
-    *u = (uint32_t)ps->src[i];
-    *v = (uint32_t)ps->dst[i];
-  }
 }
 
 static void note_violation(int32_t* rule_out, int64_t* bad_out, int32_t rule, int64_t where) {

@@ -335,6 +335,23 @@ def test_csr_from_rmat_par_equals_serial_and_pairs():
             np.testing.assert_array_equal(c.cols, a.cols)
         np.testing.assert_array_equal(a.off, b.off)
         np.testing.assert_array_equal(a.cols, b.cols)
+        for nt in (1, 5):
+            c = oracle.csr_from_pairs_par(spec.n_vertices, src, dst, n_threads=nt)
+            np.testing.assert_array_equal(c.off, a.off)
+            np.testing.assert_array_equal(c.cols, a.cols)
+
+
+def test_csr_from_pairs_par_set_construction_and_range():
+    rng = np.random.default_rng(11)
+    for _ in range(10):
+        n = int(rng.integers(1, 60))
+        pairs = _random_pairs(rng, n, int(rng.integers(0, 200)))
+        src, dst, g = _graph(n, pairs)
+        c = oracle.csr_from_pairs_par(n, src, dst, n_threads=4)
+        np.testing.assert_array_equal(c.off, g.off)
+        np.testing.assert_array_equal(c.cols, g.cols)
+    with pytest.raises(ValueError):
+        oracle.csr_from_pairs_par(3, [0], [3])
 
 
 def test_bfs_partial_path_closed_form():
