@@ -114,9 +114,10 @@ def _load():
                                                      P32, P8, i32, P64]
         lib.oracle_check_bfs_rmat_stream_multi.restype = i32
         lib.oracle_check_bfs_rmat_stream_multi.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, i32, P32, P32,
-                                                           P32, P32, i32, P32, P64]
+                                                           P32, P32, i32, P32, P64, i32]
         lib.oracle_check_bfs_pairs_multi.restype = i32
-        lib.oracle_check_bfs_pairs_multi.argtypes = [i64, i64, P32, P32, i32, P32, P32, P32, P32, P8, i32, P32, P64]
+        lib.oracle_check_bfs_pairs_multi.argtypes = [i64, i64, P32, P32, i32, P32, P32, P32, P32, P8, i32, P32, P64,
+                                                     i32]
         _lib = lib
     return _lib
 
@@ -282,22 +283,27 @@ def check_bfs_rmat_stream(spec, root: int, level, parent=None, want_canon: bool 
     return int(rc), int(bad.value), canon, has_nbr
 
 
-def _multi_outputs(roots, levels, parents, n, want_canon):
+def _multi_outputs(roots, levels, parents, n, want_canon, vertex_major):
     roots = np.ascontiguousarray(roots, dtype=np.int32)
     R = len(roots)
-    levels = np.ascontiguousarray(levels, dtype=np.int32).reshape(R, n)
+    shape = (n, R) if vertex_major else (R, n)
+    levels = np.ascontiguousarray(levels, dtype=np.int32).reshape(shape)
     if parents is not None:
-        parents = np.ascontiguousarray(parents, dtype=np.int32).reshape(R, n)
-    canon = np.empty((R, n), dtype=np.int32) if want_canon else None
+        parents = np.ascontiguousarray(parents, dtype=np.int32).reshape(shape)
+    canon = np.empty(shape, dtype=np.int32) if want_canon else None
     return roots, R, levels, parents, canon
 
 
-def check_bfs_rmat_stream_multi(spec, roots, levels, parents=None, want_canon=False, n_threads=None):
-    """Streaming invariant check of R BFS results [R, n] on an R-MAT workload in
-    one pass over the regenerated pairs. Returns (rules[R], bad[R], canon or None)."""
+def check_bfs_rmat_stream_multi(spec, roots, levels, parents=None, want_canon=False, n_threads=None,
+                                vertex_major=False):
+    """Streaming invariant check of R BFS results on an R-MAT workload in one
+    pass over the regenerated pairs. levels / parents are [R, n], or [n, R]
+    with vertex_major (a pair's entries for all roots side by side: far less
+    memory traffic for many roots). Returns (rules[R], bad[R], canon or None),
+    canon in the layout of levels."""
     lib = _load()
     n = spec.n_vertices
-    roots, R, levels, parents, canon = _multi_outputs(roots, levels, parents, n, want_canon)
+    roots, R, levels, parents, canon = _multi_outputs(roots, levels, parents, n, want_canon, vertex_major)
     rc = np.zeros(R, dtype=np.int32)
     bad = np.zeros(R, dtype=np.int64)
     ta, tab, tabc = spec.thresholds
@@ -305,18 +311,19 @@ def check_bfs_rmat_stream_multi(spec, roots, levels, parents=None, want_canon=Fa
         spec.scale, spec.n_pairs, ta, tab, tabc, spec.seed, R, _p(roots, ctypes.c_int32), _p(levels, ctypes.c_int32),
         _p(parents, ctypes.c_int32) if parents is not None else None,
         _p(canon, ctypes.c_int32) if want_canon else None, n_threads or os.cpu_count() or 1,
-        _p(rc, ctypes.c_int32), _p(bad, ctypes.c_int64))
+        _p(rc, ctypes.c_int32), _p(bad, ctypes.c_int64), 1 if vertex_major else 0)
     return rc, bad, canon
 
 
 def check_bfs_pairs_multi(n, src, dst, roots, levels, parents=None, want_canon=False, want_has_nbr=False,
-                          n_threads=None):
-    """Streaming invariant check of R BFS results on the graph of the pairs (src, dst).
+                          n_threads=None, vertex_major=False):
+    """Streaming invariant check of R BFS results on the graph of the pairs (src, dst)
+    (layouts as for check_bfs_rmat_stream_multi).
     Returns (rules[R], bad[R], canon or None, has_nbr or None)."""
     lib = _load()
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
-    roots, R, levels, parents, canon = _multi_outputs(roots, levels, parents, n, want_canon)
+    roots, R, levels, parents, canon = _multi_outputs(roots, levels, parents, n, want_canon, vertex_major)
     has_nbr = np.empty(n, dtype=np.uint8) if want_has_nbr else None
     rc = np.zeros(R, dtype=np.int32)
     bad = np.zeros(R, dtype=np.int64)
@@ -325,5 +332,5 @@ def check_bfs_pairs_multi(n, src, dst, roots, levels, parents=None, want_canon=F
         _p(levels, ctypes.c_int32), _p(parents, ctypes.c_int32) if parents is not None else None,
         _p(canon, ctypes.c_int32) if want_canon else None,
         _p(has_nbr, ctypes.c_uint8) if want_has_nbr else None, n_threads or os.cpu_count() or 1,
-        _p(rc, ctypes.c_int32), _p(bad, ctypes.c_int64))
+        _p(rc, ctypes.c_int32), _p(bad, ctypes.c_int64), 1 if vertex_major else 0)
     return rc, bad, canon, has_nbr

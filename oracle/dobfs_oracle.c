@@ -399,14 +399,36 @@ static void atomic_min_i32(int32_t* p, int32_t x) {
   }
 }
 
+/* The rules checked per vertex after the pass over the pairs (see below):
+ * 7, 10, 5, 9, 6 for vertex v of the root whose entries start at base (entry
+ * of v at ov = base + v*sv); 0 if all hold. */
+static int32_t vertex_rule(int64_t ov, int64_t v, int32_t root, int64_t n, const int32_t* level,
+                           const int32_t* parent, const uint8_t* up, const uint8_t* confirmed, int64_t base,
+                           int64_t sv) {
+  const int32_t lvv = level[ov];
+  if (lvv < -1) return 7;
+  if (lvv == -1) return (parent && parent[ov] != -1) ? 7 : 0;
+  if (v == root) return 0;
+  if (!up[ov]) return 10;
+  if (!parent) return 0;
+  const int32_t p = parent[ov];
+  if (p < 0 || p >= n) return 5;
+  if (!confirmed[ov]) return 9;
+  if (level[base + (int64_t)p * sv] != lvv - 1) return 6;
+  return 0;
+}
+
 /*
- * Streaming check of R BFS results (roots[r], level[r*n ..], parent[r*n ..])
- * on a graph given only by its pair stream, without building a CSR. For
+ * Streaming check of R BFS results (roots[r], level[(r, v)], parent[(r, v)])
+ * on a graph given only by its pair stream, without building a CSR. Entry
+ * (r, v) of every per-root array sits at r*n + v (root-major) or, with
+ * vertex_major, at v*R + r, so that a pair's levels for all roots are read
+ * together (the same check; the layout only changes the memory traffic). For
  * every pair u != v (stored both ways in the graph) the edge rules 3 and 4
  * of oracle_check_bfs are checked; a pair also confirms parent[v] == u (or
  * parent[u] == v) as an edge and marks a neighbour one level up. After the
  * pass every reached v != root must have a neighbour one level up (rule 10)
- * and a confirmed parent one level up, and canon[r*n + v] receives
+ * and a confirmed parent one level up, and canon[(r, v)] receives
  * min{u in N(v) : level[u] = level[v] - 1} (canon may be NULL). has_nbr (may
  * be NULL) receives 1 for every vertex with at least one neighbour.
  * rc[r] receives 0 or the rule number as above, with bad[r] the vertex;
@@ -416,7 +438,8 @@ static void atomic_min_i32(int32_t* p, int32_t x) {
  */
 static int32_t check_stream_core(const pair_source* ps, int64_t n, int64_t m, int32_t R, const int32_t* roots,
                                  const int32_t* level, const int32_t* parent, int32_t* canon, uint8_t* has_nbr,
-                                 int32_t n_threads, int32_t* rc, int64_t* bad) {
+                                 int32_t n_threads, int32_t* rc, int64_t* bad, int vertex_major) {
+  const int64_t sr = vertex_major ? 1 : n, sv = vertex_major ? R : 1;  /* (r, v) -> r*sr + v*sv */
   uint8_t* confirmed = (uint8_t*)calloc((size_t)(n * R), 1);
   uint8_t* up = (uint8_t*)calloc((size_t)(n * R), 1);
   if (canon)
@@ -424,12 +447,10 @@ static int32_t check_stream_core(const pair_source* ps, int64_t n, int64_t m, in
   if (has_nbr) memset(has_nbr, 0, (size_t)n);
   for (int32_t r = 0; r < R; ++r) {
     const int32_t root = roots[r];
-    const int32_t* lv = level + (int64_t)r * n;
-    const int32_t* pa = parent ? parent + (int64_t)r * n : NULL;
     rc[r] = 0;
     bad[r] = root;
-    if (root < 0 || root >= n || lv[root] != 0) rc[r] = 1;
-    else if (pa && pa[root] != root) rc[r] = 2;
+    if (root < 0 || root >= n || level[r * sr + root * sv] != 0) rc[r] = 1;
+    else if (parent && parent[r * sr + root * sv] != root) rc[r] = 2;
   }
 #pragma omp parallel for schedule(static, 1 << 16) num_threads(n_threads > 0 ? n_threads : 1)
   for (int64_t i = 0; i < m; ++i) {
@@ -443,8 +464,8 @@ static int32_t check_stream_core(const pair_source* ps, int64_t n, int64_t m, in
     }
     for (int32_t r = 0; r < R; ++r) {
       if (rc[r] == 1 || rc[r] == 2) continue;
-      const int64_t o = (int64_t)r * n;
-      const int32_t lu = level[o + u], lv = level[o + v];
+      const int64_t ou = r * sr + (int64_t)u * sv, ov = r * sr + (int64_t)v * sv;
+      const int32_t lu = level[ou], lv = level[ov];
       if ((lu >= 0) != (lv >= 0)) {
         note_violation(&rc[r], &bad[r], 4, lu >= 0 ? u : v);
         continue;
@@ -454,39 +475,36 @@ static int32_t check_stream_core(const pair_source* ps, int64_t n, int64_t m, in
         note_violation(&rc[r], &bad[r], 3, u);
         continue;
       }
-      if (lu == lv - 1) __atomic_store_n(&up[o + v], 1, __ATOMIC_RELAXED);
-      if (lv == lu - 1) __atomic_store_n(&up[o + u], 1, __ATOMIC_RELAXED);
+      if (lu == lv - 1) __atomic_store_n(&up[ov], 1, __ATOMIC_RELAXED);
+      if (lv == lu - 1) __atomic_store_n(&up[ou], 1, __ATOMIC_RELAXED);
       if (parent) {
-        if (parent[o + v] == u) __atomic_store_n(&confirmed[o + v], 1, __ATOMIC_RELAXED);
-        if (parent[o + u] == v) __atomic_store_n(&confirmed[o + u], 1, __ATOMIC_RELAXED);
+        if (parent[ov] == u) __atomic_store_n(&confirmed[ov], 1, __ATOMIC_RELAXED);
+        if (parent[ou] == v) __atomic_store_n(&confirmed[ou], 1, __ATOMIC_RELAXED);
       }
       if (canon) {
-        if (lu == lv - 1) atomic_min_i32(&canon[o + v], u);
-        if (lv == lu - 1) atomic_min_i32(&canon[o + u], v);
+        if (lu == lv - 1) atomic_min_i32(&canon[ov], u);
+        if (lv == lu - 1) atomic_min_i32(&canon[ou], v);
       }
     }
   }
+  /* vertex rules, in increasing v for each root (the first failure is kept);
+     the loop order follows the layout so that memory is read in order */
+  if (vertex_major) {
+    for (int64_t v = 0; v < n; ++v)
+      for (int32_t r = 0; r < R; ++r)
+        if (!rc[r] && (rc[r] = vertex_rule(r * sr + v * sv, v, roots[r], n, level, parent, up, confirmed,
+                                           r * sr, sv)))
+          bad[r] = v;
+  } else {
+    for (int32_t r = 0; r < R; ++r)
+      for (int64_t v = 0; v < n && !rc[r]; ++v)
+        if ((rc[r] = vertex_rule(r * sr + v * sv, v, roots[r], n, level, parent, up, confirmed, r * sr, sv)))
+          bad[r] = v;
+  }
   int32_t failed = 0;
   for (int32_t r = 0; r < R; ++r) {
-    const int64_t o = (int64_t)r * n;
     const int32_t root = roots[r];
-    for (int64_t v = 0; v < n && !rc[r]; ++v) {
-      const int32_t lvv = level[o + v];
-      if (lvv < -1) rc[r] = 7;
-      else if (lvv == -1) {
-        if (parent && parent[o + v] != -1) rc[r] = 7;
-      } else if (v != root) {
-        if (!up[o + v]) rc[r] = 10;
-        else if (parent) {
-          const int32_t p = parent[o + v];
-          if (p < 0 || p >= n) rc[r] = 5;
-          else if (!confirmed[o + v]) rc[r] = 9;
-          else if (level[o + p] != lvv - 1) rc[r] = 6;
-        }
-      }
-      if (rc[r]) bad[r] = v;
-    }
-    if (canon && !rc[r]) canon[o + root] = root;
+    if (canon && !rc[r]) canon[r * sr + (int64_t)root * sv] = root;
     failed += rc[r] ? 1 : 0;
   }
   free(confirmed);
@@ -501,24 +519,25 @@ int32_t oracle_check_bfs_rmat_stream(int scale, int64_t m, uint32_t t_a, uint32_
                                      int32_t n_threads, int64_t* bad) {
   const pair_source ps = {0, scale, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed), NULL, NULL};
   int32_t rc = 0;
-  check_stream_core(&ps, (int64_t)1 << scale, m, 1, &root, level, parent, canon, has_nbr, n_threads, &rc, bad);
+  check_stream_core(&ps, (int64_t)1 << scale, m, 1, &root, level, parent, canon, has_nbr, n_threads, &rc, bad, 0);
   return rc;
 }
 
-/* Streaming check of R BFS results on the R-MAT graph of gen.h. */
+/* Streaming check of R BFS results on the R-MAT graph of gen.h (vertex_major: layout of the per-root arrays). */
 int32_t oracle_check_bfs_rmat_stream_multi(int scale, int64_t m, uint32_t t_a, uint32_t t_ab, uint32_t t_abc,
                                            uint64_t seed, int32_t R, const int32_t* roots, const int32_t* level,
                                            const int32_t* parent, int32_t* canon, int32_t n_threads, int32_t* rc,
-                                           int64_t* bad) {
+                                           int64_t* bad, int32_t vertex_major) {
   const pair_source ps = {0, scale, t_a, t_ab, t_abc, gen_key_pairs(seed), gen_key_perm(seed), NULL, NULL};
-  return check_stream_core(&ps, (int64_t)1 << scale, m, R, roots, level, parent, canon, NULL, n_threads, rc, bad);
+  return check_stream_core(&ps, (int64_t)1 << scale, m, R, roots, level, parent, canon, NULL, n_threads, rc, bad,
+                           vertex_major);
 }
 
 /* Streaming check of R BFS results on the graph of m pairs held in src/dst. */
 int32_t oracle_check_bfs_pairs_multi(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int32_t R,
                                      const int32_t* roots, const int32_t* level, const int32_t* parent,
                                      int32_t* canon, uint8_t* has_nbr, int32_t n_threads, int32_t* rc,
-                                     int64_t* bad) {
+                                     int64_t* bad, int32_t vertex_major) {
   const pair_source ps = {1, 0, 0, 0, 0, 0, 0, src, dst};
-  return check_stream_core(&ps, n, m, R, roots, level, parent, canon, has_nbr, n_threads, rc, bad);
+  return check_stream_core(&ps, n, m, R, roots, level, parent, canon, has_nbr, n_threads, rc, bad, vertex_major);
 }

@@ -384,3 +384,36 @@ def test_bfs_partial_prefix_of_full_bfs():
         got = lv >= 0
         assert np.array_equal(lv[got], full[got])
         assert min(budget, total) <= read < budget + maxdeg
+
+
+def test_stream_check_vertex_major_equals_root_major():
+    """The vertex-major layout (entry (r, v) at v*R + r) changes only where
+    the per-root arrays live: the same planted mistakes give the same rule,
+    vertex and canonical parents as the root-major layout."""
+    spec, g, root = _rmat_small()
+    roots = inputs.sample_roots(91, g.n, 7, g.degrees() > 0)
+    lv, pa = oracle.bfs_many(g, roots)
+    lv, pa = lv.copy(), pa.copy()
+    deep = [int(np.flatnonzero(lv[i] > 1)[0]) for i in range(7)]
+    lv[1, deep[1]] = -1                                   # rule 4
+    pa[2, deep[2]] = -5                                   # rule 5
+    v = deep[3]                                           # rule 9: a non-neighbour one level up
+    nb = set(g.row(v).tolist())
+    pa[3, v] = next(u for u in range(g.n) if u != v and u not in nb and lv[3, u] == lv[3, v] - 1)
+    v = deep[4]                                           # rule 6: a neighbour on the same level
+    same = [u for u in g.row(v).tolist() if lv[4, u] == lv[4, v]]
+    if same:
+        pa[4, v] = same[0]
+    lv[5, int(roots[5])] = 1                              # rule 1
+    rm = oracle.check_bfs_rmat_stream_multi(spec, roots, lv, pa, want_canon=True)
+    vm = oracle.check_bfs_rmat_stream_multi(spec, roots, np.ascontiguousarray(lv.T), np.ascontiguousarray(pa.T),
+                                            want_canon=True, vertex_major=True)
+    assert rm[0].tolist()[:4] == [0, 4, 5, 9] and rm[0][5] == 1
+    np.testing.assert_array_equal(rm[0], vm[0])
+    np.testing.assert_array_equal(rm[1], vm[1])
+    np.testing.assert_array_equal(rm[2], vm[2].T)
+    src, dst = inputs.rmat_pairs(spec)
+    pm = oracle.check_bfs_pairs_multi(g.n, src, dst, roots, np.ascontiguousarray(lv.T), np.ascontiguousarray(pa.T),
+                                      want_canon=True, vertex_major=True)
+    np.testing.assert_array_equal(rm[0], pm[0])
+    np.testing.assert_array_equal(rm[2], pm[2].T)
