@@ -13,9 +13,10 @@
 //
 // The array lives on every GPU that loads this library, for the life of the
 // process (kStaticBytes, about 8.4 MB). Host code never uses the array's
-// name as a device address: on the first call on a device, with that device
-// current, cudaGetSymbolAddress yields the device address, which is cached
-// per device and passed to the kernels.
+// name as a device address: every call, with the caller's device current,
+// asks cudaGetSymbolAddress for the device address (a lookup, no
+// allocation) and passes it to the kernels, so no address outlives the
+// context it came from.
 //
 // The kernels are plain variants of the main path's: top-down expands one
 // frontier vertex per thread, bottom-up scans one vertex's full row per
@@ -41,6 +42,7 @@ struct StaticCtl {
   unsigned int conv_tail;  // bitmap -> queue conversion tail
   unsigned long long nx_n; // vertices discovered by the step
   unsigned long long nx_m; // their degree sum
+  int32_t bc_site;         // bounds-check builds: first failing check (0: none)
 };
 
 constexpr size_t kBitmapBytes = sizeof(uint32_t) * kStaticWords;
@@ -65,12 +67,22 @@ struct Scratch {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void st_enqueue(unsigned int* tail, int32_t* q, int32_t v) {
+__device__ __forceinline__ void st_enqueue(unsigned int* tail, int32_t* q, int32_t v, int64_t cap,
+                                           int32_t* bc) {
   cg::coalesced_group g = cg::coalesced_threads();
   unsigned int base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
   base = g.shfl(base, 0);
-  q[base + g.thread_rank()] = v;
+  if (bc_pos((int64_t)base + g.thread_rank(), cap, bc, kBcTdQueue)) q[base + g.thread_rank()] = v;
+}
+
+// Row bounds of u from the caller's offsets, clamped to [0, nnz] in
+// bounds-check builds.
+__device__ __forceinline__ void st_row(const int32_t* __restrict__ off, int32_t u, int64_t nnz, int32_t* bc,
+                                       int site, int64_t& s, int64_t& e) {
+  s = off[u];
+  e = off[u + 1];
+  bc_row(s, e, nnz, bc, site);
 }
 
 __global__ void k_st_clear(Scratch S, int64_t n, int64_t words, int32_t* __restrict__ level,
@@ -90,6 +102,7 @@ __global__ void k_st_clear(Scratch S, int64_t n, int64_t words, int32_t* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S.ctl->q_tail = S.ctl->conv_tail = 0;
     S.ctl->nx_n = S.ctl->nx_m = 0;
+    S.ctl->bc_site = 0;
   }
 }
 
@@ -105,23 +118,29 @@ __global__ void k_st_seed(Scratch S, int32_t root, int32_t* __restrict__ level, 
 // on the visited bitmap writes its level and parent and enqueues it.
 __global__ void __launch_bounds__(kThreads) k_st_topdown(const int32_t* __restrict__ off,
                                                          const int32_t* __restrict__ cols, Scratch S, int32_t L,
-                                                         int64_t nf, int32_t* __restrict__ level,
+                                                         int64_t nf, int64_t n, int64_t nnz,
+                                                         int32_t* __restrict__ level,
                                                          int32_t* __restrict__ parent) {
   __shared__ unsigned long long sh[kThreads / 32];
   const int32_t* cur = S.q[L & 1];
   int32_t* nxt = S.q[(L + 1) & 1];
+  int32_t* bc = &S.ctl->bc_site;
   unsigned long long m_new = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = cur[i];
-    for (int32_t j = off[u]; j < off[u + 1]; ++j) {
-      const int32_t v = cols[j];
+    const int32_t u = bc_vid(cur[i], n, bc, kBcTdFrontier);
+    int64_t s, e;
+    st_row(off, u, nnz, bc, kBcTdRow, s, e);
+    for (int64_t j = s; j < e; ++j) {
+      const int32_t v = bc_vid(cols[j], n, bc, kBcTdColumn);
       const uint32_t bit = 1u << (v & 31);
       if (__ldcg(S.visited + (v >> 5)) & bit) continue;
       if (atomicOr(S.visited + (v >> 5), bit) & bit) continue;
       level[v] = L + 1;
       if (parent) parent[v] = u;
-      m_new += (unsigned long long)(off[v + 1] - off[v]);
-      st_enqueue(&S.ctl->q_tail, nxt, v);
+      int64_t vs, ve;
+      st_row(off, v, nnz, bc, kBcTdRow, vs, ve);
+      m_new += (unsigned long long)(ve - vs);
+      st_enqueue(&S.ctl->q_tail, nxt, v, n, bc);
     }
   }
   m_new = block_sum_u64(m_new, sh);
@@ -132,11 +151,13 @@ __global__ void __launch_bounds__(kThreads) k_st_topdown(const int32_t* __restri
 // row in order and stops at the first neighbour in the frontier.
 __global__ void __launch_bounds__(kThreads) k_st_bottomup(const int32_t* __restrict__ off,
                                                           const int32_t* __restrict__ cols, Scratch S, int32_t L,
-                                                          int64_t n, int64_t words, int32_t* __restrict__ level,
+                                                          int64_t n, int64_t nnz, int64_t words,
+                                                          int32_t* __restrict__ level,
                                                           int32_t* __restrict__ parent) {
   __shared__ unsigned long long sh[kThreads / 32];
   const uint32_t* front = S.f[L & 1];
   uint32_t* next = S.f[(L + 1) & 1];
+  int32_t* bc = &S.ctl->bc_site;
   const unsigned lane = lane_id();
   unsigned long long n_new = 0, m_new = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -144,12 +165,13 @@ __global__ void __launch_bounds__(kThreads) k_st_bottomup(const int32_t* __restr
     const uint32_t vis = S.visited[w];
     const int64_t v = w * 32 + lane;
     bool found = false;
-    int32_t d = 0;
+    int64_t d = 0;
     if (v < n && !((vis >> lane) & 1u)) {
-      const int32_t s = off[v], e = off[v + 1];
+      int64_t s, e;
+      st_row(off, (int32_t)v, nnz, bc, kBcBuRow, s, e);
       d = e - s;
-      for (int32_t j = s; j < e; ++j) {
-        const int32_t u = cols[j];
+      for (int64_t j = s; j < e; ++j) {
+        const int32_t u = bc_vid(cols[j], n, bc, kBcBuColumn);
         if ((front[u >> 5] >> (u & 31)) & 1u) {
           level[v] = L + 1;
           if (parent) parent[v] = u;
@@ -174,14 +196,16 @@ __global__ void __launch_bounds__(kThreads) k_st_bottomup(const int32_t* __restr
   }
 }
 
-__global__ void k_st_queue_to_bitmap(Scratch S, int32_t L, int64_t nf, int64_t words) {
+__global__ void k_st_queue_to_bitmap(Scratch S, int32_t L, int64_t nf, int64_t n) {
   uint32_t* bm = S.f[L & 1];
   const int32_t* q = S.q[L & 1];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x)
-    atomicOr(bm + (q[i] >> 5), 1u << (q[i] & 31));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = bc_vid(q[i], n, &S.ctl->bc_site, kBcConvert);
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+  }
 }
 
-__global__ void k_st_bitmap_to_queue(Scratch S, int32_t L, int64_t words) {
+__global__ void k_st_bitmap_to_queue(Scratch S, int32_t L, int64_t n, int64_t words) {
   const uint32_t* bm = S.f[L & 1];
   int32_t* q = S.q[L & 1];
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
@@ -191,26 +215,24 @@ __global__ void k_st_bitmap_to_queue(Scratch S, int32_t L, int64_t words) {
     while (x) {
       const int b = __ffs(x) - 1;
       x &= x - 1;
-      q[pos++] = (int32_t)(w * 32 + b);
+      if (bc_pos(pos, n, &S.ctl->bc_site, kBcConvert)) q[pos] = (int32_t)(w * 32 + b);
+      ++pos;
     }
   }
 }
 
-// Device address of g_static_scratch per device, looked up once per device
-// (with that device current) on its first call.
+// Calls are serialised: they share the one array per device.
 std::mutex g_static_mu;
-void* g_static_addr[256] = {};
 
-int static_scratch(int device, Scratch* S) {
-  if (device < 0 || device >= 256) return set_error(DOBFS_ERR_INVALID, "device index out of range");
-  if (!g_static_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(DOBFS_ERR_CUDA, "cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
-    g_static_addr[device] = p;
-  }
-  unsigned char* b = static_cast<unsigned char*>(g_static_addr[device]);
+// Device address of g_static_scratch on the current device. Looked up on
+// every call (a lookup, not an allocation), so an address never outlives the
+// context it belongs to (a cudaDeviceReset between calls is harmless).
+int static_scratch(Scratch* S) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(DOBFS_ERR_CUDA, "cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
+  unsigned char* b = static_cast<unsigned char*>(p);
   S->visited = reinterpret_cast<uint32_t*>(b + kOffVisited);
   S->f[0] = reinterpret_cast<uint32_t*>(b + kOffF0);
   S->f[1] = reinterpret_cast<uint32_t*>(b + kOffF1);
@@ -238,10 +260,8 @@ extern "C" int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_i
     return set_error(DOBFS_ERR_INVALID, "dobfs_run_static: root %d out of range [0, %d)", root, n_vertices);
   cudaStream_t s = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_static_mu);
-  int dev = 0;
-  DOBFS_CUDA_TRY(cudaGetDevice(&dev));
   Scratch S;
-  DOBFS_TRY(static_scratch(dev, &S));
+  DOBFS_TRY(static_scratch(&S));
 
   const int64_t n = n_vertices;
   const int64_t words = ceil_div(n, 32);
@@ -265,20 +285,24 @@ extern "C" int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_i
       else dir = (n_f * beta < n && n_f < n_f_prev) ? 0 : 1;
     }
     if (dir == 0) {
-      if (fmt == 1) k_st_bitmap_to_queue<<<grid, kThreads, 0, s>>>(S, L, words);
-      k_st_topdown<<<grid, kThreads, 0, s>>>(row_offsets, col_indices, S, L, n_f, level_out, parent_out);
+      if (fmt == 1) k_st_bitmap_to_queue<<<grid, kThreads, 0, s>>>(S, L, n, words);
+      k_st_topdown<<<grid, kThreads, 0, s>>>(row_offsets, col_indices, S, L, n_f, n, nnz, level_out, parent_out);
     } else {
       if (fmt == 0) {
         DOBFS_CUDA_TRY(cudaMemsetAsync(S.f[L & 1], 0, sizeof(uint32_t) * (size_t)words, s));
-        k_st_queue_to_bitmap<<<grid, kThreads, 0, s>>>(S, L, n_f, words);
+        k_st_queue_to_bitmap<<<grid, kThreads, 0, s>>>(S, L, n_f, n);
       }
-      k_st_bottomup<<<grid, kThreads, 0, s>>>(row_offsets, col_indices, S, L, n, words, level_out, parent_out);
+      k_st_bottomup<<<grid, kThreads, 0, s>>>(row_offsets, col_indices, S, L, n, nnz, words, level_out,
+                                              parent_out);
     }
     DOBFS_CUDA_TRY(cudaGetLastError());
     StaticCtl c;
     DOBFS_CUDA_TRY(cudaMemcpyAsync(&c, S.ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
     DOBFS_CUDA_TRY(cudaMemsetAsync(S.ctl, 0, sizeof(StaticCtl), s));
     DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c.bc_site)
+      return set_error(DOBFS_ERR_BOUNDS, "dobfs_run_static: device bounds check failed: %s",
+                       bounds_site_name(c.bc_site));
     const int64_t n_new = (dir == 0) ? (int64_t)c.q_tail : (int64_t)c.nx_n;
     m_u -= (int64_t)c.nx_m;
     n_f_prev = n_f;

@@ -7,7 +7,7 @@ libdobfs_bc.so); started by test_gpu_bounds_check.py.
 2. A graph corrupted on purpose (a stored column set to n + 3, inside the
    allocation slack of this build) makes each path fail with
    DOBFS_ERR_BOUNDS instead of reading out of bounds, and the library stays
-   usable afterwards.
+   usable afterwards; the same for a caller's CSR given to dobfs_run_static.
 """
 import os
 import sys
@@ -122,7 +122,30 @@ def corrupted_runs():
     lv, _ = levels(g, root)
     np.testing.assert_array_equal(lv, oracle.bfs(og, root)[0])
     g.close()
+    static_corrupted(spec, og, root)
     print("corrupted runs: every path reported DOBFS_ERR_BOUNDS", flush=True)
+
+
+def static_corrupted(spec, og, root):
+    """dobfs_run_static on a caller CSR with one column set to n + 3: the
+    root's last entry (read by the top-down step of level 0), then the first
+    entry of a neighbour (read at level 1 in either direction). The output
+    buffers have 1024 entries of slack past n, so even a missed check would
+    stay inside them."""
+    n = og.n
+    off = torch.from_numpy(og.off.astype(np.int32)).cuda()
+    lv = torch.full((n + 1024,), 7, dtype=torch.int32, device="cuda")
+    pa = torch.full((n + 1024,), 7, dtype=torch.int32, device="cuda")
+    w = int(og.cols[og.off[root]])
+    for pos, what in ((int(og.off[root + 1]) - 1, "static top-down"), (int(og.off[w]), "static level 1")):
+        cols = og.cols.copy()
+        cols[pos] = n + 3
+        cd = torch.from_numpy(cols).cuda()
+        expect_bounds(lambda: (d.dobfs_run_static(off, cd, n, root, lv, pa), torch.cuda.synchronize()), what)
+    cd = torch.from_numpy(og.cols).cuda()
+    d.dobfs_run_static(off, cd, n, root, lv, pa)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lv[:n].cpu().numpy(), oracle.bfs(og, root)[0])
 
 
 def main():
