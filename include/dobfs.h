@@ -246,7 +246,17 @@ typedef struct {
   int64_t reached;          /* vertices reached */
   int64_t teps_edges;       /* undirected edges in the root's component */
   int64_t edges_examined;   /* adjacency entries read by the level kernels */
-  int64_t alg_bytes;        /* algorithmic DRAM bytes of the run (see DESIGN notes) */
+  int64_t alg_bytes;        /* algorithmic DRAM bytes of the run: the sum over levels of
+                               top-down (queue output): 20 n_f + 4 m_f + 12 n_new
+                                 (+ 4 n_f after a bitmap -> queue conversion);
+                               bottom-up: 8 n_scanned + 4 e_examined + 8 n_new
+                                 (+ 4 n_f after a queue -> bitmap conversion);
+                               top-down with bitmap output and mixed levels:
+                                 24 n_f + 4 e_examined + 8 n_scanned + 12 n_new;
+                               plus the output pass: 8 n (level and parent written)
+                                 + 4 n (map read, renumbered graphs) + 8 reached
+                                 ((level, parent) gathered). Frontier and visited
+                               bitmaps are counted as L2 traffic, not DRAM. */
 } dobfs_run_stats;
 
 /* Fills *opts with the defaults. */
@@ -298,7 +308,12 @@ int dobfs_graph_wait(dobfs_graph* g, int32_t timeout_ms);
  * td_chunk, bu_scan, schedule_seed, stream; with opts NULL, the defaults of
  * dobfs_run_opts_init except alpha = DOBFS_BATCH_ALPHA (the union frontier of
  * 64 lanes reaches a bottom-up size sooner than one lane's). stats
- * (nullable): device_ms, levels (deepest group), edges_examined.
+ * (nullable): device_ms, levels (deepest group), edges_examined, and
+ * alg_bytes: per step of a lane group of W mask words (64 W lanes), 16 W
+ * bytes per active vertex (its seen and next masks; a top-down step's
+ * frontier vertices, a bottom-up step's searched vertices) + (8 W + 4) per
+ * examined entry (the neighbour's frontier mask and the column), plus 4
+ * bytes per (vertex, root) level written by the flush.
  * Asynchronous on the batch's stream when level_out is device memory and
  * stats is NULL (device roots are first read back with a synchronous copy);
  * otherwise the call returns when the levels are written.
@@ -332,8 +347,12 @@ int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_roots, int32
  * host memory, a device staging buffer of n int32 counted against
  * max_device_bytes; queries wait (in arrival order per graph) until both are
  * available. More lane groups (up to max_groups_per_graph) are created while
- * queries wait and the budget allows; each group holds 152 bytes per vertex
- * plus records (see DESIGN notes).
+ * queries wait and the budget allows. A group of W mask words (64 W lanes)
+ * holds 8 W bytes per vertex for each of its 3 + 16 masks (lanes seen,
+ * current and next frontier, and 16 bit planes of the discovery level):
+ * 152 W bytes per vertex, i.e. 152 for 64 lanes and 304 for the default 128,
+ * plus 4 bytes per vertex for deferred rows and 8-byte top-down records (one
+ * per vertex with an edge, and one per 256 stored entries).
  */
 typedef struct dobfs_server dobfs_server;
 
@@ -438,7 +457,13 @@ int dobfs_last_trace(const dobfs_graph* g, dobfs_level_trace* out, int32_t max_l
  *
  * BFS from `root` on the caller's CSR: row_offsets[n_vertices+1] (int32) and
  * col_indices[row_offsets[n_vertices]] (int32), both device pointers, the
- * graph undirected (every edge stored both ways). level_out[n_vertices] and
+ * graph undirected (every edge stored both ways). Every row_offsets entry
+ * must lie in [0, row_offsets[n_vertices]] and be non-decreasing, and every
+ * col_indices entry in [0, n_vertices): the normal build reads and writes
+ * through these values unchecked (a column at or past n_vertices writes
+ * past level_out and the working memory); the bounds-check build
+ * libdobfs_bc.so checks each of them on the device and returns
+ * DOBFS_ERR_BOUNDS instead. level_out[n_vertices] and
  * parent_out[n_vertices] (device pointers; parent_out may be NULL) receive
  * the level (-1 if unreached) and a BFS parent (parent[root] = root).
  *
@@ -448,15 +473,18 @@ int dobfs_last_trace(const dobfs_graph* g, dobfs_level_trace* out, int32_t max_l
  * 1), a root out of range or a NULL pointer give DOBFS_ERR_INVALID before
  * any GPU work.
  *
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture. Every call on a device shares the array and
- * clears what must start at zero. The library serialises calls and each
- * call returns only when its GPU work on `stream` has finished, so calls do
- * not overlap; GPU work that overlapped with a call (for instance the same
- * array used from another thread bypassing this lock) would race on it.
- * Levels are chosen by the alpha/beta rule with the defaults of
- * dobfs_run_opts_init, one small device-to-host read per level.
+ * Every call looks up the array's device address on the current device with
+ * cudaGetSymbolAddress (a lookup, not an allocation), so a call made after
+ * cudaDeviceReset uses the new context's array. The call is synchronous:
+ * it reads two row offsets and, after every level, a few counters back to
+ * the host and synchronises `stream` each time, and returns when the BFS is
+ * done. It therefore cannot be called on a stream that is being captured
+ * into a CUDA graph. Every call on a device shares the array and clears
+ * what must start at zero. The library serialises calls, so calls through
+ * this entry point do not overlap; GPU work that overlapped with a call
+ * (for instance a second copy of this library in the process using its own
+ * lock) would race on the array. Levels are chosen by the alpha/beta rule
+ * with the defaults of dobfs_run_opts_init.
  */
 #define DOBFS_STATIC_MAX_VERTICES (1 << 20)
 int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int32_t n_vertices, int32_t root,

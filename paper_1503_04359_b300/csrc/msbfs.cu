@@ -269,6 +269,9 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   MsCtl* c = A.ctl;
   if (!c->fresh) {
+    const int64_t act = c->dir == 0 ? c->n_f : (int64_t)c->nx_act;
+    c->alg_bytes += 16 * W * act + (8 * W + 4) * (int64_t)c->nx_examined;
+    c->nx_act = 0;
     c->n_f_prev = c->n_f;
     c->n_f = (int64_t)c->nx_n;
     c->m_f = (int64_t)c->nx_m;
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
 // Folds the lanes found at vertex v into the step's counters.
 template <int W>
 struct MsCount {
-  unsigned long long n = 0, m = 0, mu = 0, ex = 0;
+  unsigned long long n = 0, m = 0, mu = 0, ex = 0, act = 0;
   unsigned long long live[W] = {};
 };
 
@@ -431,12 +434,16 @@ __device__ __forceinline__ void ms_count_flush(MsCtl* c, MsCount<W>& k, unsigned
   k.n = block_sum_u64(k.n, sh);
   k.m = block_sum_u64(k.m, sh);
   k.mu = block_sum_u64(k.mu, sh);
-  if (with_ex) k.ex = block_sum_u64(k.ex, sh);
+  if (with_ex) {
+    k.ex = block_sum_u64(k.ex, sh);
+    k.act = block_sum_u64(k.act, sh);
+  }
   if (threadIdx.x == 0) {
     if (k.n) atomicAdd(&c->nx_n, k.n);
     if (k.m) atomicAdd(&c->nx_m, k.m);
     if (k.mu) atomicAdd(&c->nx_mu, k.mu);
     if (with_ex && k.ex) atomicAdd(&c->nx_examined, k.ex);
+    if (with_ex && k.act) atomicAdd(&c->nx_act, k.act);
   }
 }
 
@@ -501,6 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
       st_lanes<W>(next, v, zero_lanes<W>());
       continue;
     }
+    k.act += 1;
     const int2 fd = A.firstdeg[v];
     Lanes<W> acc = zero_lanes<W>();
     int64_t j = 0;
@@ -1149,7 +1157,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
   g->last_trace_batch = host_loop;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
   int32_t max_levels = 0;
-  int64_t examined = 0;
+  int64_t examined = 0, alg_bytes = 0;
   for (int32_t b0 = 0; b0 < n_roots; b0 += group_lanes) {
     const int cnt = (int)std::min<int32_t>(group_lanes, n_roots - b0);
     DOBFS_TRY(ms_group_reset(m, o));
@@ -1210,6 +1218,8 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
       if (c.runaway) return set_error(DOBFS_ERR_CUDA, "internal: the batch loop ran past n iterations");
       max_levels = std::max(max_levels, c.levels_run);
       examined += c.examined;
+      // the steps' bytes, plus the flush: one 4-byte level per (vertex, lane)
+      alg_bytes += c.alg_bytes + 4 * (int64_t)cnt * g->n;
     }
   }
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t1, s));
@@ -1223,6 +1233,7 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     stats->device_ms = ms;
     stats->levels = max_levels;
     stats->edges_examined = examined;
+    stats->alg_bytes = alg_bytes;
   }
   return DOBFS_OK;
 }

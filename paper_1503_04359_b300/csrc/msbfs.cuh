@@ -45,6 +45,7 @@ struct MsCtl {
   int64_t n_f, m_f, m_u, n_f_prev;
   // accumulators of the running step
   unsigned long long nx_n, nx_m, nx_mu, nx_examined;
+  unsigned long long nx_act;   // bottom-up: vertices still missing live lanes (searched)
   unsigned long long nx_live[kMsMaxWords];
   unsigned int n_rec, n_def;
   // parameters
@@ -53,6 +54,12 @@ struct MsCtl {
   int32_t runaway;       // graph-driven loop stopped after n iterations (a fault; never expected)
   uint64_t sched_seed;
   int64_t examined;
+  // algorithmic DRAM bytes of the steps since the last reset: per step,
+  // 16 W per active vertex (its seen and next masks of W 8-byte words; a
+  // top-down step's active vertices are its frontier, a bottom-up step's the
+  // vertices it searches) + (8 W + 4) per examined entry (the neighbour's
+  // frontier mask and the column)
+  int64_t alg_bytes;
 };
 
 struct MsGroup {

@@ -117,3 +117,23 @@ def test_batch_rejects_parents_and_bad_roots(d, s14):
     with pytest.raises(d.DobfsError) as e:
         d.dobfs_run_batch(g.handle, np.array([0, g.n], dtype=np.int32), out)
     assert e.value.status == d.DOBFS_ERR_INVALID
+
+
+def test_batch_alg_bytes_closed_form(d, s14):
+    """The batch's algorithmic byte count in closed form. One root, top-down
+    only, one 64-lane mask word: every reached vertex is active once (its
+    seen and next masks, 16 bytes), every entry of its row is examined once
+    (the neighbour's mask and the column, 12 bytes), and the flush writes one
+    4-byte level per vertex: 16 reached + 12 * (sum of their degrees) + 4 n."""
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=0x2)
+    for i in range(3):
+        r = np.asarray(roots[i:i + 1], dtype=np.int32)
+        out = torch.empty((1, og.n), dtype=torch.int32, device="cuda")
+        st = d.dobfs_run_batch(g.handle, torch.from_numpy(r).cuda(), out,
+                               opts=d.make_opts(direction=d.DOBFS_DIR_TOPDOWN), want_stats=True)
+        reached = ref[i] >= 0
+        deg_sum = int(og.degrees()[reached].sum())
+        assert st.edges_examined == deg_sum
+        assert st.alg_bytes == 16 * int(reached.sum()) + 12 * deg_sum + 4 * og.n
+    g.close()
