@@ -1,28 +1,36 @@
 """Benchmark: single-source direction-optimized BFS, GTEPS on R-MAT scale 28.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--scale S] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat28|rmat22|rmat16|chunglu26]
+                    [--impl ours|reference]
 
 One step = one BFS from one seeded root on the resident graph: status init,
 the device-driven level loop (top-down / bottom-up steps and the switch),
 and the outputs (level and parent per vertex, original IDs) written to device
 buffers. GTEPS per root = undirected edges in the root's component / device
 time (CUDA events on the launching stream); the reported value is the
-harmonic mean over the K timed roots (Graph500 convention). The graph
-(~36 GB at scale 28) is far larger than L2, so no flush is needed between
+harmonic mean over the K timed roots (Graph500 convention). The scale-28
+graph (~48 GB resident) is far larger than L2, so no flush is needed between
 steps. With N > 1 (torchrun) every rank runs independent replicas on its own
 GPU: BFS from a single root does not shard without a per-level exchange, so
 the job's value is the sum of the ranks' rates measured over the max time.
 
-Also reported: the roofline of the dominant kernel (the bottom-up step,
-measured per level with CUDA events in host-driven mode on a fixed sample of
-16 roots, the same whatever --steps and --warmup are, so that an ncu capture
-of this command measures the same launches; its DRAM traffic per level is
-read from the committed ncu summary when the kernel sources still match it),
-an end-to-end number through the C ABI with host (pinned) output buffers,
-the CPU oracle on a bounded sample, SM clocks sampled during the timed
-region, and the number of kernels launched. With --tune the direction policy
-and degree-bin cutoffs are first tuned on 8 other roots (autotune.py) and
-the timed pass uses the tuned options.
+Workloads: rmat28 (default, the headline), rmat22 (int64 offsets), rmat16
+(no renumbering, int32 offsets) and chunglu26 (Chung-Lu power-law graph,
+2^26 vertices, exponent 2.1, mean degree 35); batched and served BFS are
+measured with the default workload only.
+
+Also reported: the roofline of each step kind (top-down, bottom-up, mixed;
+the dominant one in `roofline` itself), measured per level with CUDA events
+in host-driven mode on a fixed sample of 16 roots, the same whatever
+--steps and --warmup are, so that an ncu capture of this command measures
+the same launches; the DRAM traffic per bottom-up level, scaled from the
+committed ncu capture of a smaller graph when the kernel sources still
+match it; an end-to-end number through the C ABI with host (pinned) output
+buffers; the batched BFS against its algorithmic bytes; the CPU oracle on a
+bounded sample of the same workload; SM clocks sampled during the timed
+region; and the number of kernels launched. With --tune the direction
+policy and degree-bin cutoffs are first tuned on 8 other roots
+(autotune.py) and the timed pass uses the tuned options.
 """
 from __future__ import annotations
 
@@ -45,6 +53,53 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GTEPS at R-MAT scale 28; batched BFS/s and p50/p99 latency vs serial BFS"
 
+# name -> (generator, size, build flags by name, timed roots by default)
+WORKLOADS = {
+    "rmat16": ("rmat", 16, ("",), 16),
+    "rmat22": ("rmat", 22, ("REINDEX", "OFFSETS64"), 64),
+    "rmat28": ("rmat", 28, ("REINDEX",), 64),
+    "chunglu26": ("chunglu", 26, ("REINDEX",), 64),
+}
+DEFAULT_WORKLOAD = "rmat28"
+
+# the oracle's sample on graphs it cannot traverse in full on one core in the
+# time allowed: the FIFO BFS stopped after this many adjacency entries per root
+CPU_SAMPLE_ENTRIES = 1 << 29
+REF_STEP_ENTRIES = 1 << 28
+
+
+def workload_name(kind: str, size: int) -> str:
+    """The graph's identity (the same for the oracle and the library, whatever
+    the library's internal layout)."""
+    return "rmat-s%d-ef16" % size if kind == "rmat" else "chunglu-2^%d-g2.1-mean35-max2^20" % size
+
+
+def make_spec(inputs, kind: str, size: int):
+    return inputs.rmat(size) if kind == "rmat" else inputs.chunglu(size)
+
+
+def host_info() -> dict:
+    """CPU model, logical cores and memory of this host (for the CPU baseline)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    mem_gb = avail_gb = None
+    try:
+        with open("/proc/meminfo") as f:
+            kv = {l.split(":")[0]: l.split(":")[1].strip() for l in f}
+        mem_gb = int(kv["MemTotal"].split()[0]) / 1e6
+        avail_gb = int(kv["MemAvailable"].split()[0]) / 1e6
+    except (OSError, KeyError, ValueError):
+        pass
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"cpu": model, "cores": cores, "mem_gb": mem_gb, "mem_available_gb": avail_gb}
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -55,7 +110,7 @@ def _dist():
 
 KERNEL_SOURCES = ("paper_1503_04359_b300/csrc/bfs.cu", "paper_1503_04359_b300/csrc/graph.cuh",
                   "paper_1503_04359_b300/csrc/common.cuh")
-TRAFFIC_PROFILE = "profiles/bu_step_rmat_s28.md"
+TRAFFIC_PROFILE = "profiles/bu_step_rmat_s25.md"
 STEP_NAMES = {0: "top-down", 1: "bottom-up", 2: "mixed"}
 STEP_KERNELS = {0: "top-down step (k_td_bin + k_td_chunks [+ k_bu parent search])",
                 1: "bottom-up step (k_bu + k_bu_long)",
@@ -70,16 +125,18 @@ def kernel_sha256() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per bottom-up level from the committed ncu summary, if it
-    was taken on this workload with the current kernel sources; else None."""
+def profiled_traffic():
+    """The traffic record of the committed ncu summary (DRAM bytes and
+    algorithmic bytes of the bottom-up levels of a capture on a graph small
+    enough to capture with several metrics), if it was taken with the current
+    kernel sources; else None."""
     try:
         with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
             m = re.search(r"<!-- traffic (\{.*?\}) -->", f.read(), re.S)
         rec = json.loads(m.group(1))
     except Exception:
         return None
-    if rec.get("kernel_sha256") != kernel_sha256() or rec.get("workload") != workload:
+    if rec.get("kernel_sha256") != kernel_sha256():
         return None
     return rec
 
@@ -226,35 +283,106 @@ def energy_pass(torch, g, roots, level, parent, opts, teps, bus_id: str, seconds
             "source": "NVML total energy counter (read only), graph-driven runs of the timed roots"}
 
 
-def cpu_baseline(scale: int = 22, n_roots: int = 4) -> dict:
-    """The CPU oracle (serial queue BFS, 1 thread) on a bounded sample."""
+def oracle_graph(inputs, oracle, kind: str, size: int, threads: int):
+    """The workload's spec and the oracle's host CSR of it (threaded build)."""
+    spec = make_spec(inputs, kind, size)
+    if kind == "rmat":
+        return spec, oracle.csr_from_rmat_par(spec, n_threads=threads)
+    cdf = inputs.chunglu_cdf(spec)
+    src, dst = inputs.chunglu_pairs(spec, cdf)
+    g = oracle.csr_from_pairs_par(spec.n_vertices, src, dst, n_threads=threads)
+    del src, dst
+    return spec, g
+
+
+def oracle_host_gb(kind: str, size: int) -> float:
+    """Host memory the oracle's graph build and BFS need at peak (GB)."""
+    n = 1 << size
+    m = 16 * n if kind == "rmat" else int(n * 35 / 2)
+    pairs = 0 if kind == "rmat" else 8 * m
+    return (8 * m + 16 * n + 8 * n + pairs) / 1e9  # columns, offsets + cursors, level and parent
+
+
+def oracle_timing(oracle, g, roots, limit):
+    """Times the oracle's serial BFS (levels) from each root on one core:
+    the full BFS (limit None) or the FIFO BFS stopped after `limit`
+    adjacency entries. Returns (harmonic-mean GTEPS, seconds): TEPS =
+    undirected edges traversed = entries read / 2 (for a full BFS, the edges
+    of the root's component)."""
+    rates, t_sum = [], 0.0
+    for r in roots:
+        t0 = time.perf_counter()
+        if limit is None:
+            lv, _, _ = oracle.bfs(g, int(r), want_parent=False)
+            dt = time.perf_counter() - t0
+            e = oracle.teps_edges(g, lv)
+        else:
+            _, read = oracle.bfs_partial(g, int(r), limit)
+            dt = time.perf_counter() - t0
+            e = read / 2.0
+        t_sum += dt
+        rates.append(e / dt / 1e9)
+    return len(rates) / sum(1.0 / x for x in rates), t_sum, rates
+
+
+def pick_oracle_size(kind: str, size: int, avail_gb) -> int:
+    """The workload's size, or the largest smaller one of the same family whose
+    oracle graph fits in the available host memory (with 15 % to spare)."""
+    s = size
+    while avail_gb is not None and s > 10 and oracle_host_gb(kind, s) * 1.15 > avail_gb:
+        s -= 1
+    return s
+
+
+def cpu_baseline(workload: str, n_roots: int = 4, full: bool = False, all_cores: bool = False) -> dict:
+    """The CPU oracle (serial FIFO BFS, levels, 1 thread) on the bench's own
+    workload: full BFS from n_roots seeded roots where the graph is small
+    enough, else (or unless `full`) the BFS of each root stopped after
+    CPU_SAMPLE_ENTRIES adjacency entries. The oracle's graph is built by its
+    threaded builder first (not timed). With all_cores, also roots/s of full
+    BFS, one root per core on every core."""
     import dobfs_inputs as inputs
     import oracle
 
-    spec = inputs.rmat(scale)
-    g = oracle.csr_from_rmat(spec)
-    roots = inputs.sample_roots(inputs.root_seed(spec.seed), g.n, n_roots, g.degrees() > 0)
-    t_sum, rates, e_sum = 0.0, [], 0
-    for r in roots:
+    kind, size, _, _ = WORKLOADS[workload]
+    info = host_info()
+    osize = pick_oracle_size(kind, size, info["mem_available_gb"])
+    t0 = time.perf_counter()
+    spec, g = oracle_graph(inputs, oracle, kind, osize, info["cores"] or 1)
+    build_s = time.perf_counter() - t0
+    deg = g.degrees()
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), g.n, n_roots, deg > 0)
+    limit = None if (full or g.nnz <= 2 * CPU_SAMPLE_ENTRIES) else CPU_SAMPLE_ENTRIES
+    hm, t_sum, rates = oracle_timing(oracle, g, roots, limit)
+    what = ("full BFS" if limit is None else
+            "BFS stopped after %d adjacency entries (of %d stored)" % (limit, g.nnz))
+    sample = ("oracle serial FIFO BFS (levels), %d seeded roots on %s (%s; graph built by the oracle's threaded "
+              "builder in %.0f s, not timed), %s, harmonic mean" %
+              (n_roots, workload_name(kind, osize), "the bench's own graph" if osize == size else
+               "the largest of its family that fits in host memory", build_s, what))
+    out = {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample, "seconds": t_sum,
+           "per_root_gteps": rates, "oracle_build_s": build_s, "host": info,
+           "same_workload": osize == size}
+    if all_cores:
+        k = min(64, info["cores"] or 1)
+        mroots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0xA11C, g.n, k, deg > 0)
         t0 = time.perf_counter()
-        lv, _, _ = oracle.bfs(g, int(r), want_parent=True)
+        oracle.bfs_many(g, mroots, want_parent=False, n_threads=info["cores"])
         dt = time.perf_counter() - t0
-        e = oracle.teps_edges(g, lv)
-        t_sum += dt
-        e_sum += e
-        rates.append(e / dt / 1e9)
-    hm = len(rates) / sum(1.0 / x for x in rates)
-    return {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": "oracle serial FIFO BFS with canonical parents, %d seeded roots on R-MAT scale %d "
-                      "(edgefactor 16, same generator; CSR build excluded), harmonic mean" % (n_roots, scale),
-            "seconds": t_sum}
+        out["all_cores"] = {"roots": k, "threads": info["cores"], "seconds": dt, "roots_per_s": k / dt,
+                            "sample": "%d full serial BFS (levels), one per core, on %s" %
+                                      (k, workload_name(kind, osize))}
+    return out
 
 
-def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps: int = 3) -> dict:
+def measure_batch(torch, inputs, dobfs, scale: int, peak: float, sizes=(64, 256, 1024), reps: int = 3) -> dict:
     """Batched BFS (bit-parallel lane groups of 64 or 128 roots) against one-at-a-time runs on
     the same R-MAT graph: roots/s for batches of 64/256/1024 seeded roots and
     for 64 sequential single-source runs (levels only in both), with device
-    time from CUDA events. Outputs stay on the device (1024 x n int32)."""
+    time from CUDA events. Outputs stay on the device (1024 x n int32). Each
+    batch's algorithmic bytes come from an untimed run with statistics (per
+    step of a W-word lane group: 16 W per active vertex, 8 W + 4 per examined
+    entry; plus 4 per level written), its roofline from the timed runs."""
     spec = inputs.rmat(scale)
     g = dobfs.rmat_graph(spec, flags=dobfs.DOBFS_GRAPH_REINDEX)
     n = g.n
@@ -284,7 +412,7 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
     mean_teps = float(np.mean(teps))
     for b in sizes:
         rt = torch.from_numpy(np.ascontiguousarray(roots[:b])).cuda()
-        dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=bopts)
+        bst = dobfs.dobfs_run_batch(g.handle, rt, out[:b], opts=bopts, want_stats=True)
         times = []
         for _ in range(reps):
             torch.cuda.synchronize()
@@ -295,8 +423,12 @@ def measure_batch(torch, inputs, dobfs, scale: int, sizes=(64, 256, 1024), reps:
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
         rps = b / (ms * 1e-3)
+        gbs = bst.alg_bytes / (ms * 1e-3) / 1e9
         res["batches"][str(b)] = {"ms": ms, "roots_per_s": rps, "speedup_vs_sequential": rps / seq_rps,
-                                  "gteps_est": b * mean_teps / (ms * 1e-3) / 1e9}
+                                  "gteps_est": b * mean_teps / (ms * 1e-3) / 1e9,
+                                  "levels": int(bst.levels), "edges_examined": int(bst.edges_examined),
+                                  "roofline": {"bound": "hbm", "alg_bytes": int(bst.alg_bytes), "achieved": gbs,
+                                               "peak": peak, "unit": "GB/s", "frac": gbs / peak}}
     del out
     g.close()
     torch.cuda.synchronize()
@@ -404,34 +536,39 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
 
 
 def run_reference(args) -> None:
+    """The reference arm: the CPU oracle, as it stands, on the bench's
+    workload. Each step is the oracle's serial FIFO BFS (levels, one core)
+    from one seeded root: in full on graphs of at most 2 * REF_STEP_ENTRIES
+    stored entries, else stopped after REF_STEP_ENTRIES adjacency entries (a
+    bounded sample of that root's BFS; TEPS = entries read / 2 / time)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import dobfs_inputs as inputs
     import oracle
 
-    scale = min(args.scale, 22)
-    spec = inputs.rmat(scale)
-    g = oracle.csr_from_rmat(spec)
+    workload = args.workload or DEFAULT_WORKLOAD
+    kind, size, _, _ = WORKLOADS[workload]
+    info = host_info()
+    osize = pick_oracle_size(kind, size, info["mem_available_gb"])
+    t0 = time.perf_counter()
+    spec, g = oracle_graph(inputs, oracle, kind, osize, info["cores"] or 1)
+    build_s = time.perf_counter() - t0
     roots = inputs.sample_roots(inputs.root_seed(spec.seed), g.n, args.steps + args.warmup, g.degrees() > 0)
-    for r in roots[:args.warmup]:
-        oracle.bfs(g, int(r))
-    rates, t_sum = [], 0.0
-    for r in roots[args.warmup:]:
-        t0 = time.perf_counter()
-        lv, _, _ = oracle.bfs(g, int(r))
-        dt = time.perf_counter() - t0
-        t_sum += dt
-        rates.append(oracle.teps_edges(g, lv) / dt / 1e9)
-    hm = len(rates) / sum(1.0 / x for x in rates)
-    sample = ("oracle serial FIFO BFS with canonical parents on R-MAT scale %d (same generator, edgefactor 16; "
-              "CSR build excluded), one root per step" % scale)
+    limit = None if g.nnz <= 2 * REF_STEP_ENTRIES else REF_STEP_ENTRIES
+    oracle_timing(oracle, g, roots[:args.warmup], limit)
+    hm, t_sum, _ = oracle_timing(oracle, g, roots[args.warmup:], limit)
+    what = "full BFS" if limit is None else "BFS stopped after %d adjacency entries (of %d stored)" % (limit, g.nnz)
+    sample = ("oracle serial FIFO BFS (levels, one core) on %s, one seeded root per step, %s; graph built by the "
+              "oracle's threaded builder in %.0f s (not timed)" % (workload_name(kind, osize), what, build_s))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": hm, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * t_sum / max(1, len(rates)), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_sum / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "rmat-s%d-ef16" % scale, "scale": scale, "edgefactor": 16},
-        "cpu_baseline": {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(kind, osize), "scale": osize, "edgefactor": 16,
+                   "generator": kind},
+        "cpu_baseline": {"value": hm, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": info},
         "e2e": {"value": hm, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -454,10 +591,17 @@ def main() -> None:
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--scale", type=int, default=28)
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="graph to time (default rmat28, the headline)")
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale other than the named workloads'")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-reindex", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="CPU baseline: full oracle BFS from each root even on graphs where it samples")
+    ap.add_argument("--cpu-roots", type=int, default=4, help="roots of the CPU baseline")
+    ap.add_argument("--cpu-all-cores", action="store_true",
+                    help="CPU baseline: also roots/s of full BFS, one per core on every core")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--batch-scale", type=int, default=24)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-BFS measurement")
@@ -469,6 +613,13 @@ def main() -> None:
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.scale is not None and args.workload is None:
+        key = "rmat%d" % args.scale
+        if key not in WORKLOADS:
+            WORKLOADS[key] = ("rmat", args.scale, ("REINDEX",), 64)
+        args.workload = key
+    if args.workload is None:
+        args.workload = DEFAULT_WORKLOAD
 
     if args.impl == "reference":
         run_reference(args)
@@ -496,10 +647,17 @@ def main() -> None:
     dobfs.use_torch_allocator()
     dev = torch.cuda.current_device()
 
-    spec = inputs.rmat(args.scale)
-    flags = 0 if args.no_reindex else dobfs.DOBFS_GRAPH_REINDEX
+    kind, size, flag_names, _ = WORKLOADS[args.workload]
+    spec = make_spec(inputs, kind, size)
+    flags = 0
+    for nm in flag_names:
+        if nm and not (args.no_reindex and nm == "REINDEX"):
+            flags |= getattr(dobfs, "DOBFS_GRAPH_" + nm)
     t0 = time.perf_counter()
-    g = dobfs.rmat_graph(spec, flags=flags)
+    if kind == "rmat":
+        g = dobfs.rmat_graph(spec, flags=flags)
+    else:
+        g = dobfs.chunglu_graph(spec, inputs.chunglu_cdf(spec), flags=flags)
     build_s = time.perf_counter() - t0
     info = g.info
     n = int(info.n_vertices)
@@ -571,7 +729,7 @@ def main() -> None:
         job_value, job_ms = aggregate_ranks(dist, "cuda", total_ms, total_edges)
 
     peak, peak_kind = _peaks()
-    workload = "rmat-s%d-ef16%s" % (args.scale, "" if args.no_reindex else "-reindex")
+    workload = workload_name(kind, size)
     if args.jsonl:
         write_root_log(args.jsonl if rank == 0 else "%s.%d" % (args.jsonl, rank), workload, rank, roots, ms, teps,
                        levels, alg_bytes, peak, "tuned" if tuning is not None else "defaults")
@@ -592,7 +750,20 @@ def main() -> None:
     dom = max(per_kind, key=lambda k: per_kind[k][0])
     dom_ms, dom_bytes = per_kind[dom]
     achieved = (dom_bytes / n_launch[dom]) / ((dom_ms / n_launch[dom]) * 1e-3) / 1e9 if n_launch[dom] else 0.0
+    step_ms = max(1e-9, sum(v[0] for v in per_kind.values()))
+    by_step = {}
+    for k, (k_ms, k_bytes) in per_kind.items():
+        if not n_launch[k]:
+            continue
+        gbs = k_bytes / (k_ms * 1e-3) / 1e9
+        by_step[STEP_NAMES[k]] = {"levels": n_launch[k], "time_share": k_ms / step_ms,
+                                  "alg_bytes_per_level": k_bytes / n_launch[k], "achieved": gbs, "frac": gbs / peak}
     whole_gbs = (sum(alg_bytes) / (total_ms * 1e-3)) / 1e9
+    # the same whole-BFS bytes with the output pass counted as 8 bytes per reached
+    # vertex (its level and parent), without the writes of unreached vertices'
+    # -1 entries and the map reads
+    out_extra = 8 * n + (4 * n if info.reindexed else 0)
+    whole_gbs_8r = (sum(b - out_extra for b in alg_bytes) / (total_ms * 1e-3)) / 1e9
 
     energy = energy_pass(torch, g, roots, level, parent, opts, teps, gpu_bus_id(torch, dev)) if rank == 0 else None
 
@@ -614,7 +785,8 @@ def main() -> None:
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(args.workload, n_roots=args.cpu_roots, full=args.cpu_full,
+                           all_cores=args.cpu_all_cores)
 
     # the remaining measurements use their own graphs
     del level, parent, hl_lv, hl_pa
@@ -622,15 +794,19 @@ def main() -> None:
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     batch = None
-    if not args.no_batch and ws == 1:
-        batch = measure_batch(torch, inputs, dobfs, args.batch_scale)
+    default_wl = args.workload == DEFAULT_WORKLOAD
+    if not args.no_batch and ws == 1 and default_wl:
+        batch = measure_batch(torch, inputs, dobfs, args.batch_scale, peak)
     serve = None
-    if not args.no_serve and ws == 1:
+    if not args.no_serve and ws == 1 and default_wl:
         serve = measure_serve(torch, inputs, dobfs, seconds=args.serve_seconds)
 
     if rank != 0:
         return
-    prof = profiled_traffic(workload) if dom == 1 else None
+    prof = profiled_traffic() if dom == 1 else None
+    traffic = None
+    if prof:  # DRAM bytes per algorithmic byte of the captured bottom-up levels, scaled to these levels
+        traffic = prof["dram_bytes"] / prof["alg_bytes"] * (dom_bytes / n_launch[dom])
     result = {
         "metric": METRIC,
         "value": job_value,
@@ -645,8 +821,8 @@ def main() -> None:
         "dtype": "int32",
         "data": "synthetic",
         "config": {
-            "workload": workload,
-            "scale": args.scale, "edgefactor": 16, "a": spec.a, "b": spec.b, "c": spec.c, "seed": spec.seed,
+            "workload": workload, "generator": kind,
+            "scale": size, "seed": spec.seed,
             "n_vertices": n, "n_entries": int(info.n_entries), "n_nonisolated": int(info.n_nonisolated),
             "offsets_int64": int(info.offsets_int64), "reindexed": int(info.reindexed),
             "roots": len(roots), "parallelism": "replicas" if ws > 1 else "single-gpu",
@@ -660,19 +836,24 @@ def main() -> None:
                      "wall_s": wall},
         "roofline": {
             "kernel": STEP_KERNELS[dom],
-            "time_share_by_step": {STEP_NAMES[k]: per_kind[k][0] / max(1e-9, sum(v[0] for v in per_kind.values()))
-                                   for k in per_kind},
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_kind, "traffic": prof["bytes_per_level"] if prof else None,
-            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per bottom-up level (%s)"
-                               % TRAFFIC_PROFILE) if prof else None,
+            "peak_source": peak_kind, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the bottom-up levels of %s "
+                               "(%s), per algorithmic byte, times this workload's algorithmic bytes per level"
+                               % (prof["workload"], TRAFFIC_PROFILE)) if traffic is not None else None,
             "alg_bytes_per_level": (dom_bytes / n_launch[dom]) if n_launch[dom] else None,
             "levels_timed": n_launch[dom], "roots": len(roof_roots), "options": "defaults, host-driven levels",
+            "by_step": by_step,
             "whole_bfs_alg_gbs": whole_gbs, "whole_bfs_frac": whole_gbs / peak,
+            "whole_bfs_frac_out8r": whole_gbs_8r / peak,
+            "whole_bfs_note": ("whole_bfs_frac counts the output pass as 8 n (level and parent of every vertex "
+                               "written) + 4 n (map read, renumbered graphs) + 8 per reached vertex (its entry "
+                               "gathered); whole_bfs_frac_out8r counts only 8 per reached vertex"),
             "alg_bytes_per_root": float(np.mean(alg_bytes)),
         },
-        "e2e": {"value": e2e_hm, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * n,
-                "steps": len(e2e_roots), "note": "dobfs_run with pinned host outputs; root passed by value"},
+        "e2e": {"value": e2e_hm, "unit": "GTEPS", "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 8 * n,
+                "steps": len(e2e_roots),
+                "note": "dobfs_run with pinned host outputs; the step's input is the 4-byte root, passed by value"},
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
     }
@@ -681,7 +862,10 @@ def main() -> None:
     if energy is not None:
         result["energy"] = energy
     if cpu is not None:
-        result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        result["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "host",
+                                                      "same_workload", "oracle_build_s", "per_root_gteps")}
+        if "all_cores" in cpu:
+            result["cpu_baseline"]["all_cores"] = cpu["all_cores"]
     if batch is not None:
         result["batch"] = batch
     if serve is not None:

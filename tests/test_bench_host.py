@@ -50,18 +50,48 @@ def test_aggregate_ranks_gloo_two_processes():
         assert value == pytest.approx(4e9 / 0.020 / 1e9)
 
 
-def test_profiled_traffic_needs_matching_sources_and_workload(tmp_path, monkeypatch):
+def test_profiled_traffic_needs_matching_sources(tmp_path, monkeypatch):
     prof = tmp_path / "p.md"
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
-    rec = {"kernel_sha256": bench.kernel_sha256(), "workload": "rmat-s28-ef16-reindex", "bytes_per_level": 123}
+    rec = {"kernel_sha256": bench.kernel_sha256(), "workload": "rmat-s24-ef16", "dram_bytes": 150, "alg_bytes": 100}
     prof.write_text("summary\n<!-- traffic %s -->\n" % json.dumps(rec))
-    assert bench.profiled_traffic("rmat-s28-ef16-reindex")["bytes_per_level"] == 123
-    assert bench.profiled_traffic("rmat-s24-ef16-reindex") is None
+    got = bench.profiled_traffic()
+    assert got["dram_bytes"] / got["alg_bytes"] == 1.5 and got["workload"] == "rmat-s24-ef16"
     rec["kernel_sha256"] = "0" * 64
     prof.write_text("<!-- traffic %s -->" % json.dumps(rec))
-    assert bench.profiled_traffic("rmat-s28-ef16-reindex") is None
+    assert bench.profiled_traffic() is None
     prof.write_text("no record")
-    assert bench.profiled_traffic("rmat-s28-ef16-reindex") is None
+    assert bench.profiled_traffic() is None
+
+
+def test_workload_names_and_oracle_memory():
+    assert bench.workload_name("rmat", 28) == "rmat-s28-ef16"
+    assert bench.workload_name("chunglu", 26).startswith("chunglu-2^26")
+    # scale 28: 4.3 G pairs -> 34.4 GB of columns before de-duplication, plus offsets, cursors, outputs
+    assert 38 < bench.oracle_host_gb("rmat", 28) < 42
+    assert bench.pick_oracle_size("rmat", 28, None) == 28
+    assert bench.pick_oracle_size("rmat", 28, 1000.0) == 28
+    assert bench.pick_oracle_size("rmat", 28, 30.0) == 27
+    assert set(bench.WORKLOADS) >= {"rmat16", "rmat22", "rmat28", "chunglu26"}
+
+
+def test_cpu_baseline_small_workload(monkeypatch):
+    """The oracle leg on a small R-MAT workload: full BFS (the graph is below
+    the sampling threshold), 2 roots, host description recorded."""
+    monkeypatch.setitem(bench.WORKLOADS, "rmat12", ("rmat", 12, ("REINDEX",), 8))
+    out = bench.cpu_baseline("rmat12", n_roots=2, all_cores=True)
+    assert out["value"] > 0 and out["cores"] == 1 and out["same_workload"]
+    assert "rmat-s12-ef16" in out["sample"] and "full BFS" in out["sample"]
+    assert out["host"]["cores"] >= 1 and out["all_cores"]["roots"] >= 1
+
+
+def test_cpu_baseline_samples_large_graphs(monkeypatch):
+    """Above 2 * CPU_SAMPLE_ENTRIES stored entries the oracle's BFS is stopped
+    after CPU_SAMPLE_ENTRIES entries per root."""
+    monkeypatch.setattr(bench, "CPU_SAMPLE_ENTRIES", 1 << 12)
+    monkeypatch.setitem(bench.WORKLOADS, "rmat12", ("rmat", 12, ("REINDEX",), 8))
+    out = bench.cpu_baseline("rmat12", n_roots=2)
+    assert "stopped after 4096 adjacency entries" in out["sample"]
 
 
 def test_ncu_summary_groups_bottom_up_levels(tmp_path):
