@@ -152,6 +152,61 @@ def aggregate_ranks(dist, device, total_ms: float, total_edges: float) -> tuple[
     return sum(float(x[1]) for x in allt) / (mx * 1e-3) / 1e9, mx
 
 
+def combine_batch(per_rank: list) -> dict:
+    """Batched-BFS results of independent replicas (one per rank, each on its
+    own GPU and graph copy): every batch size's roots over all ranks divided
+    by the slowest rank's time; the rest from rank 0."""
+    out = json.loads(json.dumps(per_rank[0]))
+    ws = len(per_rank)
+    seq_ms = max(r["sequential"]["ms"] for r in per_rank)
+    out["sequential"]["ms"] = seq_ms
+    out["sequential"]["roots"] = sum(r["sequential"]["roots"] for r in per_rank)
+    out["sequential"]["roots_per_s"] = out["sequential"]["roots"] / (seq_ms * 1e-3)
+    for b, x in out["batches"].items():
+        ms = max(r["batches"][b]["ms"] for r in per_rank)
+        x["ms"] = ms
+        x["roots_per_s"] = ws * int(b) / (ms * 1e-3)
+        x["speedup_vs_sequential"] = x["roots_per_s"] / out["sequential"]["roots_per_s"]
+        x["gteps_est"] = sum(r["batches"][b]["gteps_est"] * r["batches"][b]["ms"] for r in per_rank) / ms
+        rf = x.get("roofline")
+        if rf:
+            rf["alg_bytes"] = sum(r["batches"][b]["roofline"]["alg_bytes"] for r in per_rank)
+            rf["achieved"] = rf["alg_bytes"] / (ms * 1e-3) / 1e9
+            rf["peak"] = rf["peak"] * ws
+            rf["frac"] = rf["achieved"] / rf["peak"]
+    out["replicas"] = ws
+    return out
+
+
+def combine_serve(per_rank: list) -> dict:
+    """Serving results of independent replicas (each rank serves its own
+    Poisson stream on its own GPU): queries over all ranks divided by the
+    longest span, latency percentiles over every rank's queries."""
+    out = json.loads(json.dumps({k: v for k, v in per_rank[0].items() if k != "rates"}))
+    out["rates"] = {}
+    ws = len(per_rank)
+    base_qps = sum(r["one_at_a_time"]["qps"] for r in per_rank)
+    out["one_at_a_time"]["qps"] = base_qps
+    for rate in per_rank[0]["rates"]:
+        rs = [r["rates"][rate] for r in per_rank]
+        lat = np.concatenate([np.asarray(x["_latencies_ms"]) for x in rs])
+        q = sum(x["queries"] for x in rs)
+        span = max(x["span_s"] for x in rs)
+        out["rates"][rate] = {"queries": q, "offered_qps_per_replica": int(rate),
+                              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                              "mean_ms": float(lat.mean()), "achieved_qps": q / span, "span_s": span,
+                              "vs_one_at_a_time": (q / span) / base_qps, "server": rs[0]["server"]}
+    out["replicas"] = ws
+    return out
+
+
+def strip_private(res):
+    """Drops the per-query latency lists (kept only for combining ranks)."""
+    if isinstance(res, dict):
+        return {k: strip_private(v) for k, v in res.items() if not k.startswith("_")}
+    return res
+
+
 def gpu_bus_id(torch, dev: int) -> str:
     """PCI bus id of CUDA device `dev` (as nvidia-smi and NVML name it), so the
     samplers read the GPU this process runs on whatever the visible-device mapping."""
@@ -375,7 +430,8 @@ def cpu_baseline(workload: str, n_roots: int = 4, full: bool = False, all_cores:
     return out
 
 
-def measure_batch(torch, inputs, dobfs, scale: int, peak: float, sizes=(64, 256, 1024), reps: int = 3) -> dict:
+def measure_batch(torch, inputs, dobfs, scale: int, peak: float, sizes=(64, 256, 1024), reps: int = 3,
+                  rank: int = 0) -> dict:
     """Batched BFS (bit-parallel lane groups of 64 or 128 roots) against one-at-a-time runs on
     the same R-MAT graph: roots/s for batches of 64/256/1024 seeded roots and
     for 64 sequential single-source runs (levels only in both), with device
@@ -387,7 +443,7 @@ def measure_batch(torch, inputs, dobfs, scale: int, peak: float, sizes=(64, 256,
     g = dobfs.rmat_graph(spec, flags=dobfs.DOBFS_GRAPH_REINDEX)
     n = g.n
     deg = g.degrees()
-    roots = inputs.sample_roots(inputs.root_seed(spec.seed) ^ 0xBA7C, n, max(sizes), deg > 0)
+    roots = inputs.sample_roots((inputs.root_seed(spec.seed) ^ 0xBA7C) + rank * 0x1000, n, max(sizes), deg > 0)
     stream = torch.cuda.current_stream()
     opts = dobfs.make_opts(stream=stream)  # single-source defaults
     bopts = dobfs.make_opts(stream=stream, alpha=dobfs.DOBFS_BATCH_ALPHA)  # the batch default
@@ -438,7 +494,7 @@ def measure_batch(torch, inputs, dobfs, scale: int, peak: float, sizes=(64, 256,
 
 def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000, 5000, 10000, 20000, 50000),
                   seconds: float = 2.0, max_queries: int = 20000, out_gb: float = 120.0, min_slots: int = 256,
-                  serve_opts=None) -> dict:
+                  serve_opts=None, rank: int = 0) -> dict:
     """Open-loop serving: R-MAT graphs of the given scales resident, Poisson
     arrivals (seeded exponential gaps) at each rate, graph ids uniform, roots
     uniform over degree >= 1 vertices. Latency runs from the scheduled arrival
@@ -475,7 +531,7 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
         for rate in rates:
             st0 = dobfs.dobfs_serve_get_stats(srv)
             n_q = int(max(200, min(max_queries, rate * seconds)))
-            rng = np.random.default_rng(0xA11CE + rate)
+            rng = np.random.default_rng(0xA11CE + rate + 7919 * rank)
             gaps = rng.exponential(1.0 / rate, n_q)
             which = rng.integers(0, len(graphs), n_q)
             ridx = rng.integers(0, 1024, n_q)
@@ -512,8 +568,9 @@ def measure_serve(torch, inputs, dobfs, scales=(18, 20, 22, 24, 26), rates=(2000
             span = (last_done - int(sched[0])) * 1e-9
             res["rates"][str(rate)] = {"queries": n_q, "p50_ms": float(np.percentile(lat, 50)),
                                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                                       "achieved_qps": n_q / span,
-                                       "vs_one_at_a_time": (n_q / span) / one_at_a_time_qps}
+                                       "achieved_qps": n_q / span, "span_s": span,
+                                       "vs_one_at_a_time": (n_q / span) / one_at_a_time_qps,
+                                       "_latencies_ms": lat.tolist()}
             st1 = dobfs.dobfs_serve_get_stats(srv)
             coh = st1.cohorts - st0.cohorts
             res["rates"][str(rate)]["server"] = {
@@ -795,11 +852,23 @@ def main() -> None:
     torch.cuda.empty_cache()
     batch = None
     default_wl = args.workload == DEFAULT_WORKLOAD
-    if not args.no_batch and ws == 1 and default_wl:
-        batch = measure_batch(torch, inputs, dobfs, args.batch_scale, peak)
+    # batched and served BFS shard as replicas: every rank runs its own on its
+    # own GPU and graph copy; rank 0 combines (roots and queries over all ranks,
+    # the slowest rank's time)
+    if not args.no_batch and default_wl:
+        batch = measure_batch(torch, inputs, dobfs, args.batch_scale, peak, rank=rank)
+        if dist:
+            allb = [None] * ws
+            dist.all_gather_object(allb, batch)
+            batch = combine_batch(allb)
     serve = None
-    if not args.no_serve and ws == 1 and default_wl:
-        serve = measure_serve(torch, inputs, dobfs, seconds=args.serve_seconds)
+    if not args.no_serve and default_wl:
+        serve = measure_serve(torch, inputs, dobfs, seconds=args.serve_seconds, rank=rank)
+        if dist:
+            alls = [None] * ws
+            dist.all_gather_object(alls, serve)
+            serve = combine_serve(alls)
+        serve = strip_private(serve)
 
     if rank != 0:
         return

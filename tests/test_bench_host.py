@@ -129,3 +129,59 @@ def test_per_root_jsonl(tmp_path):
     assert rows[0]["alg_gbs"] == pytest.approx(3200.0)
     assert rows[0]["roofline_frac"] == pytest.approx(0.5)
     assert all(r["workload"] == "rmat-s10-ef16-reindex" and r["options"] == "defaults" for r in rows)
+
+
+def _fake_batch(rank):
+    ms = 10.0 * (rank + 1)  # rank 1 is the slowest
+    return {"workload": "rmat-s24-ef16", "sequential": {"roots": 64, "ms": 20.0 + rank, "roots_per_s": 0.0,
+                                                        "gteps": 1.0},
+            "batches": {"64": {"ms": ms, "roots_per_s": 0.0, "speedup_vs_sequential": 0.0, "gteps_est": 100.0,
+                               "roofline": {"bound": "hbm", "alg_bytes": 1e9, "achieved": 0.0, "peak": 6000.0,
+                                            "unit": "GB/s", "frac": 0.0}}}}
+
+
+def _fake_serve(rank):
+    lat = [1.0 + rank, 2.0 + rank, 3.0 + rank]
+    return {"workload": "x", "one_at_a_time": {"qps": 1000.0, "mean_device_ms_per_graph": [1.0]},
+            "rates": {"2000": {"queries": 3, "span_s": 0.5 + rank, "achieved_qps": 0.0, "p50_ms": 0.0,
+                               "p99_ms": 0.0, "mean_ms": 0.0, "vs_one_at_a_time": 0.0, "server": {"cohorts": 1},
+                               "_latencies_ms": lat}}}
+
+
+def _legs_worker(rank, ws, port, q):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=ws)
+    allb, alls = [None] * ws, [None] * ws
+    dist.all_gather_object(allb, _fake_batch(rank))
+    dist.all_gather_object(alls, _fake_serve(rank))
+    q.put((rank, bench.combine_batch(allb), bench.strip_private(bench.combine_serve(alls))))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batch_and_serve_legs_combine_over_two_gloo_ranks():
+    """Batched and served BFS run as replicas: roots and queries of all ranks
+    over the slowest rank's time, latency percentiles over all queries."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_legs_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict((r, (b, s)) for r, b, s in (q.get(timeout=120) for _ in procs))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(2):
+        b, s = got[r]
+        x = b["batches"]["64"]
+        assert x["ms"] == 20.0 and x["roots_per_s"] == pytest.approx(128 / 0.020)
+        assert b["sequential"]["roots"] == 128 and b["sequential"]["ms"] == 21.0
+        assert x["speedup_vs_sequential"] == pytest.approx((128 / 0.020) / (128 / 0.021))
+        assert x["roofline"]["alg_bytes"] == 2e9 and x["roofline"]["peak"] == 12000.0
+        assert x["roofline"]["frac"] == pytest.approx(2e9 / 0.020 / 1e9 / 12000.0)
+        y = s["rates"]["2000"]
+        assert y["queries"] == 6 and y["achieved_qps"] == pytest.approx(6 / 1.5)
+        assert y["p50_ms"] == pytest.approx(2.5) and "_latencies_ms" not in y
+        assert s["one_at_a_time"]["qps"] == 2000.0 and s["replicas"] == 2
