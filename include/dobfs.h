@@ -236,6 +236,11 @@ typedef struct {
                                searches the vertices of degree >= td_split_pct/100 * nnz / m_f
                                bottom-up and expands only the rest of each frontier row top-down
                                (0: off; 0..100000; default 150) */
+  /* Threads per block of the step kernels (0: the default 256; else 128,
+     256 or 512). Like the cutoffs they change only the speed. */
+  int32_t bu_threads;       /* bottom-up search (single-source and batched runs) */
+  int32_t td_threads;       /* top-down expansion (single-source and batched runs) */
+  int32_t out_threads;      /* output pass (single-source runs) */
 } dobfs_run_opts;
 
 typedef struct {

@@ -14,7 +14,9 @@ and the faster one is kept:
               (knobs: static_pct, bu_steps, td_bitmap_div, td_split_pct).
 
 Both also tune the degree-bin cutoffs of the step kernels (td_small_max,
-td_chunk, bu_scan); batched runs tune alpha, beta, td_chunk and bu_scan.
+td_chunk, bu_scan) and the threads per block of the bottom-up, top-down and
+output kernels (bu_threads, td_threads, out_threads); batched runs tune
+alpha, beta, td_chunk, bu_scan, bu_threads and td_threads.
 The search is coordinate descent over small grids (each knob in turn, the
 best value kept, until a sweep changes nothing). A result can be cached in a
 JSON file under a key describing the graph.
@@ -39,8 +41,13 @@ CUTOFF_GRID = {
     "td_small_max": [8, 16, 32, 64],
     "td_chunk": [256, 512, 1024, 2048],
     "bu_scan": [8, 16, 32, 64],
+    # threads per block of the bottom-up, top-down and output kernels
+    "bu_threads": [128, 256, 512],
+    "td_threads": [128, 256, 512],
+    "out_threads": [128, 256, 512],
 }
-CUTOFF_DEFAULTS = {"td_small_max": 16, "td_chunk": 512, "bu_scan": 32}
+CUTOFF_DEFAULTS = {"td_small_max": 16, "td_chunk": 512, "bu_scan": 32, "bu_threads": 256, "td_threads": 256,
+                   "out_threads": 256}
 ALPHA_BETA_GRID = {
     "alpha": [4, 8, 14, 24, 48],
     "beta": [8, 16, 24, 48, 96],
@@ -56,8 +63,8 @@ STATIC_GRID = {
     **CUTOFF_GRID,
 }
 BATCH_GRID = {"alpha": [2, 4, 8, 14, 32], "beta": [8, 24, 64], "td_chunk": [256, 512, 1024, 2048, 4096],
-              "bu_scan": [8, 16, 32, 64, 128]}
-BATCH_DEFAULTS = {"td_chunk": 1024, "bu_scan": 32}
+              "bu_scan": [8, 16, 32, 64, 128], "bu_threads": [128, 256, 512], "td_threads": [128, 256, 512]}
+BATCH_DEFAULTS = {"td_chunk": 1024, "bu_scan": 32, "bu_threads": 256, "td_threads": 256}
 
 
 def graph_key(g: dobfs.Graph, kind: str) -> str:

@@ -57,6 +57,9 @@ constexpr int kTdClaimPer = 8;   // top-down chunk entries claimed per lane per 
 constexpr int kTdSmallMin = 8;   // smallest allowed cutoffs (they size the record buffer)
 constexpr int kChunkMin = 256;
 constexpr int kCases = 6;      // step kinds of the level loop's switch node
+// Threads per block of the step kernels a run may choose (block sizes change
+// only the speed, never the result): 128, 256 (default) or 512.
+__host__ __device__ constexpr int bu_min_blocks(int t) { return t <= 128 ? 10 : (t <= 256 ? 5 : 2); }
 constexpr int kCaseNone = 7;   // switch value with no body: loop ends
 
 template <class OffT>
@@ -329,9 +332,9 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
 
 // Top-down, part 1: short rows expanded in place, long rows cut into
 // chunk records.
-template <class OffT, bool BM>
-__global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
-  __shared__ unsigned long long sh[kThreads / 32];
+template <class OffT, bool BM, int NT>
+__global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[NT / 32];
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nf = c->n_f;
@@ -402,9 +405,9 @@ __global__ void __launch_bounds__(kThreads) k_td_bin(BfsArgs<OffT> A) {
 }
 
 // Top-down, part 2: one warp per chunk record, 16-byte column loads.
-template <class OffT, bool BM>
-__global__ void __launch_bounds__(kThreads) k_td_chunks(BfsArgs<OffT> A) {
-  __shared__ unsigned long long sh[kThreads / 32];
+template <class OffT, bool BM, int NT>
+__global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[NT / 32];
   const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
@@ -539,11 +542,11 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // rows without a hit go to the deferred list. Found vertices are collected
 // per word in shared memory and every lane writes its own next-frontier and
 // visited word: no global atomics.
-template <class OffT, bool RECOVER>
-__global__ void __launch_bounds__(kThreads, 5) k_bu(BfsArgs<OffT> A) {
-  __shared__ unsigned long long sh[kThreads / 32];
-  __shared__ uint32_t s_found[kThreads / 32][32];
-  __shared__ uint16_t s_cand[kThreads / 32][1024];
+template <class OffT, bool RECOVER, int NT>
+__global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
+  __shared__ unsigned long long sh[NT / 32];
+  __shared__ uint32_t s_found[NT / 32][32];
+  __shared__ uint16_t s_cand[NT / 32][1024];
   __shared__ int64_t s_tab[2 * kSmallDeg];
   if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
   __syncthreads();
@@ -767,8 +770,8 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
 // output stores). Vertices renumbered past the last one with an edge are
 // isolated: unreached unless they are the root, so only the root among them
 // needs the visited bit and the (level, parent) gather.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
+template <class OffT, int NT>
+__global__ void __launch_bounds__(NT) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
                                                      int32_t root_orig, int32_t* __restrict__ level_out,
                                                      int32_t* __restrict__ parent_out) {
   constexpr int kQ = 2;  // quads per thread and step: eight independent gathers in flight
@@ -940,43 +943,55 @@ struct Grids {
 // One full wave of resident blocks per kernel: the grid-stride loops then
 // run every block to the end of the work without a second, partial wave.
 template <class K>
-int resident_grid(K kernel) {
+int resident_grid(K kernel, int threads) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 4;
   }
-  fit_carveout(kernel, kThreads, per_sm);
+  fit_carveout(kernel, threads, per_sm);
   return grid_cap(per_sm);
 }
 
-template <class OffT>
+// Block sizes of the step kernels: bottom-up search (bu), top-down binning
+// and chunks (td).
+struct BlockCfg {
+  int bu = kThreads, td = kThreads;
+};
+BlockCfg block_cfg(const dobfs_run_opts& o) {
+  BlockCfg b;
+  if (o.bu_threads) b.bu = o.bu_threads;
+  if (o.td_threads) b.td = o.td_threads;
+  return b;
+}
+
+template <class OffT, int TB, int TT>
 Grids grids() {
   static Grids G = {0, 0, 0, 0, 0};
   if (G.bu == 0) {
-    G.td_bin = resident_grid(k_td_bin<OffT, false>);
-    G.td_chunks = resident_grid(k_td_chunks<OffT, false>);
-    G.conv = resident_grid(k_bitmap_to_queue<OffT>);
-    G.bu = resident_grid(k_bu<OffT, false>);
-    G.bu_long = resident_grid(k_bu_long<OffT>);
+    G.td_bin = resident_grid(k_td_bin<OffT, false, TT>, TT);
+    G.td_chunks = resident_grid(k_td_chunks<OffT, false, TT>, TT);
+    G.conv = resident_grid(k_bitmap_to_queue<OffT>, kThreads);
+    G.bu = resident_grid(k_bu<OffT, false, TB>, TB);
+    G.bu_long = resident_grid(k_bu_long<OffT>, kThreads);
   }
   return G;
 }
 
 // Enqueues the kernels of step kind `kase` on s (used both for graph capture
 // and for host-driven levels).
-template <class OffT>
-int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t main_begin,
-                cudaEvent_t main_end) {
-  const Grids G = grids<OffT>();
+template <class OffT, int TB, int TT>
+int launch_case_t(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t main_begin,
+                  cudaEvent_t main_end) {
+  const Grids G = grids<OffT, TB, TT>();
   const size_t bm_bytes = sizeof(uint32_t) * (size_t)g->words;
   switch (kase) {
     case 0:
     case 2:
       if (kase == 2) k_bitmap_to_queue<OffT><<<G.conv, kThreads, 0, s>>>(A);
       if (main_begin) cudaEventRecord(main_begin, s);
-      k_td_bin<OffT, false><<<G.td_bin, kThreads, 0, s>>>(A);
-      k_td_chunks<OffT, false><<<G.td_chunks, kThreads, 0, s>>>(A);
+      k_td_bin<OffT, false, TT><<<G.td_bin, TT, 0, s>>>(A);
+      k_td_chunks<OffT, false, TT><<<G.td_chunks, TT, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
       break;
     case 1:
@@ -987,7 +1002,7 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
         k_queue_to_bitmap<OffT><<<G.conv, kThreads, 0, s>>>(A);
       }
       if (main_begin) cudaEventRecord(main_begin, s);
-      k_bu<OffT, false><<<G.bu, kThreads, 0, s>>>(A);
+      k_bu<OffT, false, TB><<<G.bu, TB, 0, s>>>(A);
       k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
       break;
@@ -1002,10 +1017,10 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
         k_clear_next<OffT><<<G.conv, kThreads, 0, s>>>(A);
       }
       if (main_begin) cudaEventRecord(main_begin, s);
-      k_td_bin<OffT, true><<<G.td_bin, kThreads, 0, s>>>(A);
-      k_td_chunks<OffT, true><<<G.td_chunks, kThreads, 0, s>>>(A);
-      k_bu<OffT, false><<<G.bu, kThreads, 0, s>>>(A);  // the bottom-up part of a mixed level
-      k_bu<OffT, true><<<G.bu, kThreads, 0, s>>>(A);
+      k_td_bin<OffT, true, TT><<<G.td_bin, TT, 0, s>>>(A);
+      k_td_chunks<OffT, true, TT><<<G.td_chunks, TT, 0, s>>>(A);
+      k_bu<OffT, false, TB><<<G.bu, TB, 0, s>>>(A);  // the bottom-up part of a mixed level
+      k_bu<OffT, true, TB><<<G.bu, TB, 0, s>>>(A);
       k_bu_long<OffT><<<G.bu_long, kThreads, 0, s>>>(A);
       if (main_end) cudaEventRecord(main_end, s);
       break;
@@ -1016,8 +1031,46 @@ int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s
   return DOBFS_OK;
 }
 
+template <class OffT, int TB>
+int launch_case_td(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t mb, cudaEvent_t me,
+                   int td) {
+  switch (td) {
+    case 128: return launch_case_t<OffT, TB, 128>(g, A, kase, s, mb, me);
+    case 512: return launch_case_t<OffT, TB, 512>(g, A, kase, s, mb, me);
+    default: return launch_case_t<OffT, TB, 256>(g, A, kase, s, mb, me);
+  }
+}
+
 template <class OffT>
-int build_level_graph(dobfs_graph* g) {
+int launch_case(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t mb, cudaEvent_t me,
+                BlockCfg b) {
+  switch (b.bu) {
+    case 128: return launch_case_td<OffT, 128>(g, A, kase, s, mb, me, b.td);
+    case 512: return launch_case_td<OffT, 512>(g, A, kase, s, mb, me, b.td);
+    default: return launch_case_td<OffT, 256>(g, A, kase, s, mb, me, b.td);
+  }
+}
+
+// The output pass with T threads per block.
+template <class OffT, int T>
+void launch_output_t(dobfs_graph* g, const BfsArgs<OffT>& A, const int32_t* n2o, int32_t root, int32_t* lv,
+                     int32_t* pa, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>(ceil_div(ceil_div(g->n, 4), T), (int64_t)grid_cap(16 * kThreads / T));
+  k_output<OffT, T><<<grid, T, 0, s>>>(A, n2o, root, lv, pa);
+}
+
+template <class OffT>
+void launch_output(dobfs_graph* g, const BfsArgs<OffT>& A, const int32_t* n2o, int32_t root, int32_t* lv,
+                   int32_t* pa, cudaStream_t s, int threads) {
+  switch (threads) {
+    case 128: launch_output_t<OffT, 128>(g, A, n2o, root, lv, pa, s); break;
+    case 512: launch_output_t<OffT, 512>(g, A, n2o, root, lv, pa, s); break;
+    default: launch_output_t<OffT, 256>(g, A, n2o, root, lv, pa, s); break;
+  }
+}
+
+template <class OffT>
+int build_level_graph(dobfs_graph* g, BlockCfg b) {
   const BfsArgs<OffT> A = make_args<OffT>(g);
   cudaStream_t cs = nullptr;
   DOBFS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1067,7 +1120,7 @@ int build_level_graph(dobfs_graph* g) {
     if (cudaStreamBeginCaptureToGraph(cs, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return fail(set_error(DOBFS_ERR_CUDA, "capture to case %d failed", k));
-    int rc = launch_case<OffT>(g, A, k, cs, nullptr, nullptr);
+    int rc = launch_case<OffT>(g, A, k, cs, nullptr, nullptr, b);
     cudaGraph_t cap = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &cap);
     if (rc != DOBFS_OK) return fail(rc);
@@ -1076,13 +1129,15 @@ int build_level_graph(dobfs_graph* g) {
   cudaError_t e = cudaGraphInstantiate(&g->cg_exec, g->cg, 0);
   if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)));
   cudaStreamDestroy(cs);
+  g->cg_bu = b.bu;
+  g->cg_td = b.td;
   return DOBFS_OK;
 }
 
 // Host-driven levels: same kernels, one round trip per level, every level's
 // kernels timed with events (diagnostics).
 template <class OffT>
-int host_loop(dobfs_graph* g, const BfsArgs<OffT>& A, cudaStream_t s) {
+int host_loop(dobfs_graph* g, const BfsArgs<OffT>& A, cudaStream_t s, BlockCfg b) {
   g->host_level_ms.clear();
   g->host_level_main_ms.clear();
   cudaEvent_t e0, e1, m0, m1;
@@ -1102,7 +1157,7 @@ int host_loop(dobfs_graph* g, const BfsArgs<OffT>& A, cudaStream_t s) {
     const int done = hdr[5], kase = hdr[3];
     if (done) break;
     cudaEventRecord(e0, s);
-    rc = launch_case<OffT>(g, A, kase, s, m0, m1);
+    rc = launch_case<OffT>(g, A, kase, s, m0, m1, b);
     cudaEventRecord(e1, s);
     if (rc != DOBFS_OK) break;
     cudaEventSynchronize(e1);
@@ -1131,7 +1186,17 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   if (dev_level != dev_parent)
     return set_error(DOBFS_ERR_INVALID, "level_out and parent_out must both be host or both be device memory");
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
-  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g));
+  const BlockCfg bc = block_cfg(o);
+  if (!host_loop_mode && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
+    // another block configuration: the level graph is rebuilt for it (after
+    // the previous run, which may still use the old one)
+    DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
+    cudaGraphExecDestroy(g->cg_exec);
+    cudaGraphDestroy(g->cg);
+    g->cg_exec = nullptr;
+    g->cg = nullptr;
+  }
+  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
   const BfsArgs<OffT> A = make_args<OffT>(g);
   int32_t* lv = level_out;
   int32_t* pa = parent_out;
@@ -1148,13 +1213,12 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
                                 o.td_split_pct);
   DOBFS_CUDA_TRY(cudaGetLastError());
   if (host_loop_mode) {
-    DOBFS_TRY(host_loop<OffT>(g, A, s));
+    DOBFS_TRY(host_loop<OffT>(g, A, s, bc));
   } else {
     DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
   }
-  const int out_grid = (int)std::min<int64_t>(ceil_div(ceil_div(g->n, 4), kThreads), (int64_t)grid_cap(16));
   const int32_t* n2o = g->reindexed ? g->new2orig.as<int32_t>() : nullptr;
-  k_output<OffT><<<out_grid, kThreads, 0, s>>>(A, n2o, root, lv, pa);
+  launch_output<OffT>(g, A, n2o, root, lv, pa, s, o.out_threads ? o.out_threads : kThreads);
   if (pa && (o.flags & DOBFS_RUN_CANONICAL_PARENT))
     k_canonical_parent<OffT><<<grid_cap(8), kThreads, 0, s>>>(A, n2o, pa);
   DOBFS_CUDA_TRY(cudaGetLastError());
@@ -1281,6 +1345,9 @@ int dobfs_run_opts_init(dobfs_run_opts* o) {
   o->td_chunk = 0;
   o->bu_scan = 0;
   o->td_split_pct = 150;
+  o->bu_threads = 0;
+  o->td_threads = 0;
+  o->out_threads = 0;
   return DOBFS_OK;
 }
 

@@ -25,7 +25,9 @@ inline bool cutoffs_valid(const dobfs_run_opts& o) {
   const bool chunk_ok = o.td_chunk == 0 || (o.td_chunk >= 256 && o.td_chunk <= 8192 && o.td_chunk % 128 == 0);
   const bool scan_ok = o.bu_scan == 0 || (o.bu_scan >= 1 && o.bu_scan <= 256);
   const bool split_ok = o.td_split_pct >= 0 && o.td_split_pct <= 100000;
-  return small_ok && chunk_ok && scan_ok && split_ok;
+  auto block_ok = [](int32_t t) { return t == 0 || t == 128 || t == 256 || t == 512; };
+  const bool blocks_ok = block_ok(o.bu_threads) && block_ok(o.td_threads) && block_ok(o.out_threads);
+  return small_ok && chunk_ok && scan_ok && split_ok && blocks_ok;
 }
 
 // Device-side control block of one BFS run (one per graph). The level loop
@@ -111,6 +113,7 @@ struct dobfs_graph {
   // level loop as a CUDA graph with a device-driven while node
   cudaGraph_t cg = nullptr;
   cudaGraphExec_t cg_exec = nullptr;
+  int cg_bu = 0, cg_td = 0;           // block sizes the level graph was built with
   cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool last_host_loop = false;

@@ -383,9 +383,9 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
 
 // Top-down, part 2: one warp per record pushes front[u] to the unseen lanes
 // of each neighbour.
-template <class OffT, int W>
-__global__ void __launch_bounds__(kThreads) k_ms_td(MsArgs<OffT> A) {
-  __shared__ unsigned long long sh[kThreads / 32];
+template <class OffT, int W, int NT>
+__global__ void __launch_bounds__(NT) k_ms_td(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[NT / 32];
   const MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
@@ -487,9 +487,9 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
 // the frontier masks of its first bu_scan neighbours and stops once every
 // missing lane is found; longer rows continue in k_ms_bu_long with the
 // partial mask kept in next[v].
-template <class OffT, int W>
-__global__ void __launch_bounds__(kThreads) k_ms_bu(MsArgs<OffT> A) {
-  __shared__ unsigned long long sh[kThreads / 32];
+template <class OffT, int W, int NT>
+__global__ void __launch_bounds__(NT) k_ms_bu(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[NT / 32];
   __shared__ int64_t s_tab[2 * kSmallDeg];
   if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
   __syncthreads();
@@ -831,18 +831,35 @@ MsArgs<OffT> ms_args(MsGroup* m) {
 
 int ms_grid(int per_sm = 8) { return sm_count() * per_sm; }
 
+// The main kernel of a step (top-down push or bottom-up search) with T
+// threads per block, as many threads per SM as the others.
+template <class OffT, int W, int NT>
+void ms_main_t(const MsArgs<OffT>& A, int kase, cudaStream_t s) {
+  const int G = ms_grid(8 * kThreads / NT);
+  if (kase == 0)
+    k_ms_td<OffT, W, NT><<<G, NT, 0, s>>>(A);
+  else
+    k_ms_bu<OffT, W, NT><<<G, NT, 0, s>>>(A);
+}
+
 template <class OffT, int W>
 int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   const int G = ms_grid();
+  const int t = kase == 0 ? m->td_threads : m->bu_threads;
+  auto main_step = [&]() {
+    if (t == 128) ms_main_t<OffT, W, 128>(A, kase, s);
+    else if (t == 512) ms_main_t<OffT, W, 512>(A, kase, s);
+    else ms_main_t<OffT, W, 256>(A, kase, s);
+  };
   k_ms_clear_plane<OffT, W><<<G, kThreads, 0, s>>>(A);
   if (kase == 0) {
     k_ms_clear_next<OffT, W><<<G, kThreads, 0, s>>>(A);
     k_ms_td_list<OffT, W><<<G, kThreads, 0, s>>>(A);
-    k_ms_td<OffT, W><<<G, kThreads, 0, s>>>(A);
+    main_step();
     k_ms_td_post<OffT, W><<<G, kThreads, 0, s>>>(A);
   } else {
-    k_ms_bu<OffT, W><<<G, kThreads, 0, s>>>(A);
+    main_step();
     k_ms_bu_long<OffT, W><<<G, kThreads, 0, s>>>(A);
     k_ms_bu_fin<OffT, W><<<G, kThreads, 0, s>>>(A);
   }
@@ -907,6 +924,8 @@ int ms_build_graph(MsGroup* m) {
   const cudaError_t e = cudaGraphInstantiate(&m->exec, m->cg, 0);
   if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e)));
   cudaStreamDestroy(cs);
+  m->graph_bu = m->bu_threads;
+  m->graph_td = m->td_threads;
   return DOBFS_OK;
 }
 
@@ -1043,6 +1062,8 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   c.td_chunk = o.td_chunk ? o.td_chunk : kMsChunk;
   c.bu_scan = o.bu_scan ? o.bu_scan : kMsT;
   c.sched_seed = o.schedule_seed;
+  m->bu_threads = o.bu_threads ? o.bu_threads : kThreads;
+  m->td_threads = o.td_threads ? o.td_threads : kThreads;
   // written by a kernel that takes the block by value, so the host neither
   // keeps a staging copy alive nor waits for the stream
   k_ms_set_ctl<<<1, 1, 0, s>>>(m->ctl.as<MsCtl>(), c);
@@ -1067,6 +1088,15 @@ int ms_group_step(MsGroup* m, MsCtl* after_switch, float* case_ms) {
 }
 
 int ms_group_run_to_end(MsGroup* m) {
+  if (m->exec && (m->graph_bu != m->bu_threads || m->graph_td != m->td_threads)) {
+    // the loop graph was built for other block sizes: rebuild it (the
+    // group's stream orders it after any launch still running)
+    DOBFS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    cudaGraphExecDestroy(m->exec);
+    cudaGraphDestroy(m->cg);
+    m->exec = nullptr;
+    m->cg = nullptr;
+  }
   if (!m->exec) DOBFS_TRY(MS_DISPATCH(m, ms_build_graph, m));
   DOBFS_CUDA_TRY(cudaGraphLaunch(m->exec, m->stream));
   return DOBFS_OK;

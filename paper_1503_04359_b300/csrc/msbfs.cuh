@@ -76,6 +76,8 @@ struct MsGroup {
   DevBuf args;            // device copy of seeding arguments
   cudaGraph_t cg = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int bu_threads = 256, td_threads = 256;  // block sizes of the step's main kernels (set by a reset)
+  int graph_bu = 0, graph_td = 0;          // block sizes the loop graph was built with
 };
 
 // Device bytes of one lane group of `words` mask words on g (what ms_group_create allocates).

@@ -62,7 +62,8 @@ class dobfs_run_opts(ctypes.Structure):
                 ("static_pct", ctypes.c_int32), ("bu_steps", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("schedule_seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("td_bitmap_div", ctypes.c_int32),
                 ("td_small_max", ctypes.c_int32), ("td_chunk", ctypes.c_int32), ("bu_scan", ctypes.c_int32),
-                ("td_split_pct", ctypes.c_int32)]
+                ("td_split_pct", ctypes.c_int32), ("bu_threads", ctypes.c_int32), ("td_threads", ctypes.c_int32),
+                ("out_threads", ctypes.c_int32)]
 
 
 class dobfs_run_stats(ctypes.Structure):
@@ -299,7 +300,8 @@ def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: i
               static_pct: int | None = None, bu_steps: int | None = None, flags: int = 0, schedule_seed: int = 0,
               stream=None, td_bitmap_div: int | None = None, td_small_max: int | None = None,
               td_chunk: int | None = None, bu_scan: int | None = None,
-              td_split_pct: int | None = None) -> dobfs_run_opts:
+              td_split_pct: int | None = None, bu_threads: int | None = None, td_threads: int | None = None,
+              out_threads: int | None = None) -> dobfs_run_opts:
     o = dobfs_run_opts()
     _check(load().dobfs_run_opts_init(ctypes.byref(o)))
     o.direction = direction
@@ -321,6 +323,12 @@ def make_opts(direction: int = DOBFS_DIR_AUTO, alpha: int | None = None, beta: i
         o.bu_scan = bu_scan
     if td_split_pct is not None:
         o.td_split_pct = td_split_pct
+    if bu_threads is not None:
+        o.bu_threads = bu_threads
+    if td_threads is not None:
+        o.td_threads = td_threads
+    if out_threads is not None:
+        o.out_threads = out_threads
     o.flags = flags
     o.schedule_seed = schedule_seed
     o.stream = _stream(stream)

@@ -69,6 +69,9 @@ def test_argument_errors_without_gpu(lib):
     assert list(buf[ctypes.sizeof(dobfs.dobfs_run_opts):]) == [0xA5] * 64
     last = dobfs.dobfs_run_opts.td_split_pct.offset
     assert list(buf[last:last + 4]) == [150, 0, 0, 0]
+    assert (o.bu_threads, o.td_threads, o.out_threads) == (0, 0, 0)
+    tail = dobfs.dobfs_run_opts.out_threads.offset
+    assert tail + 4 == ctypes.sizeof(dobfs.dobfs_run_opts) and list(buf[tail:tail + 4]) == [0, 0, 0, 0]
     # allocator hook: both or neither
     assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(lambda n, s, c: None), dobfs.FREE_FN(), None) == dobfs.DOBFS_ERR_INVALID
     assert lib.dobfs_set_allocator(dobfs.ALLOC_FN(), dobfs.FREE_FN(), None) == dobfs.DOBFS_OK

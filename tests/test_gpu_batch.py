@@ -68,6 +68,18 @@ def test_batch_degree_bin_cutoffs(d, s14, cut):
         _batch(d, g, roots[:4], td_chunk=100)
 
 
+@pytest.mark.parametrize("blocks", [dict(bu_threads=128, td_threads=512), dict(bu_threads=512, td_threads=128)])
+def test_batch_block_sizes(d, s14, blocks):
+    """Threads per block of the batched step kernels change only the speed;
+    the loop graph is rebuilt when they change between batches."""
+    spec, og, roots, ref = s14
+    g = d.rmat_graph(spec, flags=0x2)
+    for mode, seed in ((0, 0), (3, 4)):
+        np.testing.assert_array_equal(_batch(d, g, roots[:64], mode, seed, **blocks), ref[:64])
+        np.testing.assert_array_equal(_batch(d, g, roots[:64], mode, seed), ref[:64])
+        np.testing.assert_array_equal(_batch(d, g, roots[:200], mode, seed, **blocks), ref[:200])
+
+
 def test_batch_sizes_duplicates_host(d, s14):
     spec, og, roots, ref = s14
     g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64)

@@ -260,9 +260,31 @@ def test_degree_bin_cutoffs(d, s16, cut, mode, seed):
             _check_run(og, int(r), lv, pa, ref_l[i])
 
 
+@pytest.mark.parametrize("blocks", [dict(bu_threads=128, td_threads=512, out_threads=128),
+                                    dict(bu_threads=512, td_threads=128, out_threads=512),
+                                    dict(bu_threads=128, td_threads=128, out_threads=256)])
+@pytest.mark.parametrize("mode,seed", [(0, 0), (3, 7)])
+def test_block_sizes(d, s16, blocks, mode, seed):
+    """Threads per block of the step and output kernels change only the
+    speed: levels bit-exact and parents valid for every block size, with the
+    level graph rebuilt when the block sizes change between runs, and in
+    host-driven levels."""
+    spec, og, roots, ref_l, ref_p = s16
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    for i, r in enumerate(roots[:3]):
+        for div in (0, 2):
+            lv, pa, _ = _run(d, g, int(r), mode, seed, td_bitmap_div=div, **blocks)
+            _check_run(og, int(r), lv, pa, ref_l[i])
+            lv, pa, _ = _run(d, g, int(r), mode, seed, td_bitmap_div=div)  # back to the defaults
+            _check_run(og, int(r), lv, pa, ref_l[i])
+        lv, pa, _ = _run(d, g, int(r), mode, seed, flags=d.DOBFS_RUN_HOST_LOOP, **blocks)
+        _check_run(og, int(r), lv, pa, ref_l[i])
+
+
 @pytest.mark.parametrize("bad", [dict(td_small_max=7), dict(td_small_max=257), dict(td_chunk=200),
                                  dict(td_chunk=8320), dict(td_chunk=300), dict(bu_scan=-1), dict(bu_scan=257),
-                                 dict(td_split_pct=-1), dict(td_split_pct=100001)])
+                                 dict(td_split_pct=-1), dict(td_split_pct=100001), dict(bu_threads=64),
+                                 dict(td_threads=1024), dict(out_threads=300)])
 def test_bad_cutoffs_rejected(d, s16, bad):
     spec, og, roots, ref_l, ref_p = s16
     g = d.rmat_graph(spec)
