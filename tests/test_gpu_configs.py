@@ -102,28 +102,31 @@ def _gpu_runs_vm(d, g, roots, flags=0):
 
 
 def test_config3a_rmat28_streaming_check(d):
-    """Scale 28: 16 roots (default parents) in one pass of the streaming
-    checker, and 4 more with canonical parents compared with the checker's
-    canonical parents."""
+    """Scale 28: 20 roots in one pass of the streaming checker, 16 with the
+    default parents and 4 with canonical parents, compared bit-exact with
+    the checker's canonical parents."""
     spec = inputs.rmat(28)
     src, dst = inputs.rmat_pairs(spec, count=1 << 20)
     roots = _pair_roots(src, dst, inputs.root_seed(spec.seed), 20)
     del src, dst
     g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
-    lv, pa = _gpu_runs_vm(d, g, roots[:16])
-    lv_c, pa_c = _gpu_runs_vm(d, g, roots[16:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    n = g.n
+    lv = torch.empty((20, n), dtype=torch.int32, device="cuda")
+    pa = torch.empty((20, n), dtype=torch.int32, device="cuda")
+    for i, r in enumerate(roots):
+        g.run(int(r), lv[i], pa[i], d.make_opts(flags=d.DOBFS_RUN_CANONICAL_PARENT if i >= 16 else 0))
+    torch.cuda.synchronize()
     g.close()
+    levels, parents = lv.t().contiguous().cpu().numpy(), pa.t().contiguous().cpu().numpy()
+    del lv, pa
     torch.cuda.empty_cache()
     t0 = time.time()
-    rc, bad, _ = oracle.check_bfs_rmat_stream_multi(spec, roots[:16], lv, pa, vertex_major=True)
-    print("scale 28: 16 roots checked in %.0f s" % (time.time() - t0), flush=True)
-    assert rc.tolist() == [0] * 16, [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
-    assert all(int((lv[:, i] >= 0).sum()) > 1000 for i in range(16))
-    del lv, pa
-    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots[16:], lv_c, pa_c, want_canon=True,
+    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, levels, parents, want_canon=True,
                                                         vertex_major=True)
-    assert rc.tolist() == [0] * 4, [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
-    np.testing.assert_array_equal(pa_c, canon)
+    print("scale 28: 20 roots checked in %.0f s" % (time.time() - t0), flush=True)
+    assert rc.tolist() == [0] * 20, [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
+    np.testing.assert_array_equal(parents[:, 16:], canon[:, 16:])
+    assert all(int((levels[:, i] >= 0).sum()) > 1000 for i in range(20))
 
 
 @pytest.mark.skipif(os.environ.get("DOBFS_FULL_VALIDATION", "0") in ("", "0"),
@@ -163,17 +166,18 @@ def test_rmat29_chunked_build_streaming_check(d):
     del src, dst
     g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
     assert g.info.offsets_int64 == 1 and g.info.n_entries > (1 << 33)
-    lv, pa = _gpu_runs(d, g, roots[:1])
-    lv_c, pa_c = _gpu_runs(d, g, roots[1:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
+    lv, pa = _gpu_runs_vm(d, g, roots[:1])
+    lv_c, pa_c = _gpu_runs_vm(d, g, roots[1:], flags=d.DOBFS_RUN_CANONICAL_PARENT)
     g.close()
     torch.cuda.empty_cache()
-    levels = np.concatenate([lv, lv_c])
-    parents = np.concatenate([pa, pa_c])
+    levels = np.ascontiguousarray(np.concatenate([lv, lv_c], axis=1))
+    parents = np.ascontiguousarray(np.concatenate([pa, pa_c], axis=1))
     del lv, pa, lv_c, pa_c
-    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, levels, parents, want_canon=True)
+    rc, bad, canon = oracle.check_bfs_rmat_stream_multi(spec, roots, levels, parents, want_canon=True,
+                                                        vertex_major=True)
     assert rc.tolist() == [0, 0], [(oracle.RULES[int(r)], int(b)) for r, b in zip(rc, bad)]
-    np.testing.assert_array_equal(parents[1:], canon[1:])
-    assert all(int((levels[i] >= 0).sum()) > 1000 for i in range(2))
+    np.testing.assert_array_equal(parents[:, 1:], canon[:, 1:])
+    assert all(int((levels[:, i] >= 0).sum()) > 1000 for i in range(2))
 
 
 def test_config3b_chunglu26_streaming_check(d):
