@@ -1333,8 +1333,8 @@ int dobfs_graph_get_info(const dobfs_graph* g, dobfs_graph_info* info) {
   info->offsets_int64 = g->off64 ? 1 : 0;
   info->reindexed = g->reindexed ? 1 : 0;
   int64_t bytes = 0;
-  const DevBuf* bufs[] = {&g->off, &g->cols, &g->new2orig, &g->orig2new, &g->isolated, &g->visited, &g->fbm0,
-                          &g->fbm1, &g->lp, &g->q0, &g->q1, &g->rec, &g->deferred, &g->firstdeg, &g->ctl, &g->trace,
+  const DevBuf* bufs[] = {&g->off, &g->cols, &g->new2orig, &g->orig2new, &g->isolated, &g->visited, &g->fbm,
+                          &g->lp, &g->q0, &g->q1, &g->rec, &g->deferred, &g->firstdeg, &g->ctl, &g->trace,
                           &g->out_stage};
   for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
   info->device_bytes = bytes;
