@@ -211,9 +211,6 @@ int dobfs_graph_load(const char* path, uint32_t flags, void* stream, dobfs_graph
 #define DOBFS_RUN_HOST_LOOP 0x2u        /* drive levels from the host and time every kernel
                                            (diagnostics; adds one host round trip per level) */
 #define DOBFS_RUN_SYNC_STATS 0x4u       /* wait for completion and fill *stats */
-#define DOBFS_RUN_L2_PERSIST 0x8u       /* keep the frontier bitmaps in the L2's persisting part during
-                                           the level loop (raises the calling process's persisting-L2
-                                           limit to their size, within the device's maximum) */
 
 typedef struct {
   int32_t direction;        /* DOBFS_DIR_* */

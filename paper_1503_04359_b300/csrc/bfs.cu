@@ -1067,52 +1067,8 @@ void launch_output(dobfs_graph* g, const BfsArgs<OffT>& A, const int32_t* n2o, i
   }
 }
 
-// The frontier bitmaps as an L2 persisting access window (run flag
-// DOBFS_RUN_L2_PERSIST): a bottom-up step tests a frontier bit for every
-// neighbour it reads, while the columns, (first, degree) pairs and (level,
-// parent) entries stream past; in the window the bitmap lines are kept in the
-// L2's persisting part. The size of that part is a limit of the calling
-// process's context, which ends with the process; it is raised to the
-// window's size (within the device's maximum) when a run first asks for it.
-int persist_window(dobfs_graph* g, cudaAccessPolicyWindow* w) {
-  int dev = 0, max_win = 0, max_persist = 0;
-  DOBFS_CUDA_TRY(cudaGetDevice(&dev));
-  DOBFS_CUDA_TRY(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev));
-  DOBFS_CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
-  const size_t bytes = 2 * sizeof(uint32_t) * (size_t)g->words;
-  const size_t win = std::min<size_t>(bytes, (size_t)std::max(max_win, 0));
-  const size_t want = std::min<size_t>(win, (size_t)std::max(max_persist, 0));
-  size_t cur = 0;
-  DOBFS_CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
-  if (cur < want) DOBFS_CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
-  *w = cudaAccessPolicyWindow{};
-  w->base_ptr = g->fbm.ptr;
-  w->num_bytes = win;
-  w->hitRatio = win ? std::min(1.0f, (float)std::max(cur, want) / (float)win) : 0.f;
-  w->hitProp = cudaAccessPropertyPersisting;
-  w->missProp = cudaAccessPropertyStreaming;
-  return DOBFS_OK;
-}
-
-// Gives every kernel node of graph cg the access policy window w.
-int set_window_on_kernels(cudaGraph_t cg, const cudaAccessPolicyWindow& w) {
-  size_t nn = 0;
-  DOBFS_CUDA_TRY(cudaGraphGetNodes(cg, nullptr, &nn));
-  std::vector<cudaGraphNode_t> nodes(nn);
-  if (nn) DOBFS_CUDA_TRY(cudaGraphGetNodes(cg, nodes.data(), &nn));
-  cudaKernelNodeAttrValue v = {};
-  v.accessPolicyWindow = w;
-  for (cudaGraphNode_t nd : nodes) {
-    cudaGraphNodeType t;
-    DOBFS_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
-    if (t == cudaGraphNodeTypeKernel)
-      DOBFS_CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeAccessPolicyWindow, &v));
-  }
-  return DOBFS_OK;
-}
-
 template <class OffT>
-int build_level_graph(dobfs_graph* g, BlockCfg b, bool persist) {
+int build_level_graph(dobfs_graph* g, BlockCfg b) {
   const BfsArgs<OffT> A = make_args<OffT>(g);
   cudaStream_t cs = nullptr;
   DOBFS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1167,19 +1123,12 @@ int build_level_graph(dobfs_graph* g, BlockCfg b, bool persist) {
     cudaError_t e = cudaStreamEndCapture(cs, &cap);
     if (rc != DOBFS_OK) return fail(rc);
     if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture case %d: %s", k, cudaGetErrorString(e)));
-    if (persist) {
-      cudaAccessPolicyWindow w;
-      rc = persist_window(g, &w);
-      if (rc == DOBFS_OK) rc = set_window_on_kernels(sp.conditional.phGraph_out[k], w);
-      if (rc != DOBFS_OK) return fail(rc);
-    }
   }
   cudaError_t e = cudaGraphInstantiate(&g->cg_exec, g->cg, 0);
   if (e != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)));
   cudaStreamDestroy(cs);
   g->cg_bu = b.bu;
   g->cg_td = b.td;
-  g->cg_persist = persist;
   return DOBFS_OK;
 }
 
@@ -1236,8 +1185,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     return set_error(DOBFS_ERR_INVALID, "level_out and parent_out must both be host or both be device memory");
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
   const BlockCfg bc = block_cfg(o);
-  const bool persist = (o.flags & DOBFS_RUN_L2_PERSIST) != 0;
-  if (!host_loop_mode && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td || g->cg_persist != persist)) {
+  if (!host_loop_mode && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
     // another block configuration: the level graph is rebuilt for it (after
     // the previous run, which may still use the old one)
     DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
@@ -1246,7 +1194,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     g->cg_exec = nullptr;
     g->cg = nullptr;
   }
-  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc, persist));
+  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
   const BfsArgs<OffT> A = make_args<OffT>(g);
   int32_t* lv = level_out;
   int32_t* pa = parent_out;
@@ -1263,19 +1211,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
                                 o.td_split_pct);
   DOBFS_CUDA_TRY(cudaGetLastError());
   if (host_loop_mode) {
-    if (persist) {  // the window on the stream for the levels only, then taken off again
-      cudaStreamAttrValue v = {};
-      DOBFS_TRY(persist_window(g, &v.accessPolicyWindow));
-      DOBFS_CUDA_TRY(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v));
-    }
-    const int rc = host_loop<OffT>(g, A, s, bc);
-    if (persist) {
-      cudaStreamAttrValue off = {};
-      off.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
-      off.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
-      DOBFS_CUDA_TRY(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &off));
-    }
-    DOBFS_TRY(rc);
+    DOBFS_TRY(host_loop<OffT>(g, A, s, bc));
   } else {
     DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
   }

@@ -98,8 +98,7 @@ struct dobfs_graph {
 
   // BFS workspace
   dobfs::DevBuf visited;              // bitmap
-  dobfs::DevBuf fbm;                  // both frontier bitmaps, words [0, words) and [words, 2 words):
-                                      // one allocation, so one L2 access window covers them
+  dobfs::DevBuf fbm;                  // both frontier bitmaps: words [0, words) and [words, 2 words)
   dobfs::DevBuf lp;                   // int2[n]: (level, parent) in internal IDs
   dobfs::DevBuf q0, q1;               // int32[n] queues
   dobfs::DevBuf rec;                  // int2[] top-down chunk records
@@ -116,7 +115,6 @@ struct dobfs_graph {
   cudaGraph_t cg = nullptr;
   cudaGraphExec_t cg_exec = nullptr;
   int cg_bu = 0, cg_td = 0;           // block sizes the level graph was built with
-  bool cg_persist = false;            // ... and whether its kernels keep the frontier bitmaps in L2
   cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool last_host_loop = false;
