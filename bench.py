@@ -819,7 +819,7 @@ def main() -> None:
     # the same whole-BFS bytes with the output pass counted as 8 bytes per reached
     # vertex (its level and parent), without the writes of unreached vertices'
     # -1 entries and the map reads
-    out_extra = 8 * n + (4 * int(info.n_nonisolated) + 2 * ((n + 7) // 8) if info.reindexed else 0)
+    out_extra = 8 * n + (4 * n if info.reindexed else 0)
     whole_gbs_8r = (sum(b - out_extra for b in alg_bytes) / (total_ms * 1e-3)) / 1e9
 
     energy = energy_pass(torch, g, roots, level, parent, opts, teps, gpu_bus_id(torch, dev)) if rank == 0 else None
@@ -916,9 +916,8 @@ def main() -> None:
             "whole_bfs_alg_gbs": whole_gbs, "whole_bfs_frac": whole_gbs / peak,
             "whole_bfs_frac_out8r": whole_gbs_8r / peak,
             "whole_bfs_note": ("whole_bfs_frac counts the output pass as 8 n (level and parent of every vertex "
-                               "written) + 8 per reached vertex (its entry gathered) + on renumbered graphs the map "
-                               "(4 per vertex with an edge, n / 4 for the bit and count per 32 original IDs); "
-                               "whole_bfs_frac_out8r counts only 8 per reached vertex"),
+                               "written) + 4 n (map read, renumbered graphs) + 8 per reached vertex (its entry "
+                               "gathered); whole_bfs_frac_out8r counts only 8 per reached vertex"),
             "alg_bytes_per_root": float(np.mean(alg_bytes)),
         },
         "e2e": {"value": e2e_hm, "unit": "GTEPS", "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 8 * n,

@@ -259,11 +259,9 @@ typedef struct {
                                top-down with bitmap output and mixed levels:
                                  24 n_f + 4 e_examined + 8 n_scanned + 12 n_new;
                                plus the output pass: 8 n (level and parent written)
-                                 + 8 reached ((level, parent) gathered), and on
-                                 renumbered graphs the map: 4 per vertex with an
-                                 edge + n / 4 (a bit and a 4-byte count per 32
-                                 original IDs). Frontier and visited bitmaps are
-                               counted as L2 traffic, not DRAM. */
+                                 + 4 n (map read, renumbered graphs) + 8 reached
+                                 ((level, parent) gathered). Frontier and visited
+                               bitmaps are counted as L2 traffic, not DRAM. */
 } dobfs_run_stats;
 
 /* Fills *opts with the defaults. */

@@ -68,9 +68,6 @@ struct BfsArgs {
   const int32_t* cols;
   const uint32_t* iso;
   const int32_t* o2n;  // NULL when not reindexed
-  const uint32_t* ohas;   // renumbered graphs: bit o = original ID o has an edge
-  const int32_t* orank;   // ... original IDs with an edge before each word
-  const int32_t* o2n_c;   // ... their new IDs in original-ID order
   const int2* firstdeg;  // (first neighbour, degree) per vertex; first = -1 for isolated vertices
   const int64_t* deg_ge;  // [33]: vertices of degree >= 2^k
   const int64_t* small_tab;  // [2 * kSmallDeg]: row offset and first ID of each small degree (renumbered graphs)
@@ -769,12 +766,10 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
 }
 
 // Results in original IDs: level_out[o], parent_out[o] for every vertex.
-// Each thread handles four consecutive original IDs (16-byte output
-// stores). On a renumbered graph an isolated vertex is unreached unless it
-// is the root, so the map is read only for the original IDs with an edge:
-// a bit per original ID says which have one, a count per 32 IDs gives
-// their position in the compacted map of their new IDs (4 bytes per vertex
-// with an edge instead of 4 per vertex).
+// Each thread handles four consecutive original IDs (16-byte map loads and
+// output stores). Vertices renumbered past the last one with an edge are
+// isolated: unreached unless they are the root, so only the root among them
+// needs the visited bit and the (level, parent) gather.
 template <class OffT, int NT>
 __global__ void __launch_bounds__(NT) k_output(BfsArgs<OffT> A, const int32_t* __restrict__ n2o,
                                                      int32_t root_orig, int32_t* __restrict__ level_out,
@@ -803,21 +798,11 @@ __global__ void __launch_bounds__(NT) k_output(BfsArgs<OffT> A, const int32_t* _
         const int64_t q = q0 + a * (int64_t)blockDim.x;
         inq[a] = q < qhi;
         if (A.o2n) {
-          // quad q: bits 4 (q & 7) .. +3 of word q >> 3; -1 marks an isolated vertex
-          const int64_t w = q >> 3;
-          const int sh = (int)(q & 7) * 4;
-          const uint32_t hw = inq[a] ? __ldg(A.ohas + w) : 0u;
-          const uint32_t bits = (hw >> sh) & 0xFu;
-          int32_t r = bits ? __ldg(A.orank + w) + __popc(hw & ((1u << sh) - 1u)) : 0;
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if ((bits >> t) & 1u) {
-              v[a][t] = bc_vid(__ldg(A.o2n_c + r), A.n, &A.ctl->bc_site, kBcOutput);
-              ++r;
-            } else {
-              v[a][t] = (q * 4 + t == root_orig) ? root : -1;
-            }
-          }
+          const int4 m = inq[a] ? __ldg(reinterpret_cast<const int4*>(A.o2n) + q) : make_int4(0, 0, 0, 0);
+          v[a][0] = bc_vid(m.x, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][1] = bc_vid(m.y, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][2] = bc_vid(m.z, A.n, &A.ctl->bc_site, kBcOutput);
+          v[a][3] = bc_vid(m.w, A.n, &A.ctl->bc_site, kBcOutput);
         } else {
 #pragma unroll
           for (int t = 0; t < 4; ++t) v[a][t] = (int32_t)(q * 4 + t);
@@ -833,7 +818,7 @@ __global__ void __launch_bounds__(NT) k_output(BfsArgs<OffT> A, const int32_t* _
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int32_t vt = v[a][t];
-          need[a][t] = inq[a] && vt >= 0;
+          need[a][t] = inq[a] && (!A.o2n || vt < A.n_nonisolated || vt == root);
           // the visited word and the (level, parent) pair are loaded together;
           // the pair is used only if the vertex was visited
           vw[a][t] = need[a][t] ? __ldg(A.visited + (vt >> 5)) : 0u;
@@ -926,9 +911,6 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   A.cols = g->cols.as<int32_t>();
   A.iso = g->isolated.as<uint32_t>();
   A.o2n = g->reindexed ? g->orig2new.as<int32_t>() : nullptr;
-  A.ohas = g->reindexed ? g->ohas.as<uint32_t>() : nullptr;
-  A.orank = g->reindexed ? g->orank.as<int32_t>() : nullptr;
-  A.o2n_c = g->reindexed ? g->o2n_c.as<int32_t>() : nullptr;
   A.firstdeg = g->firstdeg.as<int2>();
   A.deg_ge = g->degge.as<int64_t>();
   A.small_tab = g->degge.as<int64_t>() + 33;
@@ -1267,11 +1249,9 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
       stats->reached = c.reached;
       stats->teps_edges = c.teps2 / 2;
       stats->edges_examined = c.examined;
-      // output pass: 8 bytes written per vertex, the (level, parent) pair of
-      // every reached vertex, and on renumbered graphs the map: a bit and a
-      // quarter of a 4-byte count per original ID, 4 bytes per vertex with an edge
-      stats->alg_bytes = c.alg_bytes + 8 * g->n + 8 * c.reached +
-                         (g->reindexed ? 4 * g->n_nonisolated + 2 * ceil_div(g->n, 8) : 0);
+      // output pass: 8 bytes written per vertex, the map read when renumbered,
+      // and the (level, parent) pair of every reached vertex
+      stats->alg_bytes = c.alg_bytes + 8 * g->n + (g->reindexed ? 4 * g->n : 0) + 8 * c.reached;
     }
   }
   return DOBFS_OK;
@@ -1306,7 +1286,6 @@ int graph_alloc_workspace(dobfs_graph* g) {
                                                    g->firstdeg.as<int2>());
     DOBFS_CUDA_TRY(cudaGetLastError());
   }
-  DOBFS_TRY(build_output_map(g, s));
   DOBFS_TRY(g->ctl.alloc(sizeof(BfsCtl), s));
   DOBFS_TRY(g->trace.alloc(sizeof(LevelRec) * kMaxTrace, s));
   DOBFS_CUDA_TRY(cudaMemsetAsync(g->ctl.ptr, 0, sizeof(BfsCtl), s));

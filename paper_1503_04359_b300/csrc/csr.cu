@@ -1009,62 +1009,6 @@ int new_graph(int64_t n, cudaStream_t s, dobfs_graph** out) {
 }
 
 // Finishes a build: workspace, timing; on failure frees the graph.
-namespace {
-
-// One warp per 32 original IDs: bit o of has[] = o has an edge (its new ID is
-// below n_nonisolated), cnt[w] = such IDs in word w.
-__global__ void k_has_edge_words(const int32_t* __restrict__ o2n, int64_t n, int64_t n_non, int64_t words,
-                                 uint32_t* __restrict__ has, int64_t* __restrict__ cnt) {
-  const unsigned lane = lane_id();
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words; w += warps) {
-    const int64_t o = w * 32 + lane;
-    const unsigned b = __ballot_sync(0xffffffffu, o < n && (int64_t)o2n[o] < n_non);
-    if (lane == 0) {
-      has[w] = b;
-      cnt[w] = __popc(b);
-    }
-  }
-}
-
-// o2n_c[rank of o among the original IDs with an edge] = o2n[o].
-__global__ void k_compact_map(const int32_t* __restrict__ o2n, int64_t n, int64_t words,
-                              const uint32_t* __restrict__ has, const int32_t* __restrict__ rank,
-                              int32_t* __restrict__ o2n_c) {
-  const unsigned lane = lane_id();
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words; w += warps) {
-    const uint32_t b = has[w];
-    if ((b >> lane) & 1u) o2n_c[rank[w] + __popc(b & lanemask_lt())] = o2n[w * 32 + lane];
-  }
-}
-
-}  // namespace
-
-int build_output_map(dobfs_graph* g, cudaStream_t s) {
-  if (!g->reindexed) return DOBFS_OK;
-  const int64_t words = g->words;
-  DOBFS_TRY(g->ohas.alloc(sizeof(uint32_t) * (size_t)words, s));
-  DOBFS_TRY(g->orank.alloc(sizeof(int32_t) * (size_t)(words + 1), s));
-  DOBFS_TRY(g->o2n_c.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(g->n_nonisolated, 1), s));
-  DevBuf cnt;
-  DOBFS_TRY(cnt.alloc(sizeof(int64_t) * (size_t)words, s));
-  const int grid = (int)std::min<int64_t>(ceil_div(words * 32, kThreads), (int64_t)sm_count() * 16);
-  k_has_edge_words<<<grid, kThreads, 0, s>>>(g->orig2new.as<int32_t>(), g->n, g->n_nonisolated, words,
-                                             g->ohas.as<uint32_t>(), cnt.as<int64_t>());
-  DOBFS_CUDA_TRY(cudaGetLastError());
-  int64_t total = 0;
-  DOBFS_TRY(exclusive_scan<int32_t>(cnt.as<int64_t>(), words, g->orank.as<int32_t>(), s, &total));
-  if (total != g->n_nonisolated)
-    return set_error(DOBFS_ERR_BAD_GRAPH, "output map: %lld original IDs with an edge, %lld expected",
-                     (long long)total, (long long)g->n_nonisolated);
-  k_compact_map<<<grid, kThreads, 0, s>>>(g->orig2new.as<int32_t>(), g->n, words, g->ohas.as<uint32_t>(),
-                                          g->orank.as<int32_t>(), g->o2n_c.as<int32_t>());
-  DOBFS_CUDA_TRY(cudaGetLastError());
-  DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
-  return DOBFS_OK;
-}
-
 int finish_graph(dobfs_graph* g, int rc, cudaEvent_t e0, cudaEvent_t e1, dobfs_graph** out) {
   if (rc == DOBFS_OK) rc = graph_alloc_workspace(g);
   if (rc == DOBFS_OK && e0 && e1) {
@@ -1389,9 +1333,8 @@ int dobfs_graph_get_info(const dobfs_graph* g, dobfs_graph_info* info) {
   info->offsets_int64 = g->off64 ? 1 : 0;
   info->reindexed = g->reindexed ? 1 : 0;
   int64_t bytes = 0;
-  const DevBuf* bufs[] = {&g->off,   &g->cols,  &g->new2orig, &g->orig2new, &g->isolated, &g->visited,
-                          &g->fbm,   &g->ohas,  &g->orank,    &g->o2n_c,    &g->lp,       &g->q0,
-                          &g->q1,    &g->rec,   &g->deferred, &g->firstdeg, &g->ctl,      &g->trace,
+  const DevBuf* bufs[] = {&g->off, &g->cols, &g->new2orig, &g->orig2new, &g->isolated, &g->visited, &g->fbm,
+                          &g->lp, &g->q0, &g->q1, &g->rec, &g->deferred, &g->firstdeg, &g->ctl, &g->trace,
                           &g->out_stage};
   for (const DevBuf* b : bufs) bytes += (int64_t)b->bytes;
   info->device_bytes = bytes;

@@ -88,12 +88,6 @@ struct dobfs_graph {
   // vector loads of a row's last aligned chunk stay inside the allocation.
   dobfs::DevBuf off, cols;
   dobfs::DevBuf new2orig, orig2new;  // int32[n] each, only when reindexed
-  // the output pass's map (renumbered graphs): bit o of ohas is set when
-  // original ID o has an edge; orank[w] = such IDs before word w; o2n_c =
-  // the new IDs of those original IDs, in original-ID order. The output pass
-  // reads the map of vertices with an edge only (isolated ones are
-  // unreached unless they are the root).
-  dobfs::DevBuf ohas, orank, o2n_c;
   dobfs::DevBuf isolated;            // bitmap: degree-0 vertices and bits >= n
   int64_t deg_ge[33] = {};           // vertices of degree >= 2^k (a prefix of the IDs when reindexed)
   // renumbered graphs: [d] row offset and [kSmallDeg + d] first ID of the
@@ -159,7 +153,5 @@ int read_err_flag(DevBuf& err, cudaStream_t s, int* h);
 // g->reindexed; g->orig2new allocated): checks the build's invariants
 // (DOBFS_ERR_BAD_GRAPH otherwise), fills orig2new and the degree statistics.
 int adopt_csr(dobfs_graph* g, bool check_symmetric, cudaStream_t s);
-// Builds ohas, orank and o2n_c from orig2new (renumbered graphs).
-int build_output_map(dobfs_graph* g, cudaStream_t s);
 
 }  // namespace dobfs
