@@ -1310,6 +1310,13 @@ void graph_release(dobfs_graph* g) {
   g->last_stream = nullptr;
   ms_group_destroy(g->ms);
   g->ms = nullptr;
+  ms_group_destroy(g->ms2);
+  g->ms2 = nullptr;
+  if (g->ms_stream2) cudaStreamDestroy(g->ms_stream2);
+  if (g->ms_ev_fork) cudaEventDestroy(g->ms_ev_fork);
+  if (g->ms_ev_join) cudaEventDestroy(g->ms_ev_join);
+  g->ms_stream2 = nullptr;
+  g->ms_ev_fork = g->ms_ev_join = nullptr;
   if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
   if (g->cg) cudaGraphDestroy(g->cg);
   g->cg_exec = nullptr;

@@ -122,6 +122,9 @@ struct dobfs_graph {
 
   // batched runs: one lane group and a staging buffer for host outputs
   dobfs::MsGroup* ms = nullptr;
+  dobfs::MsGroup* ms2 = nullptr;      // a second group, so that two groups of a batch overlap
+  cudaStream_t ms_stream2 = nullptr;  // ... on their own stream
+  cudaEvent_t ms_ev_fork = nullptr, ms_ev_join = nullptr;
   dobfs::DevBuf ms_stage;
   std::vector<dobfs_level_trace> batch_trace;  // host-driven batch levels (first group)
   bool last_trace_batch = false;

@@ -1177,19 +1177,47 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
     g->ms = nullptr;
   }
   if (!g->ms) DOBFS_TRY(ms_group_create(g, s, words, &g->ms));
-  MsGroup* m = g->ms;
-  m->stream = s;
   const bool dev_out = is_device_ptr(level_out);
   const size_t stage_bytes = sizeof(int32_t) * (size_t)group_lanes * (size_t)g->n;
   if (!dev_out && g->ms_stage.bytes < stage_bytes) DOBFS_TRY(g->ms_stage.alloc(stage_bytes, g->stream));
   const bool host_loop = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
+  // Batches of several groups with device outputs run two groups at a time,
+  // alternating between two lane groups on two streams: one group's
+  // latency-bound steps overlap the other's bandwidth-bound flush. Needs the
+  // memory of a second group; without it (or with statistics, host outputs,
+  // host-driven levels or bounds checks, which read each group back in turn)
+  // the groups run one after another on one.
+  bool two = dev_out && !host_loop && !stats && !kBoundsCheck && n_roots > group_lanes;
+  if (two && g->ms2 && g->ms2->words != words) {
+    ms_group_destroy(g->ms2);
+    g->ms2 = nullptr;
+  }
+  if (two && !g->ms_stream2) {
+    if (cudaStreamCreateWithFlags(&g->ms_stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ms_ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ms_ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      two = false;
+    }
+  }
+  if (two && !g->ms2 && ms_group_create(g, g->ms_stream2, words, &g->ms2) != DOBFS_OK) {
+    clear_error();  // not enough memory for a second group: one group it is
+    two = false;
+  }
   g->batch_trace.clear();
   g->last_trace_batch = host_loop;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
+  if (two) {  // the second stream starts after everything queued on s so far
+    DOBFS_CUDA_TRY(cudaEventRecord(g->ms_ev_fork, s));
+    DOBFS_CUDA_TRY(cudaStreamWaitEvent(g->ms_stream2, g->ms_ev_fork, 0));
+  }
   int32_t max_levels = 0;
   int64_t examined = 0, alg_bytes = 0;
   for (int32_t b0 = 0; b0 < n_roots; b0 += group_lanes) {
     const int cnt = (int)std::min<int32_t>(group_lanes, n_roots - b0);
+    const bool odd = two && ((b0 / group_lanes) & 1);
+    MsGroup* m = odd ? g->ms2 : g->ms;
+    m->stream = odd ? g->ms_stream2 : s;
     DOBFS_TRY(ms_group_reset(m, o));
     int32_t lanes[kMsLanes];
     for (int i = 0; i < cnt; ++i) lanes[i] = i;
@@ -1251,6 +1279,10 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
       // the steps' bytes, plus the flush: one 4-byte level per (vertex, lane)
       alg_bytes += c.alg_bytes + 4 * (int64_t)cnt * g->n;
     }
+  }
+  if (two) {  // s waits for the second stream's groups
+    DOBFS_CUDA_TRY(cudaEventRecord(g->ms_ev_join, g->ms_stream2));
+    DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ms_ev_join, 0));
   }
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t1, s));
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_done, s));
