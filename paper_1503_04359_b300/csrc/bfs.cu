@@ -1310,13 +1310,16 @@ void graph_release(dobfs_graph* g) {
   g->last_stream = nullptr;
   ms_group_destroy(g->ms);
   g->ms = nullptr;
-  ms_group_destroy(g->ms2);
-  g->ms2 = nullptr;
-  if (g->ms_stream2) cudaStreamDestroy(g->ms_stream2);
+  for (int k = 0; k < kMsConcurrent - 1; ++k) {
+    ms_group_destroy(g->ms_more[k]);
+    g->ms_more[k] = nullptr;
+    if (g->ms_streams[k]) cudaStreamDestroy(g->ms_streams[k]);
+    if (g->ms_ev_join[k]) cudaEventDestroy(g->ms_ev_join[k]);
+    g->ms_streams[k] = nullptr;
+    g->ms_ev_join[k] = nullptr;
+  }
   if (g->ms_ev_fork) cudaEventDestroy(g->ms_ev_fork);
-  if (g->ms_ev_join) cudaEventDestroy(g->ms_ev_join);
-  g->ms_stream2 = nullptr;
-  g->ms_ev_fork = g->ms_ev_join = nullptr;
+  g->ms_ev_fork = nullptr;
   if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
   if (g->cg) cudaGraphDestroy(g->cg);
   g->cg_exec = nullptr;

@@ -11,6 +11,9 @@ namespace dobfs {
 
 struct MsGroup;
 
+// Lane groups of one batch that run at the same time (on as many streams).
+constexpr int kMsConcurrent = 4;
+
 // Sentinel edge key: a dropped entry (self-loop or duplicate). Sorts last.
 constexpr uint64_t kSentinelKey = ~0ull;
 
@@ -122,9 +125,12 @@ struct dobfs_graph {
 
   // batched runs: one lane group and a staging buffer for host outputs
   dobfs::MsGroup* ms = nullptr;
-  dobfs::MsGroup* ms2 = nullptr;      // a second group, so that two groups of a batch overlap
-  cudaStream_t ms_stream2 = nullptr;  // ... on their own stream
-  cudaEvent_t ms_ev_fork = nullptr, ms_ev_join = nullptr;
+  // more groups, so that the groups of a batch overlap, each further one on
+  // its own stream
+  dobfs::MsGroup* ms_more[dobfs::kMsConcurrent - 1] = {};
+  cudaStream_t ms_streams[dobfs::kMsConcurrent - 1] = {};
+  cudaEvent_t ms_ev_fork = nullptr;
+  cudaEvent_t ms_ev_join[dobfs::kMsConcurrent - 1] = {};
   dobfs::DevBuf ms_stage;
   std::vector<dobfs_level_trace> batch_trace;  // host-driven batch levels (first group)
   bool last_trace_batch = false;

@@ -1181,43 +1181,51 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
   const size_t stage_bytes = sizeof(int32_t) * (size_t)group_lanes * (size_t)g->n;
   if (!dev_out && g->ms_stage.bytes < stage_bytes) DOBFS_TRY(g->ms_stage.alloc(stage_bytes, g->stream));
   const bool host_loop = (o.flags & DOBFS_RUN_HOST_LOOP) != 0;
-  // Batches of several groups with device outputs run two groups at a time,
-  // alternating between two lane groups on two streams: one group's
-  // latency-bound steps overlap the other's bandwidth-bound flush. Needs the
-  // memory of a second group; without it (or with statistics, host outputs,
-  // host-driven levels or bounds checks, which read each group back in turn)
-  // the groups run one after another on one.
-  bool two = dev_out && !host_loop && !stats && !kBoundsCheck && n_roots > group_lanes;
-  if (two && g->ms2 && g->ms2->words != words) {
-    ms_group_destroy(g->ms2);
-    g->ms2 = nullptr;
-  }
-  if (two && !g->ms_stream2) {
-    if (cudaStreamCreateWithFlags(&g->ms_stream2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ms_ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ms_ev_join, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      two = false;
+  // Batches of several groups with device outputs run up to kMsConcurrent
+  // groups at a time, each on its own stream, the groups taken in turn:
+  // one group's latency-bound steps overlap another's bandwidth-bound flush.
+  // A further group is created only while the device keeps at least one
+  // more group's worth of memory free after it (else fewer run at a time);
+  // with statistics, host outputs, host-driven levels or bounds checks,
+  // which read each group back in turn, the groups run one after another.
+  const int n_groups = (int)ceil_div(n_roots, group_lanes);
+  int par = (dev_out && !host_loop && !stats && !kBoundsCheck) ? std::min(n_groups, kMsConcurrent) : 1;
+  for (int k = 0; k + 1 < par; ++k) {
+    if (g->ms_more[k] && g->ms_more[k]->words != words) {
+      ms_group_destroy(g->ms_more[k]);
+      g->ms_more[k] = nullptr;
     }
-  }
-  if (two && !g->ms2 && ms_group_create(g, g->ms_stream2, words, &g->ms2) != DOBFS_OK) {
-    clear_error();  // not enough memory for a second group: one group it is
-    two = false;
+    bool ok = true;
+    if (!g->ms_streams[k])
+      ok = cudaStreamCreateWithFlags(&g->ms_streams[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&g->ms_ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (ok && !g->ms_ev_fork) ok = cudaEventCreateWithFlags(&g->ms_ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && !g->ms_more[k]) {
+      size_t free_b = 0, total_b = 0;
+      ok = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (int64_t)free_b >= 2 * ms_group_bytes(g, words) &&
+           ms_group_create(g, g->ms_streams[k], words, &g->ms_more[k]) == DOBFS_OK;
+    }
+    if (!ok) {  // no memory (or stream) for this group: fewer groups at a time
+      cudaGetLastError();
+      clear_error();
+      par = k + 1;
+      break;
+    }
   }
   g->batch_trace.clear();
   g->last_trace_batch = host_loop;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
-  if (two) {  // the second stream starts after everything queued on s so far
+  if (par > 1) {  // the other streams start after everything queued on s so far
     DOBFS_CUDA_TRY(cudaEventRecord(g->ms_ev_fork, s));
-    DOBFS_CUDA_TRY(cudaStreamWaitEvent(g->ms_stream2, g->ms_ev_fork, 0));
+    for (int k = 0; k + 1 < par; ++k) DOBFS_CUDA_TRY(cudaStreamWaitEvent(g->ms_streams[k], g->ms_ev_fork, 0));
   }
   int32_t max_levels = 0;
   int64_t examined = 0, alg_bytes = 0;
   for (int32_t b0 = 0; b0 < n_roots; b0 += group_lanes) {
     const int cnt = (int)std::min<int32_t>(group_lanes, n_roots - b0);
-    const bool odd = two && ((b0 / group_lanes) & 1);
-    MsGroup* m = odd ? g->ms2 : g->ms;
-    m->stream = odd ? g->ms_stream2 : s;
+    const int slot = (b0 / group_lanes) % par;
+    MsGroup* m = slot ? g->ms_more[slot - 1] : g->ms;
+    m->stream = slot ? g->ms_streams[slot - 1] : s;
     DOBFS_TRY(ms_group_reset(m, o));
     int32_t lanes[kMsLanes];
     for (int i = 0; i < cnt; ++i) lanes[i] = i;
@@ -1280,9 +1288,9 @@ extern "C" int dobfs_run_batch(dobfs_graph* g, const int32_t* roots, int32_t n_r
       alg_bytes += c.alg_bytes + 4 * (int64_t)cnt * g->n;
     }
   }
-  if (two) {  // s waits for the second stream's groups
-    DOBFS_CUDA_TRY(cudaEventRecord(g->ms_ev_join, g->ms_stream2));
-    DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ms_ev_join, 0));
+  for (int k = 0; k + 1 < par; ++k) {  // s waits for the other streams' groups
+    DOBFS_CUDA_TRY(cudaEventRecord(g->ms_ev_join[k], g->ms_streams[k]));
+    DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ms_ev_join[k], 0));
   }
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t1, s));
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_done, s));
