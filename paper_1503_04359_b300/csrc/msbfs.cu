@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
 // the frontier masks of its first bu_scan neighbours and stops once every
 // missing lane is found; longer rows continue in k_ms_bu_long with the
 // partial mask kept in next[v].
+// (at most 64 registers: 32 resident warps per SM at any block size)
 template <class OffT, int W, int NT>
-__global__ void __launch_bounds__(NT) k_ms_bu(MsArgs<OffT> A) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
   __shared__ unsigned long long sh[NT / 32];
   __shared__ int64_t s_tab[2 * kSmallDeg];
   if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
