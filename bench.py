@@ -110,7 +110,7 @@ def _dist():
 
 KERNEL_SOURCES = ("paper_1503_04359_b300/csrc/bfs.cu", "paper_1503_04359_b300/csrc/graph.cuh",
                   "paper_1503_04359_b300/csrc/common.cuh")
-TRAFFIC_PROFILE = "profiles/bu_step_rmat_s25.md"
+TRAFFIC_PROFILE = "profiles/bu_step_rmat_s24.md"
 STEP_NAMES = {0: "top-down", 1: "bottom-up", 2: "mixed"}
 STEP_KERNELS = {0: "top-down step (k_td_bin + k_td_chunks [+ k_bu parent search])",
                 1: "bottom-up step (k_bu + k_bu_long)",
