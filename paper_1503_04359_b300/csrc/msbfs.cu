@@ -42,7 +42,7 @@ constexpr int kMsChunk = 1024;  // top-down chunk record length (default; a run 
 constexpr int kMsT = 32;        // bottom-up entries per thread before a row continues warp-wide (default)
 constexpr int kMsChunkMin = 256;
 constexpr int kMsLongChunk = 4096;  // entries of a long bottom-up row per warp (chunk record)
-constexpr int kMsCases = 2;
+constexpr int kMsCases = 3;
 constexpr int kMsCaseNone = 7;
 constexpr unsigned kIterMask = (1u << kMsPlanes) - 1u;
 constexpr int kFirstPlanes = 4;  // planes cleared by a reset: iterations below 16
@@ -60,6 +60,7 @@ struct MsArgs {
   int2* rec;
   int32_t* def;
   MsCtl* ctl;
+  MsLaneStats* ls;
   const int64_t* small_tab;  // [2 * kSmallDeg]: row offset and first ID of each small degree (renumbered graphs)
   int32_t small_deg;         // degrees below this use small_tab for the row start (0: none)
   int64_t n, nnz, n_cand, rec_cap;
@@ -248,6 +249,11 @@ __global__ void k_ms_seed(MsArgs<OffT> A, SeedArgs S) {
         atomicOr(reinterpret_cast<unsigned long long*>(A.planes + (int64_t)b * A.n * W + (int64_t)r * W + w), bit);
     atomicOr(&c->active[w], bit);
     atomicOr(&c->live[w], bit);
+    // a lane starts top-down, also when it joins after the switch chose this
+    // step's directions (the server then runs both kinds of step)
+    atomicAnd(&c->lane_bu[w], ~bit);
+    atomicOr(&c->td_mask[w], bit);
+    atomicAnd(&c->bu_mask[w], ~bit);
     bool first = true;
     for (int j = 0; j < i && first; ++j) first = S.root[j] != S.root[i];
     if (first) {
@@ -269,9 +275,10 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   MsCtl* c = A.ctl;
   if (!c->fresh) {
-    const int64_t act = c->dir == 0 ? c->n_f : (int64_t)c->nx_act;
+    // active vertices: the frontier vertices pushed top-down and the vertices searched bottom-up
+    const int64_t act = (int64_t)c->nx_tdact + (int64_t)c->nx_act;
     c->alg_bytes += 16 * W * act + (8 * W + 4) * (int64_t)c->nx_examined;
-    c->nx_act = 0;
+    c->nx_act = c->nx_tdact = 0;
     c->n_f_prev = c->n_f;
     c->n_f = (int64_t)c->nx_n;
     c->m_f = (int64_t)c->nx_m;
@@ -299,18 +306,50 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
   const bool done = (any_live == 0 || c->n_f == 0 || runaway);
   if (done)
     for (int w = 0; w < W; ++w) c->live[w] = 0;
-  int dir;
-  switch (c->mode) {
-    case DOBFS_DIR_TOPDOWN: dir = 0; break;
-    case DOBFS_DIR_BOTTOMUP: dir = 1; break;
-    case DOBFS_DIR_RANDOM: dir = (int)(gen_mix64(c->sched_seed ^ (uint64_t)c->iter) & 1ull); break;
-    default:
-      if (prev_dir == 0)
-        dir = (c->m_f * (int64_t)c->alpha > c->m_u) ? 1 : 0;
-      else
-        dir = (c->n_f * (int64_t)c->beta < A.n && c->n_f < c->n_f_prev) ? 0 : 1;
-      break;
+  // direction by lane: a top-down lane turns bottom-up by the alpha rule on
+  // its own (sampled) frontier statistics, so that lanes whose frontier is
+  // still small push it top-down while the others search bottom-up in the
+  // same step (a bottom-up search for a lane with a small frontier scans
+  // whole rows); bottom-up lanes return to top-down together, by the beta
+  // rule on the union of the frontiers (late levels stay one kind of step)
+  (void)prev_dir;
+  unsigned long long was_any_bu = 0;
+  for (int w = 0; w < W; ++w) was_any_bu |= c->lane_bu[w] & c->live[w];
+  const bool union_to_td = was_any_bu && c->n_f * (int64_t)c->beta < A.n && c->n_f < c->n_f_prev;
+  unsigned long long bu[kMsMaxWords] = {};
+  for (int w = 0; w < W; ++w) {
+    const unsigned long long lv = c->live[w];
+    switch (c->mode) {
+      case DOBFS_DIR_TOPDOWN: bu[w] = 0; break;
+      case DOBFS_DIR_BOTTOMUP: bu[w] = lv; break;
+      case DOBFS_DIR_RANDOM:  // a seeded coin per lane and step
+        bu[w] = lv & gen_mix64(c->sched_seed ^ ((uint64_t)c->iter << 1) ^ ((uint64_t)w << 40));
+        break;
+      default:
+        for (unsigned long long x = lv; x; x &= x - 1) {
+          const int b = __ffsll((long long)x) - 1, l = w * kMsWordLanes + b;
+          const int64_t mf = (int64_t)A.ls->m_f[l] * kMsLaneSample;
+          const int64_t mu = (int64_t)A.ls->m_u[l] * kMsLaneSample;
+          const bool was_bu = (c->lane_bu[w] >> b) & 1ull;
+          const bool to_bu = was_bu ? !union_to_td : (mf * (int64_t)c->alpha > mu);
+          if (to_bu) bu[w] |= 1ull << b;
+        }
+        break;
+    }
   }
+  bool any_td = false, any_bu = false;
+  for (int l = 0; l < kMsLanes; ++l) {  // statistics of this step become the previous ones
+    A.ls->n_f_prev[l] = A.ls->n_f[l];
+    A.ls->n_f[l] = A.ls->m_f[l] = A.ls->m_u[l] = 0;
+  }
+  for (int w = 0; w < W; ++w) {
+    c->bu_mask[w] = bu[w];
+    c->td_mask[w] = c->live[w] & ~bu[w];
+    c->lane_bu[w] = (c->lane_bu[w] & ~c->live[w]) | bu[w];
+    any_td |= c->td_mask[w] != 0;
+    any_bu |= bu[w] != 0;
+  }
+  const int dir = (any_td && any_bu) ? 2 : (any_bu ? 1 : 0);
   // the planes needed by iteration t+1 must be clean: clear the next one the
   // first time t+1 reaches it
   const unsigned tn = (unsigned)(c->iter + 1) & kIterMask;
@@ -330,6 +369,75 @@ __global__ void k_ms_switch(MsArgs<OffT> A, cudaGraphConditionalHandle h_while, 
       cudaGraphSetConditional(h_case, (unsigned)dir);
     }
   }
+}
+
+// Per-lane frontier statistics for the direction switch (auto policy only),
+// sampled from every kMsLaneSample-th block of 32 candidate vertices: for each
+// lane, the sampled vertices in its frontier, their degree sum, and the
+// degree sum of the sampled vertices it has not reached. Runs just before the
+// switch, so the frontier is what the step before wrote (or the seeds). Skips
+// the work while every lane is top-down and the rule on the union of the
+// lanes says top-down: no single lane's rule can then say bottom-up (a lane's
+// frontier is part of the union's, and its unreached part holds the union's).
+template <class OffT, int W>
+__global__ void __launch_bounds__(kThreads) k_ms_lane_stats(MsArgs<OffT> A) {
+  const MsCtl* c = A.ctl;
+  if (c->mode != DOBFS_DIR_AUTO) return;
+  const int64_t m_f = c->fresh ? c->m_f : (int64_t)c->nx_m;
+  const int64_t m_u = c->fresh ? c->m_u : c->m_u - (int64_t)c->nx_mu;
+  unsigned long long any_bu = 0;
+  for (int w = 0; w < W; ++w) any_bu |= c->lane_bu[w] & c->live[w];
+  if (!any_bu && m_f * (int64_t)c->alpha <= m_u) return;
+  __shared__ unsigned long long s_n[kMsWordLanes * W], s_m[kMsWordLanes * W], s_u[kMsWordLanes * W];
+  for (int i = threadIdx.x; i < kMsWordLanes * W; i += blockDim.x) s_n[i] = s_m[i] = s_u[i] = 0;
+  __syncthreads();
+  // the frontier of the step about to be chosen (the switch that follows
+  // advances the iteration unless no step ran since the seeds)
+  const bool at_seed = c->fresh != 0;
+  const uint64_t* front = (((c->iter & 1) != 0) == at_seed) ? A.fb1 : A.fb0;
+  const unsigned lane = lane_id();
+  const int64_t rounds = ceil_div(A.n_cand, 32);
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t r = gw * kMsLaneSample; r < rounds; r += warps * kMsLaneSample) {
+    const int64_t v = r * 32 + lane;
+    const bool in = v < A.n_cand;
+    const Lanes<W> f = in ? ldg_lanes<W>(front, v) : zero_lanes<W>();
+    const Lanes<W> sn = in ? ldg_lanes<W>(A.seen, v) : zero_lanes<W>();
+    const unsigned d = in ? (unsigned)min(__ldg(&A.firstdeg[v].y), 1 << 26) : 0u;  // 32 of them fit 32 bits
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll 4
+      for (int b = 0; b < kMsWordLanes; ++b) {
+        const bool fb = (f.w[w] >> b) & 1ull;
+        const bool ub = in && !((sn.w[w] >> b) & 1ull);
+        const unsigned cf = __ballot_sync(0xffffffffu, fb);
+        const unsigned mf = __reduce_add_sync(0xffffffffu, fb ? d : 0u);
+        const unsigned mu = __reduce_add_sync(0xffffffffu, ub ? d : 0u);
+        if (lane == 0) {
+          const int l = w * kMsWordLanes + b;
+          if (cf) {
+            atomicAdd(&s_n[l], (unsigned long long)__popc(cf));
+            atomicAdd(&s_m[l], (unsigned long long)mf);
+          }
+          if (mu) atomicAdd(&s_u[l], (unsigned long long)mu);
+        }
+      }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMsWordLanes * W; i += blockDim.x) {
+    if (s_n[i]) atomicAdd(&A.ls->n_f[i], s_n[i]);
+    if (s_m[i]) atomicAdd(&A.ls->m_f[i], s_m[i]);
+    if (s_u[i]) atomicAdd(&A.ls->m_u[i], s_u[i]);
+  }
+}
+
+// Between the top-down and bottom-up halves of a step with lanes of both
+// directions: the chunk records of the top-down push are done with, and the
+// bottom-up search counts its own from zero.
+template <class OffT, int W>
+__global__ void k_ms_reset_records(MsArgs<OffT> A) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) A.ctl->n_rec = 0;
 }
 
 // Restarts the iteration count of a group none of whose lanes holds a query.
@@ -368,10 +476,14 @@ __global__ void k_ms_clear_next(MsArgs<OffT> A) {
 // Top-down, part 1: chunk records for the rows of the frontier vertices.
 template <class OffT, int W>
 __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
+  __shared__ unsigned long long sh[kThreads / 32];
   const uint64_t* front = (A.ctl->iter & 1) ? A.fb1 : A.fb0;
   const int64_t chunk = A.ctl->td_chunk;
+  const Lanes<W> tdm = ctl_lanes<W>(A.ctl->td_mask);  // lanes expanded top-down
+  unsigned long long act = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
-    if (!any(ld_lanes<W>(front, v))) continue;
+    if (!any(and_(ld_lanes<W>(front, v), tdm))) continue;
+    act += 1;
     const int64_t d = (int64_t)A.off[v + 1] - (int64_t)A.off[v];
     if (d == 0) continue;
     const unsigned nch = (unsigned)ceil_div(d, chunk);
@@ -379,6 +491,8 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_list(MsArgs<OffT> A) {
     if ((int64_t)base + nch > A.rec_cap) continue;  // cannot happen: one record per kMsChunkMin entries or vertex
     for (unsigned k = 0; k < nch; ++k) A.rec[base + k] = make_int2((int32_t)v, (int32_t)k);
   }
+  act = block_sum_u64(act, sh);
+  if (threadIdx.x == 0 && act) atomicAdd(&A.ctl->nx_tdact, act);
 }
 
 // Top-down, part 2: one warp per record pushes front[u] to the unseen lanes
@@ -397,7 +511,7 @@ __global__ void __launch_bounds__(NT) k_ms_td(MsArgs<OffT> A) {
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrec; r += warps) {
     const int2 rc = A.rec[r];
     const int32_t u = bc_vid(rc.x, A.n, &A.ctl->bc_site, kBcMsRecord);
-    const Lanes<W> fu = ld_lanes<W>(front, u);
+    const Lanes<W> fu = and_(ld_lanes<W>(front, u), ctl_lanes<W>(c->td_mask));
     int64_t ro = (int64_t)A.off[u], re = (int64_t)A.off[u + 1];
     bc_row(ro, re, A.nnz, &A.ctl->bc_site, kBcMsRow);
     const int64_t s = ro + (int64_t)rc.y * chunk;
@@ -497,16 +611,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
   MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
-  const Lanes<W> live = ctl_lanes<W>(c->live);
+  const Lanes<W> bum = ctl_lanes<W>(c->bu_mask);  // lanes searched bottom-up
+  // a step with lanes of both directions: next already holds the top-down
+  // lanes' pushes, which this pass records with its own finds
+  const bool merge = c->step_case == 2;
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
   const int64_t scan = c->bu_scan;
   MsCount<W> k;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < A.n_cand; v += (int64_t)gridDim.x * blockDim.x) {
     const Lanes<W> s = ld_lanes<W>(A.seen, v);
-    const Lanes<W> need = and_not(live, s);
+    const Lanes<W> need = and_not(bum, s);
+    const Lanes<W> pushed = merge ? and_not(ld_lanes<W>(next, v), s) : zero_lanes<W>();
     if (!any(need)) {
-      st_lanes<W>(next, v, zero_lanes<W>());
+      st_lanes<W>(next, v, pushed);
+      if (any(pushed)) ms_found<W>(A, v, s, pushed, A.firstdeg[v].y, T, np, k);
       continue;
     }
     k.act += 1;
@@ -533,10 +652,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
       }
     }
     k.ex += (unsigned long long)j;
-    const Lanes<W> nw = and_(acc, need);
+    Lanes<W> nw = and_(acc, need);
     if (!covers(nw, need) && fd.y > scan) {
       // partial: k_ms_bu_long scans the rest of the row in chunk records,
       // k_ms_bu_fin then records the vertex
+      or_into(nw, pushed);
       st_lanes<W>(next, v, nw);
       enqueue_ms(&c->n_def, A.def, (int32_t)v, A.n, &c->bc_site);
       if ((int64_t)fd.y - scan > kMsLongChunk) {  // chunks after the first go to chunk records
@@ -547,6 +667,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
       }
       continue;
     }
+    or_into(nw, pushed);
     st_lanes<W>(next, v, nw);
     if (!any(nw)) continue;
     ms_found<W>(A, v, s, nw, fd.y, T, np, k);
@@ -567,7 +688,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
   MsCtl* c = A.ctl;
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
-  const Lanes<W> live = ctl_lanes<W>(c->live);
+  const Lanes<W> bum = ctl_lanes<W>(c->bu_mask);  // lanes searched bottom-up
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
   const int64_t nd = c->n_def;
   const int64_t scan = c->bu_scan;
@@ -591,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_bu_long(MsArgs<OffT> A) {
       s0 = o + scan + (int64_t)rc.y * kMsLongChunk;
       e0 = min(e, s0 + kMsLongChunk);
     }
-    const Lanes<W> need = and_not(live, ld_lanes<W>(A.seen, v));
+    const Lanes<W> need = and_not(bum, ld_lanes<W>(A.seen, v));
     Lanes<W> acc = ldcg_lanes<W>(next, v);
     int step = 0;
     for (int64_t base = s0 & ~3ll; base < e0 && !covers(acc, need); base += 128, ++step) {
@@ -821,6 +942,7 @@ MsArgs<OffT> ms_args(MsGroup* m) {
   A.rec = m->rec.as<int2>();
   A.def = m->def.as<int32_t>();
   A.ctl = m->ctl.as<MsCtl>();
+  A.ls = m->lstats.as<MsLaneStats>();
   A.small_tab = g->degge.as<int64_t>() + 33;
   A.small_deg = g->small_deg;
   A.n = g->n;
@@ -847,20 +969,28 @@ template <class OffT, int W>
 int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   const int G = ms_grid();
-  const int t = kase == 0 ? m->td_threads : m->bu_threads;
-  auto main_step = [&]() {
-    if (t == 128) ms_main_t<OffT, W, 128>(A, kase, s);
-    else if (t == 512) ms_main_t<OffT, W, 512>(A, kase, s);
-    else ms_main_t<OffT, W, 256>(A, kase, s);
+  auto main_step = [&](int part) {  // part 0: top-down push, 1: bottom-up search
+    const int t = part == 0 ? m->td_threads : m->bu_threads;
+    if (t == 128) ms_main_t<OffT, W, 128>(A, part, s);
+    else if (t == 512) ms_main_t<OffT, W, 512>(A, part, s);
+    else ms_main_t<OffT, W, 256>(A, part, s);
   };
   k_ms_clear_plane<OffT, W><<<G, kThreads, 0, s>>>(A);
   if (kase == 0) {
     k_ms_clear_next<OffT, W><<<G, kThreads, 0, s>>>(A);
     k_ms_td_list<OffT, W><<<G, kThreads, 0, s>>>(A);
-    main_step();
+    main_step(0);
     k_ms_td_post<OffT, W><<<G, kThreads, 0, s>>>(A);
-  } else {
-    main_step();
+  } else if (kase == 1) {
+    main_step(1);
+    k_ms_bu_long<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_bu_fin<OffT, W><<<G, kThreads, 0, s>>>(A);
+  } else {  // top-down lanes pushed, then the bottom-up lanes searched and both recorded
+    k_ms_clear_next<OffT, W><<<G, kThreads, 0, s>>>(A);
+    k_ms_td_list<OffT, W><<<G, kThreads, 0, s>>>(A);
+    main_step(0);
+    k_ms_reset_records<OffT, W><<<1, 32, 0, s>>>(A);
+    main_step(1);
     k_ms_bu_long<OffT, W><<<G, kThreads, 0, s>>>(A);
     k_ms_bu_fin<OffT, W><<<G, kThreads, 0, s>>>(A);
   }
@@ -896,14 +1026,22 @@ int ms_build_graph(MsGroup* m) {
     return fail(set_error(DOBFS_ERR_CUDA, "conditional handle failed"));
   if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return fail(set_error(DOBFS_ERR_CUDA, "capture failed"));
+  k_ms_lane_stats<OffT, W><<<ms_grid(1), kThreads, 0, cs>>>(A);
   k_ms_switch<OffT, W><<<1, 32, 0, cs>>>(A, h_while, h_case, 1);
   cudaGraph_t captured = nullptr;
   if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) return fail(set_error(DOBFS_ERR_CUDA, "end capture failed"));
+  // the switch node (the one without a successor) is followed by the step's switch node
   size_t nn = 0;
   cudaGraphGetNodes(body, nullptr, &nn);
-  if (nn != 1) return fail(set_error(DOBFS_ERR_CUDA, "unexpected body node count %zu", nn));
-  cudaGraphNode_t sw;
-  cudaGraphGetNodes(body, &sw, &nn);
+  if (nn != 2) return fail(set_error(DOBFS_ERR_CUDA, "unexpected body node count %zu", nn));
+  cudaGraphNode_t bn[2];
+  cudaGraphGetNodes(body, bn, &nn);
+  cudaGraphNode_t sw = bn[1];
+  for (int i = 0; i < 2; ++i) {
+    size_t ndep = 0;
+    cudaGraphNodeGetDependentNodes(bn[i], nullptr, nullptr, &ndep);
+    if (ndep == 0) sw = bn[i];
+  }
   cudaGraphNodeParams sp = {};
   sp.type = cudaGraphNodeTypeConditional;
   sp.conditional.handle = h_case;
@@ -940,6 +1078,7 @@ int ms_seed_impl(MsGroup* m, const SeedArgs& S) {
 template <class OffT, int W>
 int ms_step_impl(MsGroup* m, MsCtl* after_switch, float* case_ms) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
+  k_ms_lane_stats<OffT, W><<<ms_grid(1), kThreads, 0, m->stream>>>(A);
   k_ms_switch<OffT, W><<<1, 32, 0, m->stream>>>(A, 0, 0, 0);
   MsCtl c;
   DOBFS_CUDA_TRY(cudaMemcpyAsync(&c, m->ctl.ptr, sizeof(c), cudaMemcpyDeviceToHost, m->stream));
@@ -979,6 +1118,7 @@ int ms_flush_impl(MsGroup* m, const FlushArgs& F) {
 
 template <class OffT, int W>
 int ms_switch_async_impl(MsGroup* m, MsCtl* dst) {
+  k_ms_lane_stats<OffT, W><<<ms_grid(1), kThreads, 0, m->stream>>>(ms_args<OffT>(m));
   k_ms_switch<OffT, W><<<1, 32, 0, m->stream>>>(ms_args<OffT>(m), 0, 0, 0);
   DOBFS_CUDA_TRY(cudaGetLastError());
   DOBFS_CUDA_TRY(cudaMemcpyAsync(dst, m->ctl.ptr, sizeof(MsCtl), cudaMemcpyDeviceToHost, m->stream));
@@ -1007,7 +1147,7 @@ int64_t ms_group_bytes(const dobfs_graph* g, int words) {
   const int64_t n_cand = g->reindexed ? std::max<int64_t>(g->n_nonisolated, 1) : g->n;
   return (int64_t)sizeof(uint64_t) * g->n * words * (3 + kMsPlanes) +
          (int64_t)sizeof(int2) * (n_cand + g->nnz / kMsChunkMin + 64) + (int64_t)sizeof(int32_t) * g->n +
-         (int64_t)sizeof(MsCtl);
+         (int64_t)sizeof(MsCtl) + (int64_t)sizeof(MsLaneStats);
 }
 
 int ms_group_create(dobfs_graph* g, cudaStream_t s, int words, MsGroup** out) {
@@ -1027,6 +1167,7 @@ int ms_group_create(dobfs_graph* g, cudaStream_t s, int words, MsGroup** out) {
   if (rc == DOBFS_OK) rc = m->rec.alloc(sizeof(int2) * (size_t)m->rec_cap, s);
   if (rc == DOBFS_OK) rc = m->def.alloc(sizeof(int32_t) * (size_t)g->n, s);
   if (rc == DOBFS_OK) rc = m->ctl.alloc(sizeof(MsCtl), s);
+  if (rc == DOBFS_OK) rc = m->lstats.alloc(sizeof(MsLaneStats), s);
   if (rc != DOBFS_OK) {
     delete m;
     return rc;
@@ -1051,6 +1192,7 @@ int ms_group_reset(MsGroup* m, const dobfs_run_opts& o) {
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->fb1.ptr, 0, vb, s));
   // iterations below 16 need kFirstPlanes planes; later planes are cleared on first use
   DOBFS_CUDA_TRY(cudaMemsetAsync(m->planes.ptr, 0, vb * kFirstPlanes, s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(m->lstats.ptr, 0, sizeof(MsLaneStats), s));
   MsCtl c;
   memset(&c, 0, sizeof(c));
   c.fresh = 1;

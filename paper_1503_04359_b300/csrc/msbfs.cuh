@@ -30,6 +30,16 @@ inline int first_lane(LaneMask m) {  // m != 0
   return lo ? __builtin_ctzll(lo) : kMsWordLanes + __builtin_ctzll((uint64_t)(m >> kMsWordLanes));
 }
 
+// Per-lane frontier statistics of a lane group, sampled from every
+// kMsLaneSample-th block of 32 vertices (estimates; they choose directions
+// only, never results): vertices in the lane's frontier, their degree sum,
+// the degree sum of the vertices the lane has not reached.
+constexpr int kMsLaneSample = 64;
+struct MsLaneStats {
+  unsigned long long n_f[kMsLanes], m_f[kMsLanes], m_u[kMsLanes];
+  unsigned long long n_f_prev[kMsLanes];
+};
+
 // Device control block of a lane group.
 struct MsCtl {
   int32_t iter;          // iteration t: the frontier holds the vertices found at iteration t
@@ -46,6 +56,11 @@ struct MsCtl {
   // accumulators of the running step
   unsigned long long nx_n, nx_m, nx_mu, nx_examined;
   unsigned long long nx_act;   // bottom-up: vertices still missing live lanes (searched)
+  unsigned long long nx_tdact; // top-down: frontier vertices whose rows were pushed
+  // directions by lane: the running step expands the lanes of td_mask
+  // top-down and those of bu_mask bottom-up (step_case 2 when both are
+  // non-empty); lane_bu holds the lanes whose last step was bottom-up
+  unsigned long long td_mask[kMsMaxWords], bu_mask[kMsMaxWords], lane_bu[kMsMaxWords];
   unsigned long long nx_live[kMsMaxWords];
   unsigned int n_rec, n_def;
   // parameters
@@ -73,6 +88,7 @@ struct MsGroup {
   int64_t rec_cap = 0;
   DevBuf def;             // int32[n]: bottom-up rows continued warp-wide
   DevBuf ctl;             // MsCtl
+  DevBuf lstats;          // MsLaneStats
   DevBuf args;            // device copy of seeding arguments
   cudaGraph_t cg = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -106,7 +122,8 @@ int ms_group_flush(MsGroup* m, LaneMask lanes, int32_t* const* out, const int32_
 
 // Server loop pieces, all asynchronous on the group's stream: the direction
 // switch followed by a copy of the control block into `dst` (pinned host
-// memory), and the kernels of one step (0 top-down, 1 bottom-up).
+// memory), and the kernels of one step (0 top-down, 1 bottom-up, 2 both:
+// some lanes top-down, the others bottom-up).
 int ms_group_switch_async(MsGroup* m, MsCtl* dst);
 int ms_group_case_async(MsGroup* m, int kase);
 
