@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_td_post(MsArgs<OffT> A) {
 // partial mask kept in next[v].
 // (at most 64 registers: 32 resident warps per SM at any block size)
 template <class OffT, int W, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A, int merge) {
   __shared__ unsigned long long sh[NT / 32];
   __shared__ int64_t s_tab[2 * kSmallDeg];
   if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
@@ -612,9 +612,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_ms_bu(MsArgs<OffT> A) {
   const uint64_t* front = (c->iter & 1) ? A.fb1 : A.fb0;
   uint64_t* next = (c->iter & 1) ? A.fb0 : A.fb1;
   const Lanes<W> bum = ctl_lanes<W>(c->bu_mask);  // lanes searched bottom-up
-  // a step with lanes of both directions: next already holds the top-down
-  // lanes' pushes, which this pass records with its own finds
-  const bool merge = c->step_case == 2;
+  // merge (a step with lanes of both directions): next already holds the
+  // top-down lanes' pushes, which this pass records with its own finds
   const unsigned T = (unsigned)(c->iter + 1) & kIterMask;
   const int np = c->n_planes;
   const int64_t scan = c->bu_scan;
@@ -957,23 +956,26 @@ int ms_grid(int per_sm = 8) { return sm_count() * per_sm; }
 // The main kernel of a step (top-down push or bottom-up search) with T
 // threads per block, as many threads per SM as the others.
 template <class OffT, int W, int NT>
-void ms_main_t(const MsArgs<OffT>& A, int kase, cudaStream_t s) {
+void ms_main_t(const MsArgs<OffT>& A, int part, int merge, cudaStream_t s) {
   const int G = ms_grid(8 * kThreads / NT);
-  if (kase == 0)
+  if (part == 0)
     k_ms_td<OffT, W, NT><<<G, NT, 0, s>>>(A);
   else
-    k_ms_bu<OffT, W, NT><<<G, NT, 0, s>>>(A);
+    k_ms_bu<OffT, W, NT><<<G, NT, 0, s>>>(A, merge);
 }
 
 template <class OffT, int W>
 int ms_launch_case(MsGroup* m, int kase, cudaStream_t s) {
   const MsArgs<OffT> A = ms_args<OffT>(m);
   const int G = ms_grid();
-  auto main_step = [&](int part) {  // part 0: top-down push, 1: bottom-up search
+  // part 0: top-down push, 1: bottom-up search (which records the pushes too
+  // in a step of both kinds)
+  auto main_step = [&](int part) {
     const int t = part == 0 ? m->td_threads : m->bu_threads;
-    if (t == 128) ms_main_t<OffT, W, 128>(A, part, s);
-    else if (t == 512) ms_main_t<OffT, W, 512>(A, part, s);
-    else ms_main_t<OffT, W, 256>(A, part, s);
+    const int merge = kase == 2 ? 1 : 0;
+    if (t == 128) ms_main_t<OffT, W, 128>(A, part, merge, s);
+    else if (t == 512) ms_main_t<OffT, W, 512>(A, part, merge, s);
+    else ms_main_t<OffT, W, 256>(A, part, merge, s);
   };
   k_ms_clear_plane<OffT, W><<<G, kThreads, 0, s>>>(A);
   if (kase == 0) {

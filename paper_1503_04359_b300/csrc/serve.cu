@@ -355,7 +355,9 @@ bool schedule_once(dobfs_server* S) {
       }
       if (live || k) {
         S->group_steps += 1;
-        if (ms_group_case_async(G->ms, c.step_case) != DOBFS_OK) {
+        // lanes seeded after the switch start top-down: a bottom-up step they
+        // join runs as a step of both kinds
+        if (ms_group_case_async(G->ms, (k && c.step_case == 1) ? 2 : c.step_case) != DOBFS_OK) {
           fail_all(S, DOBFS_ERR_CUDA, dobfs_last_error());
           return false;
         }

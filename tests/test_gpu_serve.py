@@ -157,3 +157,30 @@ def test_serve_errors(d, graphs):
             d.dobfs_serve_poll(srv, 123456)
     finally:
         d.dobfs_serve_destroy(srv)
+
+
+@pytest.mark.parametrize("direction", [2, 3])  # every step bottom-up; a seeded coin per lane and step
+def test_lanes_join_bottom_up_steps(d, graphs, direction):
+    """Lanes that join a group between steps start top-down: when the step
+    chosen for the running lanes is bottom-up, the server runs it as a step
+    of both kinds (the new lanes pushed top-down, the others searched
+    bottom-up). Queries join at any level here, one at a time, into groups
+    whose steps are bottom-up or mixed; every result is bit-exact."""
+    g, og, roots, ref = graphs[2]
+    srv = d.dobfs_serve_create(d.make_serve_opts(direction=direction, join_window=1000, admit_div=0, gather_us=0,
+                                                 ss_max=0, flush_delay=0))
+    try:
+        gid = d.dobfs_serve_add_graph(srv, g.handle)
+        outs, tickets = [], []
+        for k in range(48):
+            out = torch.full((og.n,), 9, dtype=torch.int32, device="cuda")
+            outs.append(out)
+            tickets.append(d.dobfs_serve_submit(srv, gid, int(roots[k]), out))
+            time.sleep(0.0002 * (k % 7))
+        for t in tickets:
+            _wait(d, srv, t)
+        for k, out in enumerate(outs):
+            np.testing.assert_array_equal(out.cpu().numpy(), ref[k])
+        assert d.dobfs_serve_get_stats(srv).cohorts < 48  # some queries joined running groups
+    finally:
+        d.dobfs_serve_destroy(srv)
