@@ -978,12 +978,30 @@ Grids grids() {
   return G;
 }
 
+// The grids of graph g: a full wave of resident blocks, or fewer where g is
+// too small to give every block work (the frontier, the records, the
+// bitmap words and the long rows of g bound each kernel's work), so that a
+// level of a small graph does not launch hundreds of idle blocks.
+template <class OffT, int TB, int TT>
+Grids graph_grids(const dobfs_graph* g) {
+  Grids G = grids<OffT, TB, TT>();
+  auto cap = [](int grid, int64_t blocks) { return (int)std::max<int64_t>(1, std::min<int64_t>(grid, blocks)); };
+  const int64_t cand_words = g->reindexed ? ceil_div(std::max<int64_t>(g->n_nonisolated, 1), 32) : g->words;
+  const int64_t n_front = std::max<int64_t>(g->n_nonisolated, 1);  // frontier vertices (the root counts)
+  G.td_bin = cap(G.td_bin, ceil_div(n_front, TT));
+  G.td_chunks = cap(G.td_chunks, ceil_div(g->rec_cap, TT / 32));
+  G.conv = cap(G.conv, ceil_div(std::max(g->words, n_front), kThreads));
+  G.bu = cap(G.bu, ceil_div(ceil_div(cand_words, 32), TB / 32));
+  G.bu_long = cap(G.bu_long, ceil_div(std::max<int64_t>(g->deg_ge[1], 1), kThreads / 32));  // rows of >= 2 entries
+  return G;
+}
+
 // Enqueues the kernels of step kind `kase` on s (used both for graph capture
 // and for host-driven levels).
 template <class OffT, int TB, int TT>
 int launch_case_t(dobfs_graph* g, const BfsArgs<OffT>& A, int kase, cudaStream_t s, cudaEvent_t main_begin,
                   cudaEvent_t main_end) {
-  const Grids G = grids<OffT, TB, TT>();
+  const Grids G = graph_grids<OffT, TB, TT>(g);
   const size_t bm_bytes = sizeof(uint32_t) * (size_t)g->words;
   switch (kase) {
     case 0:
