@@ -211,6 +211,10 @@ int dobfs_graph_load(const char* path, uint32_t flags, void* stream, dobfs_graph
 #define DOBFS_RUN_HOST_LOOP 0x2u        /* drive levels from the host and time every kernel
                                            (diagnostics; adds one host round trip per level) */
 #define DOBFS_RUN_SYNC_STATS 0x4u       /* wait for completion and fill *stats */
+#define DOBFS_RUN_LEVEL_GRAPH 0x8u      /* run the level loop as the CUDA graph also for a small
+                                           graph (by default a graph with at most 2^20 vertices
+                                           that have edges and 2^26 stored entries runs all its
+                                           levels in one cooperative kernel; same results) */
 
 typedef struct {
   int32_t direction;        /* DOBFS_DIR_* */
@@ -289,9 +293,12 @@ int dobfs_run(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_
  * DOBFS_ERR_TIMEOUT if it is still running at the limit (nothing is
  * cancelled: it completes later, and a later wait returns DOBFS_OK),
  * DOBFS_ERR_CUDA if it failed, DOBFS_ERR_INVALID for a NULL graph. The
- * graph must not be destroyed during the wait. The library's kernels never
- * wait on one another: the level loop is a CUDA graph whose conditional nodes
- * end it on the device, so host waits are the only waits there are.
+ * graph must not be destroyed during the wait. No kernel of the library
+ * waits for another kernel: the level loop is a CUDA graph whose conditional
+ * nodes end it on the device, or, for a small graph, one cooperative kernel
+ * whose blocks (all resident at once) meet at grid barriers, each wait there
+ * bounded by 2 s (a wait that runs out fails the run with DOBFS_ERR_CUDA
+ * when its stats are read).
  */
 int dobfs_graph_wait(dobfs_graph* g, int32_t timeout_ms);
 

@@ -81,12 +81,31 @@ struct BfsArgs {
   int2* rec;
   int32_t* def;
   BfsCtl* ctl;
+  uint32_t* gbar;  // grid barrier of the fused loop: arrivals, generation, timed-out flag
   LevelRec* trace;
   int64_t n, nnz, words, cand_words, rec_cap, n_nonisolated;
 };
 
+// Loads of data that the level loop writes (bitmaps, queues, records,
+// deferred rows). In the separate kernels of the graph-driven loop such data
+// does not change while a kernel runs, so it is read through the read-only
+// or L1 path. The fused loop for small graphs (COH) runs every level in one
+// kernel: there another SM may have written the data since this SM last
+// cached it, so it is read from L2 (coherent).
+template <bool COH, class T>
+__device__ __forceinline__ T ld_mut(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+template <bool COH>
+__device__ __forceinline__ uint32_t ld_ro(const uint32_t* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <bool COH = false>
 __device__ __forceinline__ bool test_bit(const uint32_t* __restrict__ bm, int32_t v) {
-  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+  return (ld_ro<COH>(bm + (v >> 5)) >> (v & 31)) & 1u;
 }
 
 // First position in the sorted row cols[s, e) whose column is >= x.
@@ -157,12 +176,12 @@ __device__ __forceinline__ unsigned td_claim4(const BfsArgs<OffT>& A, const int3
 // read-only cache; a bit already set in the next bitmap needs no atomic.
 // Parents are recovered afterwards from the frontier bitmap (k_bu in
 // recovery mode).
-template <class OffT>
+template <bool COH, class OffT>
 __device__ __forceinline__ void td_mark4(const BfsArgs<OffT>& A, const int32_t (&v)[4], unsigned valid,
                                          uint32_t* next) {
   uint32_t w[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) w[t] = ((valid >> t) & 1u) ? __ldg(A.visited + (v[t] >> 5)) : ~0u;
+  for (int t = 0; t < 4; ++t) w[t] = ((valid >> t) & 1u) ? ld_ro<COH>(A.visited + (v[t] >> 5)) : ~0u;
   uint32_t nw[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) nw[t] = ((w[t] >> (v[t] & 31)) & 1u) ? ~0u : __ldcg(next + (v[t] >> 5));
@@ -173,11 +192,19 @@ __device__ __forceinline__ void td_mark4(const BfsArgs<OffT>& A, const int32_t (
   }
 }
 
+// Run parameters the status init writes into the control block.
+struct RunParams {
+  int32_t root_orig, mode, alpha, beta, static_pct, bu_steps, td_bm_div, td_small, td_chunk, bu_scan, td_split_pct;
+  uint64_t sched_seed;
+};
+
+// Status init (one thread): the control block and the root.
 template <class OffT>
-__global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t alpha, int32_t beta,
-                       int32_t static_pct, int32_t bu_steps, uint64_t sched_seed, int32_t td_bm_div,
-                       int32_t td_small, int32_t td_chunk, int32_t bu_scan, int32_t td_split_pct) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void init_body(const BfsArgs<OffT>& A, const RunParams& P) {
+  const int32_t root_orig = P.root_orig, mode = P.mode, alpha = P.alpha, beta = P.beta;
+  const int32_t static_pct = P.static_pct, bu_steps = P.bu_steps, td_bm_div = P.td_bm_div;
+  const int32_t td_small = P.td_small, td_chunk = P.td_chunk, bu_scan = P.bu_scan, td_split_pct = P.td_split_pct;
+  const uint64_t sched_seed = P.sched_seed;
   const int32_t r = A.o2n ? A.o2n[root_orig] : root_orig;
   const int64_t d = (int64_t)A.off[r + 1] - (int64_t)A.off[r];
   BfsCtl* c = A.ctl;
@@ -216,16 +243,19 @@ __global__ void k_init(BfsArgs<OffT> A, int32_t root_orig, int32_t mode, int32_t
   c->td_split_pct = td_split_pct;
   c->split_w = 0;
   A.q0[0] = r;
-  A.visited[r >> 5] |= 1u << (r & 31);
+  atomicOr(A.visited + (r >> 5), 1u << (r & 31));
   A.lp[r] = make_int2(0, r);
 }
 
-// The direction switch: closes the step that just ran, then picks the next.
 template <class OffT>
-__global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
-                         int in_graph) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  BfsCtl* c = A.ctl;
+__global__ void k_init(BfsArgs<OffT> A, RunParams P) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) init_body(A, P);
+}
+
+// The direction switch (one thread): closes the step that just ran, then
+// picks the next. Returns the step kind, or kCaseNone when the loop ends.
+template <class OffT>
+__device__ __forceinline__ int switch_decide(const BfsArgs<OffT>& A, BfsCtl* c) {
   if (!c->fresh) {
     const int32_t L = c->level;
     // top-down steps with queue output count their new vertices in the queue
@@ -278,11 +308,7 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
   if (c->n_f == 0 || c->overflow == 2) {
     c->done = 1;
     c->n_levels = c->level;
-    if (in_graph) {
-      cudaGraphSetConditional(h_case, kCaseNone);
-      cudaGraphSetConditional(h_while, 0);
-    }
-    return;
+    return kCaseNone;
   }
   int dir = 0;
   switch (c->mode) {
@@ -327,15 +353,43 @@ __global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cu
   }
   c->dir = dir;
   c->step_case = kase;
-  if (in_graph) cudaGraphSetConditional(h_case, (unsigned)kase);
+  return kase;
+}
+
+// The switch of the fused loop works on a copy of the control block read
+// from L2 in one batch of loads (the other SMs' atomics reach the block
+// through L2 while this SM runs on) and writes it back whole; nothing else
+// touches the block while the switch runs.
+template <class OffT>
+__device__ int switch_body_coherent(const BfsArgs<OffT>& A) {
+  static_assert(sizeof(BfsCtl) % 4 == 0, "control block in words");
+  BfsCtl lc;
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(BfsCtl) / 4); ++i)
+    reinterpret_cast<uint32_t*>(&lc)[i] = __ldcg(reinterpret_cast<const uint32_t*>(A.ctl) + i);
+  const int kase = switch_decide(A, &lc);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(BfsCtl) / 4); ++i)
+    reinterpret_cast<uint32_t*>(A.ctl)[i] = reinterpret_cast<const uint32_t*>(&lc)[i];
+  return kase;
+}
+
+template <class OffT>
+__global__ void k_switch(BfsArgs<OffT> A, cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_case,
+                         int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int kase = switch_decide(A, A.ctl);
+  if (in_graph) {
+    cudaGraphSetConditional(h_case, (unsigned)kase);
+    if (kase == kCaseNone) cudaGraphSetConditional(h_while, 0);
+  }
 }
 
 // Top-down, part 1: short rows expanded in place, long rows cut into
 // chunk records.
-template <class OffT, bool BM, int NT>
-__global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
+template <class OffT, bool BM, int NT, bool COH>
+__device__ __forceinline__ void td_bin_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
   __shared__ unsigned long long sh[NT / 32];
-  const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nf = c->n_f;
   const int32_t* cur = (L & 1) ? A.q1 : A.q0;
@@ -346,7 +400,7 @@ __global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
   const int32_t x = BM ? (int32_t)(c->split_w << 5) : 0;
   unsigned long long m_new = 0, ex = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = bc_vid(cur[i], A.n, &A.ctl->bc_site, kBcTdFrontier);
+    const int32_t u = bc_vid(ld_mut<COH>(cur + i), A.n, &A.ctl->bc_site, kBcTdFrontier);
     int64_t s = (int64_t)A.off[u];
     int64_t e = (int64_t)A.off[u + 1];
     bc_row(s, e, A.nnz, &A.ctl->bc_site, kBcTdRow);
@@ -363,7 +417,7 @@ __global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
           if (j + t < e && v[t] >= x) valid |= 1u << t;
         }
         if constexpr (BM) {
-          td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
+          td_mark4<COH>(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
         } else {
           unsigned won = td_claimN<kE>(A, v, valid, u, L + 1, m_new);
           while (won) {
@@ -404,11 +458,15 @@ __global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
   }
 }
 
-// Top-down, part 2: one warp per chunk record, 16-byte column loads.
 template <class OffT, bool BM, int NT>
-__global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
+__global__ void __launch_bounds__(NT) k_td_bin(BfsArgs<OffT> A) {
+  td_bin_body<OffT, BM, NT, false>(A, A.ctl);
+}
+
+// Top-down, part 2: one warp per chunk record, 16-byte column loads.
+template <class OffT, bool BM, int NT, bool COH>
+__device__ __forceinline__ void td_chunks_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
   __shared__ unsigned long long sh[NT / 32];
-  const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nrec = min((int64_t)c->n_rec, A.rec_cap);
   const int64_t chunk = c->td_chunk;
@@ -420,13 +478,13 @@ __global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
     int32_t u = 0;
     int64_t lo, hi, lo_ok;
     if (BM) {
-      const unsigned long long rc = reinterpret_cast<const unsigned long long*>(A.rec)[r];
+      const unsigned long long rc = ld_mut<COH>(reinterpret_cast<const unsigned long long*>(A.rec) + r);
       lo = (int64_t)(rc >> 16);
       hi = lo + (int64_t)((rc >> 2) & 0x3FFFu);
       bc_row(lo, hi, A.nnz, &A.ctl->bc_site, kBcTdRecord);
       lo_ok = lo + (int64_t)(rc & 3u);
     } else {
-      const int2 rc = A.rec[r];
+      const int2 rc = ld_mut<COH>(A.rec + r);
       u = bc_vid(rc.x, A.n, &A.ctl->bc_site, kBcTdRecord);
       int64_t s = (int64_t)A.off[u], e = (int64_t)A.off[u + 1];
       bc_row(s, e, A.nnz, &A.ctl->bc_site, kBcTdRow);
@@ -452,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
       for (int t = 0; t < kE; ++t)
         if (p + t >= lo_ok && p + t < hi) valid |= 1u << t;
       if constexpr (BM) {
-        if (valid) td_mark4(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
+        if (valid) td_mark4<COH>(A, v, valid, (L & 1) ? A.fbm0 : A.fbm1);
         continue;
       }
       const unsigned won = valid ? td_claimN<kE>(A, v, valid, u, L + 1, m_new) : 0u;
@@ -482,18 +540,23 @@ __global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
   if (threadIdx.x == 0 && m_new) atomicAdd(&A.ctl->nx_m, m_new);
 }
 
+template <class OffT, bool BM, int NT>
+__global__ void __launch_bounds__(NT) k_td_chunks(BfsArgs<OffT> A) {
+  td_chunks_body<OffT, BM, NT, false>(A, A.ctl);
+}
+
 // Frontier bitmap of level L -> queue of level L (after a bottom-up level,
 // before a top-down one). A warp converts 32 consecutive words.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_bitmap_to_queue(BfsArgs<OffT> A) {
-  const int32_t L = A.ctl->level;
+template <class OffT, bool COH>
+__device__ __forceinline__ void bitmap_to_queue_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
+  const int32_t L = c->level;
   const uint32_t* bm = (L & 1) ? A.fbm1 : A.fbm0;
   int32_t* q = (L & 1) ? A.q1 : A.q0;
   const unsigned lane = lane_id();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; w0 < A.cand_words; w0 += stride) {
     const int64_t w = w0 + lane;
-    uint32_t x = (w < A.cand_words) ? bm[w] : 0u;
+    uint32_t x = (w < A.cand_words) ? ld_mut<COH>(bm + w) : 0u;
     const unsigned cnt = (unsigned)__popc(x);
     unsigned inc = cnt;
     for (int o = 1; o < 32; o <<= 1) {
@@ -514,18 +577,28 @@ __global__ void __launch_bounds__(kThreads) k_bitmap_to_queue(BfsArgs<OffT> A) {
   }
 }
 
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_bitmap_to_queue(BfsArgs<OffT> A) {
+  bitmap_to_queue_body<OffT, false>(A, A.ctl);
+}
+
 // Queue of level L -> frontier bitmap of level L (after a top-down level,
 // before a bottom-up one). Both bitmaps were cleared just before.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
-  const int32_t L = A.ctl->level;
-  const int64_t nf = A.ctl->n_f;
+template <class OffT, bool COH>
+__device__ __forceinline__ void queue_to_bitmap_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
+  const int32_t L = c->level;
+  const int64_t nf = c->n_f;
   uint32_t* bm = (L & 1) ? A.fbm1 : A.fbm0;
   const int32_t* q = (L & 1) ? A.q1 : A.q0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = bc_vid(q[i], A.n, &A.ctl->bc_site, kBcConvert);
+    const int32_t v = bc_vid(ld_mut<COH>(q + i), A.n, &A.ctl->bc_site, kBcConvert);
     atomicOr(bm + (v >> 5), 1u << (v & 31));
   }
+}
+
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
+  queue_to_bitmap_body<OffT, false>(A, A.ctl);
 }
 
 // Bottom-up, part 1 (Algorithm 1, bottom-up branch). A warp takes 32
@@ -542,15 +615,14 @@ __global__ void __launch_bounds__(kThreads) k_queue_to_bitmap(BfsArgs<OffT> A) {
 // rows without a hit go to the deferred list. Found vertices are collected
 // per word in shared memory and every lane writes its own next-frontier and
 // visited word: no global atomics.
-template <class OffT, bool RECOVER, int NT>
-__global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
+template <class OffT, bool RECOVER, int NT, bool COH>
+__device__ __forceinline__ void bu_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
   __shared__ unsigned long long sh[NT / 32];
   __shared__ uint32_t s_found[NT / 32][32];
   __shared__ uint16_t s_cand[NT / 32][1024];
   __shared__ int64_t s_tab[2 * kSmallDeg];
   if (threadIdx.x < 2 * kSmallDeg) s_tab[threadIdx.x] = A.small_deg ? A.small_tab[threadIdx.x] : 0;
   __syncthreads();
-  const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
   uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
@@ -570,9 +642,9 @@ __global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
        grp += warps) {
     const int64_t w = grp * 32 + lane;
     const bool in = w < w_hi;
-    const uint32_t vis = in ? A.visited[w] : ~0u;
+    const uint32_t vis = in ? ld_mut<COH>(A.visited + w) : ~0u;
     // recovery: the candidates are the vertices the top-down marking found
-    const uint32_t cand = in ? (RECOVER ? next[w] : ~(vis | A.iso[w])) : 0u;
+    const uint32_t cand = in ? (RECOVER ? ld_mut<COH>(next + w) : ~(vis | A.iso[w])) : 0u;
     const unsigned cnt = (unsigned)__popc(cand);
     unsigned incl = cnt;
 #pragma unroll
@@ -618,7 +690,7 @@ __global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
       }
       bool hit0[2];
 #pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) hit0[c2] = act[c2] && test_bit(front, fd[c2].x);
+      for (int c2 = 0; c2 < 2; ++c2) hit0[c2] = act[c2] && test_bit<COH>(front, fd[c2].x);
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2) {
         if (act[c2]) ex += 1;
@@ -659,7 +731,7 @@ __global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
           u[t] = (p + t < lim) ? bc_vid(A.cols[p + t], A.n, &A.ctl->bc_site, kBcBuColumn) : -1;
         bool h[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit(front, u[t]);
+        for (int t = 0; t < 4; ++t) h[t] = (u[t] >= 0) && test_bit<COH>(front, u[t]);
 #pragma unroll
         for (int t = 3; t >= 0; --t)
           if (h[t]) parent = u[t];
@@ -694,23 +766,32 @@ __global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
   }
 }
 
+template <class OffT, bool RECOVER, int NT>
+__global__ void __launch_bounds__(NT, bu_min_blocks(NT)) k_bu(BfsArgs<OffT> A) {
+  bu_body<OffT, RECOVER, NT, false>(A, A.ctl);
+}
+
 // Clears the next-frontier bitmap of level L (bitmap-output top-down step
 // after a bottom-up level, when the current frontier bitmap must stay).
 template <class OffT>
-__global__ void k_clear_next(BfsArgs<OffT> A) {
-  const int32_t L = A.ctl->level;
+__device__ __forceinline__ void clear_next_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
+  const int32_t L = c->level;
   uint32_t* next = (L & 1) ? A.fbm0 : A.fbm1;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < A.words; w += (int64_t)gridDim.x * blockDim.x)
     next[w] = 0u;
 }
 
+template <class OffT>
+__global__ void k_clear_next(BfsArgs<OffT> A) {
+  clear_next_body(A, A.ctl);
+}
+
 // Bottom-up, part 2: rows with no frontier neighbour among their first bu_scan
 // entries; one warp per row, 16-byte loads, the ballot picks the first hit
 // in row order.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
+template <class OffT, bool COH>
+__device__ __forceinline__ void bu_long_body(const BfsArgs<OffT>& A, const BfsCtl* c) {
   __shared__ unsigned long long sh[kThreads / 32];
-  const BfsCtl* c = A.ctl;
   const int32_t L = c->level;
   const int64_t nd = c->n_def;
   const uint32_t* front = (L & 1) ? A.fbm1 : A.fbm0;
@@ -719,7 +800,7 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
   unsigned long long n_new = 0, m_new = 0, ex = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nd; i += warps) {
-    const int32_t v = bc_vid(A.def[i], A.n, &A.ctl->bc_site, kBcBuDeferred);
+    const int32_t v = bc_vid(ld_mut<COH>(A.def + i), A.n, &A.ctl->bc_site, kBcBuDeferred);
     int64_t s0 = (int64_t)A.off[v], e = (int64_t)A.off[v + 1];
     bc_row(s0, e, A.nnz, &A.ctl->bc_site, kBcBuRow);
     const int64_t s = s0 + c->bu_scan;
@@ -736,7 +817,7 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int64_t idx = p + t;
-          if (hit < 0 && idx >= s && idx < e && test_bit(front, us[t])) hit = us[t];
+          if (hit < 0 && idx >= s && idx < e && test_bit<COH>(front, us[t])) hit = us[t];
         }
       }
       const unsigned b = __ballot_sync(0xffffffffu, hit >= 0);
@@ -765,6 +846,11 @@ __global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
   }
 }
 
+template <class OffT>
+__global__ void __launch_bounds__(kThreads) k_bu_long(BfsArgs<OffT> A) {
+  bu_long_body<OffT, false>(A, A.ctl);
+}
+
 // Results in original IDs: level_out[o], parent_out[o] for every vertex.
 // Each thread handles four consecutive original IDs (16-byte map loads and
 // output stores). Vertices renumbered past the last one with an edge are
@@ -776,6 +862,13 @@ __global__ void __launch_bounds__(NT) k_output(BfsArgs<OffT> A, const int32_t* _
                                                      int32_t* __restrict__ parent_out) {
   constexpr int kQ = 2;  // quads per thread and step: eight independent gathers in flight
   constexpr int64_t kOutChunk = 2048;  // quads per chunk (8192 original IDs)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the fused level loop (done by now): report a barrier that timed out
+    // and reset the barrier for the next run
+    if (A.gbar[2]) A.ctl->overflow = 3;
+    A.gbar[0] = 0u;
+    A.gbar[2] = 0u;
+  }
   const int32_t root = A.o2n ? __ldg(A.o2n + root_orig) : root_orig;
   const int64_t quads = A.n >> 2;
   const bool vec = ((reinterpret_cast<uintptr_t>(level_out) | reinterpret_cast<uintptr_t>(parent_out)) & 15) == 0;
@@ -902,7 +995,175 @@ __global__ void k_firstdeg(const OffT* __restrict__ off, const int32_t* __restri
   }
 }
 
+// ------------------------------------------------------------------ fused loop
+// The level loop of a small graph in one cooperative kernel: per level the
+// step kind's phases, separated by grid-wide barriers instead of kernel
+// launches (a level of a small graph costs its launches more than its
+// work); the last block to reach a level's final barrier runs the switch
+// (one thread) before the others leave it. Every block takes the same path:
+// the step kind and the end of the loop are read from the control block
+// after a barrier, from L2, into shared memory (s_c), and the phases read
+// the control fields from that copy; data the loop writes is read from L2
+// too (the bodies' COH loads). The loop ends at the switch's end mark, or
+// after n + 2 levels at most (a fault; the switch flags it past n).
+//
+// The cooperative launch makes every block resident at once, so each
+// barrier completes once all blocks reach it; a block still waits at most
+// kGridBarrierNs there. A wait that runs out (never expected) sets the
+// timed-out flag and ends that block's loop; the others then run out at
+// their next barrier. The output kernel that follows every run reports the
+// flag in the control block and resets the barrier.
+constexpr int64_t kFusedMaxNonisolated = int64_t(1) << 20;  // graphs this size or smaller use the fused loop
+constexpr int64_t kFusedMaxNnz = int64_t(1) << 26;          // ... with at most this many stored entries
+constexpr unsigned long long kGridBarrierNs = 2000000000ull;  // longest wait at a barrier (2 s)
+constexpr size_t kGridBarBytes = 16;                          // after the control block
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier: bar[0] counts the blocks that arrived, bar[1] is the
+// generation the last of them advances, bar[2] the timed-out flag. `gen`
+// (thread 0's copy of the generation) advances with every barrier. The last
+// block to arrive runs the hook (status init and/or the direction switch)
+// before it lets the others go: every block's writes of the phase are
+// visible to it then. Returns false in every thread of the block if the
+// wait ran out.
+enum { kHookNone = 0, kHookSwitch = 1, kHookInitSwitch = 2 };
+
+template <class OffT>
+__device__ __forceinline__ bool grid_barrier(const BfsArgs<OffT>& A, uint32_t& gen, int hook, const RunParams* P) {
+  __shared__ int s_ok;
+  uint32_t* bar = A.gbar;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();  // the block's writes of the phase, before its arrival
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      __threadfence();
+      if (hook == kHookInitSwitch) {
+        init_body(A, *P);
+        __threadfence();
+      }
+      if (hook != kHookNone) switch_body_coherent(A);
+      atomicExch(bar, 0u);  // the count starts over for the next barrier
+      __threadfence();
+      atomicExch(bar + 1, gen + 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      for (uint32_t k = 1; ld_acquire_gpu(bar + 1) == gen; ++k) {
+        if ((k & 255u) == 0 && globaltimer_ns() - t0 > kGridBarrierNs) {
+          atomicExch(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    gen += 1u;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <class OffT>
+__device__ __forceinline__ void load_ctl(BfsCtl* dst, const BfsCtl* src) {
+  static_assert(sizeof(BfsCtl) % 4 == 0, "control block in words");
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  const uint32_t* g = reinterpret_cast<const uint32_t*>(src);
+  for (int i = threadIdx.x; i < (int)(sizeof(BfsCtl) / 4); i += blockDim.x) d[i] = __ldcg(g + i);
+  __syncthreads();
+}
+
+// One barrier between levels: its last block closes the level and picks the
+// next step (the switch) before the others leave it.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 3) k_bfs_fused(BfsArgs<OffT> A, RunParams P) {
+  __shared__ BfsCtl s_c;
+  // thread 0's generation: read before this block's first arrival, which
+  // no barrier completes without
+  uint32_t gen = threadIdx.x == 0 ? ld_acquire_gpu(A.gbar + 1) : 0u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#define FUSED_BARRIER(hook) \
+  if (!grid_barrier(A, gen, hook, &P)) return
+  for (int64_t w = tid; w < A.words; w += stride) A.visited[w] = 0u;
+  FUSED_BARRIER(kHookInitSwitch);
+  for (int64_t it = 0; it <= A.n + 1; ++it) {
+    load_ctl<OffT>(&s_c, A.ctl);
+    if (s_c.done) break;
+    const int kase = s_c.step_case;
+    if (kase == 2 || kase == 5) {  // frontier as a bitmap, the step needs a queue
+      bitmap_to_queue_body<OffT, true>(A, &s_c);
+      if (kase == 5) clear_next_body(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+    }
+    if (kase == 3 || kase == 4) {  // frontier as a queue, the step needs both bitmaps cleared and the frontier's
+      uint32_t* f = A.fbm0;         // fbm1 follows fbm0
+      for (int64_t w = tid; w < 2 * A.words; w += stride) f[w] = 0u;
+      FUSED_BARRIER(kHookNone);
+      queue_to_bitmap_body<OffT, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+    }
+    if (kase == 0 || kase == 2) {
+      td_bin_body<OffT, false, kThreads, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+      td_chunks_body<OffT, false, kThreads, true>(A, &s_c);
+    } else if (kase == 1 || kase == 3) {
+      bu_body<OffT, false, kThreads, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+      bu_long_body<OffT, true>(A, &s_c);
+    } else {  // 4, 5: top-down marking a bitmap, the mixed level's bottom-up part, parent recovery
+      td_bin_body<OffT, true, kThreads, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+      td_chunks_body<OffT, true, kThreads, true>(A, &s_c);
+      bu_body<OffT, false, kThreads, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+      bu_body<OffT, true, kThreads, true>(A, &s_c);
+      FUSED_BARRIER(kHookNone);
+      load_ctl<OffT>(&s_c, A.ctl);
+      bu_long_body<OffT, true>(A, &s_c);
+    }
+    FUSED_BARRIER(kHookSwitch);
+  }
+#undef FUSED_BARRIER
+}
+
 int grid_cap(int per_sm) { return sm_count() * per_sm; }
+
+// Grid of the fused loop for g: 0 if g is too large for it, else as many
+// blocks as are resident at once (cooperative launch), at most what the
+// graph's vertices with an edge can use.
+template <class OffT>
+int fused_grid_for(const dobfs_graph* g) {
+  if (g->n_nonisolated > kFusedMaxNonisolated || g->nnz > kFusedMaxNnz) return 0;
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs_fused<OffT>, kThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
+    per_sm = occ;
+  }
+  if (per_sm < 1) return 0;
+  const int64_t want = std::max<int64_t>(1, ceil_div(std::max<int64_t>(g->n_nonisolated, 1), 1024));
+  return (int)std::min<int64_t>((int64_t)sm_count() * per_sm, want);
+}
 
 template <class OffT>
 BfsArgs<OffT> make_args(dobfs_graph* g) {
@@ -924,6 +1185,7 @@ BfsArgs<OffT> make_args(dobfs_graph* g) {
   A.rec = g->rec.as<int2>();
   A.def = g->deferred.as<int32_t>();
   A.ctl = g->ctl.as<BfsCtl>();
+  A.gbar = reinterpret_cast<uint32_t*>(g->ctl.as<char>() + sizeof(BfsCtl));
   A.trace = g->trace.as<LevelRec>();
   A.n = g->n;
   A.nnz = g->nnz;
@@ -1203,7 +1465,13 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     return set_error(DOBFS_ERR_INVALID, "level_out and parent_out must both be host or both be device memory");
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
   const BlockCfg bc = block_cfg(o);
-  if (!host_loop_mode && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
+  // small graphs (and default block sizes): one cooperative launch for all levels
+  const int fused_grid = (!host_loop_mode && !(o.flags & DOBFS_RUN_LEVEL_GRAPH) && bc.bu == kThreads &&
+                          bc.td == kThreads)
+                             ? fused_grid_for<OffT>(g)
+                             : 0;
+  const bool fused = fused_grid > 0;
+  if (!host_loop_mode && !fused && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
     // another block configuration: the level graph is rebuilt for it (after
     // the previous run, which may still use the old one)
     DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
@@ -1212,7 +1480,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     g->cg_exec = nullptr;
     g->cg = nullptr;
   }
-  if (!host_loop_mode && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
+  if (!host_loop_mode && !fused && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
   const BfsArgs<OffT> A = make_args<OffT>(g);
   int32_t* lv = level_out;
   int32_t* pa = parent_out;
@@ -1221,17 +1489,34 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     lv = g->out_stage.as<int32_t>();
     pa = parent_out ? lv + g->n : nullptr;
   }
+  RunParams P;
+  P.root_orig = root;
+  P.mode = o.direction;
+  P.alpha = o.alpha;
+  P.beta = o.beta;
+  P.static_pct = o.static_pct;
+  P.bu_steps = o.bu_steps;
+  P.sched_seed = o.schedule_seed;
+  P.td_bm_div = o.td_bitmap_div;
+  P.td_small = o.td_small_max ? o.td_small_max : kTdSmall;
+  P.td_chunk = o.td_chunk ? o.td_chunk : kChunk;
+  P.bu_scan = o.bu_scan ? o.bu_scan : kBuT;
+  P.td_split_pct = o.td_split_pct;
   DOBFS_CUDA_TRY(cudaEventRecord(g->ev_t0, s));
-  DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
-  k_init<OffT><<<1, 32, 0, s>>>(A, root, o.direction, o.alpha, o.beta, o.static_pct, o.bu_steps, o.schedule_seed,
-                                o.td_bitmap_div, o.td_small_max ? o.td_small_max : kTdSmall,
-                                o.td_chunk ? o.td_chunk : kChunk, o.bu_scan ? o.bu_scan : kBuT,
-                                o.td_split_pct);
-  DOBFS_CUDA_TRY(cudaGetLastError());
-  if (host_loop_mode) {
-    DOBFS_TRY(host_loop<OffT>(g, A, s, bc));
+  if (fused) {
+    // the whole level loop, status init included, in one cooperative launch
+    void* args[] = {(void*)&A, (void*)&P};
+    DOBFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bfs_fused<OffT>, dim3(fused_grid), dim3(kThreads), args,
+                                               0, s));
   } else {
-    DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
+    DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
+    k_init<OffT><<<1, 32, 0, s>>>(A, P);
+    DOBFS_CUDA_TRY(cudaGetLastError());
+    if (host_loop_mode) {
+      DOBFS_TRY(host_loop<OffT>(g, A, s, bc));
+    } else {
+      DOBFS_CUDA_TRY(cudaGraphLaunch(g->cg_exec, s));
+    }
   }
   const int32_t* n2o = g->reindexed ? g->new2orig.as<int32_t>() : nullptr;
   launch_output<OffT>(g, A, n2o, root, lv, pa, s, o.out_threads ? o.out_threads : kThreads);
@@ -1256,6 +1541,7 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
     if (c.bc_site)
       return set_error(DOBFS_ERR_BOUNDS, "device bounds check failed: %s", bounds_site_name(c.bc_site));
     if (c.overflow == 2) return set_error(DOBFS_ERR_CUDA, "internal: the level loop ran past n levels");
+    if (c.overflow == 3) return set_error(DOBFS_ERR_CUDA, "internal: a grid barrier of the fused level loop timed out");
     if (c.overflow) return set_error(DOBFS_ERR_CUDA, "internal: top-down record buffer overflow");
     if (stats) {
       float ms = 0.f;
@@ -1304,9 +1590,10 @@ int graph_alloc_workspace(dobfs_graph* g) {
                                                    g->firstdeg.as<int2>());
     DOBFS_CUDA_TRY(cudaGetLastError());
   }
-  DOBFS_TRY(g->ctl.alloc(sizeof(BfsCtl), s));
+  // the control block, then the fused loop's grid barrier (4 words)
+  DOBFS_TRY(g->ctl.alloc(sizeof(BfsCtl) + kGridBarBytes, s));
   DOBFS_TRY(g->trace.alloc(sizeof(LevelRec) * kMaxTrace, s));
-  DOBFS_CUDA_TRY(cudaMemsetAsync(g->ctl.ptr, 0, sizeof(BfsCtl), s));
+  DOBFS_CUDA_TRY(cudaMemsetAsync(g->ctl.ptr, 0, sizeof(BfsCtl) + kGridBarBytes, s));
   DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_done));
   DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_t0));
   DOBFS_CUDA_TRY(cudaEventCreate(&g->ev_t1));

@@ -42,6 +42,7 @@ DOBFS_DIR_AUTO, DOBFS_DIR_TOPDOWN, DOBFS_DIR_BOTTOMUP, DOBFS_DIR_RANDOM, DOBFS_D
 DOBFS_RUN_CANONICAL_PARENT = 0x1
 DOBFS_RUN_HOST_LOOP = 0x2
 DOBFS_RUN_SYNC_STATS = 0x4
+DOBFS_RUN_LEVEL_GRAPH = 0x8
 DOBFS_STATIC_MAX_VERTICES = 1 << 20
 
 

@@ -328,6 +328,29 @@ def test_host_outputs_and_host_loop(d, s16):
     assert tr1[0].direction == 0 and any(t.direction == 1 for t in tr1)
 
 
+@pytest.mark.parametrize("name,mode,seed", MODES)
+def test_fused_loop_matches_level_graph(d, s16, name, mode, seed):
+    """A small graph runs all its levels in one cooperative kernel; the same
+    runs through the CUDA level graph (DOBFS_RUN_LEVEL_GRAPH) take the same
+    schedule with the same per-level counters, and both reach the oracle's
+    levels, also with bitmap-output top-down and mixed levels."""
+    spec, og, roots, ref_l, ref_p = s16
+    for flags in (0, d.DOBFS_GRAPH_REINDEX | d.DOBFS_GRAPH_OFFSETS64):
+        g = d.rmat_graph(spec, flags=flags)
+        for i, r in enumerate(roots[:3]):
+            for div in (0, 2, 1 << 30):
+                traces, stats = [], []
+                for rf in (0, d.DOBFS_RUN_LEVEL_GRAPH):
+                    lv, pa, st = _run(d, g, int(r), mode, seed, flags=rf, td_bitmap_div=div)
+                    _check_run(og, int(r), lv, pa, ref_l[i])
+                    traces.append([(t.direction, t.n_frontier, t.m_frontier, t.n_next, t.edges_examined, t.vertices_scanned,
+                                    t.alg_bytes) for t in g.trace()])
+                    stats.append((st.levels, st.td_levels, st.bu_levels, st.reached, st.teps_edges, st.alg_bytes))
+                assert traces[0] == traces[1], (flags, div)
+                assert stats[0] == stats[1], (flags, div)
+        g.close()
+
+
 def _pairs_graph(d, n, pairs, flags=0):
     src = np.array([p[0] for p in pairs], dtype=np.int32)
     dst = np.array([p[1] for p in pairs], dtype=np.int32)
