@@ -522,6 +522,24 @@ int dobfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int
  */
 int dobfs_debug_set_column(dobfs_graph* g, int64_t pos, int32_t value);
 
+/*
+ * Self-test of the grid barrier that the fused level loop of small graphs
+ * uses between phases (all builds). One cooperative launch of `blocks`
+ * blocks (1 up to the resident capacity) runs `rounds` barriers (0..2^20);
+ * before each, every block adds one to a counter, after it one block
+ * checks that the counter holds every block's additions. With missing = 1
+ * the barrier waits for one block more than was launched, so every wait
+ * runs out after its 2 s bound and the launch ends without a fault. Out:
+ * *rounds_passed (rounds whose barrier completed), *short_counts (rounds
+ * that saw a counter short of a block's addition: 0 for a correct
+ * barrier), *timed_out (1 if a wait ran out). Synchronous, on the legacy
+ * default stream; allocates 32 bytes through the allocator hook.
+ * Errors: DOBFS_ERR_INVALID (NULL outputs, arguments out of range),
+ * DOBFS_ERR_CUDA, DOBFS_ERR_OOM.
+ */
+int dobfs_debug_grid_barrier(int32_t blocks, int32_t rounds, int32_t missing, int32_t* rounds_passed,
+                             int32_t* short_counts, int32_t* timed_out);
+
 #ifdef __cplusplus
 }
 #endif

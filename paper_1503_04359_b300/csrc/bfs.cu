@@ -1029,30 +1029,23 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Grid-wide barrier: bar[0] counts the blocks that arrived, bar[1] is the
-// generation the last of them advances, bar[2] the timed-out flag. `gen`
-// (thread 0's copy of the generation) advances with every barrier. The last
-// block to arrive runs the hook (status init and/or the direction switch)
-// before it lets the others go: every block's writes of the phase are
-// visible to it then. Returns false in every thread of the block if the
-// wait ran out.
-enum { kHookNone = 0, kHookSwitch = 1, kHookInitSwitch = 2 };
-
-template <class OffT>
-__device__ __forceinline__ bool grid_barrier(const BfsArgs<OffT>& A, uint32_t& gen, int hook, const RunParams* P) {
+// Grid-wide barrier of `nblocks` blocks (all resident): bar[0] counts the
+// blocks that arrived, bar[1] is the generation the last of them advances,
+// bar[2] the timed-out flag. `gen` (thread 0's copy of the generation)
+// advances with every barrier. The last block to arrive runs `last` (one
+// thread) before it lets the others go: every block's writes before the
+// barrier are visible to it then. Returns false in every thread of the
+// block if the wait ran out (kGridBarrierNs).
+template <class Last>
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint32_t nblocks, Last&& last) {
   __shared__ int s_ok;
-  uint32_t* bar = A.gbar;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();  // the block's writes of the phase, before its arrival
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    __threadfence();  // the block's writes, before its arrival
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
       __threadfence();
-      if (hook == kHookInitSwitch) {
-        init_body(A, *P);
-        __threadfence();
-      }
-      if (hook != kHookNone) switch_body_coherent(A);
+      last();
       atomicExch(bar, 0u);  // the count starts over for the next barrier
       __threadfence();
       atomicExch(bar + 1, gen + 1u);
@@ -1072,6 +1065,41 @@ __device__ __forceinline__ bool grid_barrier(const BfsArgs<OffT>& A, uint32_t& g
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The fused loop's hooks: status init and/or the direction switch.
+enum { kHookNone = 0, kHookSwitch = 1, kHookInitSwitch = 2 };
+
+template <class OffT>
+__device__ __forceinline__ bool fused_barrier(const BfsArgs<OffT>& A, uint32_t& gen, int hook, const RunParams* P) {
+  return grid_barrier(A.gbar, gen, gridDim.x, [&] {
+    if (hook == kHookInitSwitch) {
+      init_body(A, *P);
+      __threadfence();
+    }
+    if (hook != kHookNone) switch_body_coherent(A);
+  });
+}
+
+// Self-test of the barrier: `rounds` barriers over the launched blocks, or
+// over one block more than launched (`missing`), so that every wait runs
+// out. Before each barrier every block adds one to cnt[0]; after it block 0
+// checks that all blocks did (cnt[1] counts the rounds that passed, cnt[2]
+// the rounds that saw a short count).
+__global__ void __launch_bounds__(kThreads) k_barrier_probe(uint32_t* bar, uint32_t* cnt, uint32_t rounds,
+                                                          uint32_t missing) {
+  uint32_t gen = threadIdx.x == 0 ? ld_acquire_gpu(bar + 1) : 0u;
+  const uint32_t nb = gridDim.x + missing;
+  for (uint32_t r = 0; r < rounds; ++r) {
+    if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+    if (!grid_barrier(bar, gen, nb, [] {})) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (__ldcg(cnt) != gridDim.x * (r + 1)) atomicAdd(cnt + 2, 1u);
+      atomicAdd(cnt + 1, 1u);
+    }
+    // no block adds for the next round before block 0 has checked this one
+    if (!grid_barrier(bar, gen, nb, [] {})) return;
+  }
 }
 
 template <class OffT>
@@ -1094,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bfs_fused(BfsArgs<OffT> A, RunP
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #define FUSED_BARRIER(hook) \
-  if (!grid_barrier(A, gen, hook, &P)) return
+  if (!fused_barrier(A, gen, hook, &P)) return
   for (int64_t w = tid; w < A.words; w += stride) A.visited[w] = 0u;
   FUSED_BARRIER(kHookInitSwitch);
   for (int64_t it = 0; it <= A.n + 1; ++it) {
@@ -1745,6 +1773,33 @@ int dobfs_debug_set_column(dobfs_graph* g, int64_t pos, int32_t value) {
                                                  g->firstdeg.as<int2>());
   DOBFS_CUDA_TRY(cudaGetLastError());
   DOBFS_CUDA_TRY(cudaStreamSynchronize(s));
+  return DOBFS_OK;
+}
+
+int dobfs_debug_grid_barrier(int32_t blocks, int32_t rounds, int32_t missing, int32_t* rounds_passed,
+                             int32_t* short_counts, int32_t* timed_out) {
+  clear_error();
+  if (!rounds_passed || !short_counts || !timed_out) return set_error(DOBFS_ERR_INVALID, "output pointers are NULL");
+  int per_sm = 0;
+  DOBFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_probe, kThreads, 0));
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  if (blocks < 1 || blocks > cap || rounds < 0 || rounds > (1 << 20) || missing < 0 || missing > 1)
+    return set_error(DOBFS_ERR_INVALID, "bad barrier test: blocks %d (1..%lld), rounds %d, missing %d", blocks,
+                     (long long)cap, rounds, missing);
+  DevBuf buf;  // barrier words (4), then the counters (4)
+  DOBFS_TRY(buf.alloc(8 * sizeof(uint32_t), nullptr));
+  uint32_t* bar = buf.as<uint32_t>();
+  uint32_t* cnt = bar + 4;
+  DOBFS_CUDA_TRY(cudaMemsetAsync(bar, 0, 8 * sizeof(uint32_t), nullptr));
+  uint32_t r = (uint32_t)rounds, m = (uint32_t)missing;
+  void* args[] = {(void*)&bar, (void*)&cnt, (void*)&r, (void*)&m};
+  DOBFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(blocks), dim3(kThreads), args, 0,
+                                             nullptr));
+  uint32_t h[8];
+  DOBFS_CUDA_TRY(cudaMemcpy(h, bar, sizeof(h), cudaMemcpyDeviceToHost));
+  *rounds_passed = (int32_t)h[5];
+  *short_counts = (int32_t)h[6];
+  *timed_out = (int32_t)(h[2] != 0);
   return DOBFS_OK;
 }
 

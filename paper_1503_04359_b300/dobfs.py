@@ -129,6 +129,8 @@ def load() -> ctypes.CDLL:
         "dobfs_graph_degrees": (c_int, [G, vp, vp]),
         "dobfs_graph_save": (c_int, [G, ctypes.c_char_p, vp]),
         "dobfs_debug_set_column": (c_int, [G, i64, i32]),
+        "dobfs_debug_grid_barrier": (c_int, [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                             ctypes.POINTER(i32)]),
         "dobfs_graph_wait": (c_int, [G, i32]),
         "dobfs_graph_load": (c_int, [ctypes.c_char_p, u32, vp, ctypes.POINTER(G)]),
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
@@ -275,6 +277,14 @@ def dobfs_graph_degrees(g: int, deg_out, stream=None) -> None:
 
 def dobfs_debug_set_column(g: int, pos: int, value: int) -> None:
     _check(load().dobfs_debug_set_column(g, pos, value))
+
+
+def dobfs_debug_grid_barrier(blocks: int, rounds: int, missing: int = 0) -> tuple[int, int, bool]:
+    """(rounds passed, rounds with a short count, timed out) of the grid-barrier self-test."""
+    p, sc, to = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().dobfs_debug_grid_barrier(int(blocks), int(rounds), int(missing), ctypes.byref(p),
+                                           ctypes.byref(sc), ctypes.byref(to)))
+    return p.value, sc.value, bool(to.value)
 
 
 def dobfs_graph_wait(g: int, timeout_ms: int = -1) -> bool:

@@ -244,3 +244,31 @@ def test_bounded_wait_runs_out_then_completes(d):
     with pytest.raises(d.DobfsError) as e:
         d.dobfs_graph_wait(None, 0)
     assert e.value.status == d.DOBFS_ERR_INVALID
+
+
+def test_grid_barrier_completes_and_times_out(d):
+    """The grid barrier of the fused small-graph loop: many rounds over every
+    resident block complete with every block's writes visible after each
+    barrier; a barrier that waits for a block that was never launched runs
+    out after its 2 s bound in every block, the launch ends, the flag says
+    so, and the library (and context) stay usable."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for blocks, rounds in ((1, 10), (sms, 2000), (4 * sms, 500)):
+        assert d.dobfs_debug_grid_barrier(blocks, rounds, 0) == (rounds, 0, False)
+    t0 = time.perf_counter()
+    passed, short, timed_out = d.dobfs_debug_grid_barrier(2 * sms, 3, 1)
+    dt = time.perf_counter() - t0
+    assert timed_out and passed == 0 and short == 0
+    assert 1.5 < dt < 60, dt
+    with pytest.raises(d.DobfsError) as e:
+        d.dobfs_debug_grid_barrier(0, 1, 0)
+    assert e.value.status == d.DOBFS_ERR_INVALID
+    # a small graph (fused loop) after the timed-out launch: levels exact
+    spec = inputs.rmat(12)
+    og = oracle.csr_from_rmat(spec)
+    g = d.rmat_graph(spec)
+    r = int(inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 1, og.degrees() > 0)[0])
+    lv = np.empty(og.n, dtype=np.int32)
+    g.run(r, lv)
+    np.testing.assert_array_equal(lv, oracle.bfs(og, r)[0])
+    g.close()
