@@ -540,6 +540,22 @@ int dobfs_debug_set_column(dobfs_graph* g, int64_t pos, int32_t value);
 int dobfs_debug_grid_barrier(int32_t blocks, int32_t rounds, int32_t missing, int32_t* rounds_passed,
                              int32_t* short_counts, int32_t* timed_out);
 
+/*
+ * Measurement aid for the rooflines of the BFS steps, whose memory accesses
+ * are mostly scattered reads and writes of 4 to 16 bytes (all builds).
+ * Allocates array_bytes of device memory (a power of two, at least 1 MB)
+ * through the allocator hook, then times one launch that makes at least
+ * `accesses` accesses of `width` bytes (4, 8 or 16; reads, or writes with
+ * write = 1) at positions drawn by a hash, eight in flight per thread, over
+ * every SM. Out: *ms_out (CUDA-event time of the launch, after one untimed
+ * launch) and *made_out (accesses made: the request rounded up to whole
+ * rounds of the grid). Synchronous, on the legacy default stream.
+ * Errors: DOBFS_ERR_INVALID (NULL outputs, arguments out of range),
+ * DOBFS_ERR_OOM, DOBFS_ERR_CUDA.
+ */
+int dobfs_debug_random_access(int64_t array_bytes, int64_t accesses, int32_t width, int32_t write,
+                              float* ms_out, int64_t* made_out);
+
 #ifdef __cplusplus
 }
 #endif

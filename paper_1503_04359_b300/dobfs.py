@@ -131,6 +131,8 @@ def load() -> ctypes.CDLL:
         "dobfs_debug_set_column": (c_int, [G, i64, i32]),
         "dobfs_debug_grid_barrier": (c_int, [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                              ctypes.POINTER(i32)]),
+        "dobfs_debug_random_access": (c_int, [i64, i64, i32, i32, ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(i64)]),
         "dobfs_graph_wait": (c_int, [G, i32]),
         "dobfs_graph_load": (c_int, [ctypes.c_char_p, u32, vp, ctypes.POINTER(G)]),
         "dobfs_run_opts_init": (c_int, [ctypes.POINTER(dobfs_run_opts)]),
@@ -285,6 +287,14 @@ def dobfs_debug_grid_barrier(blocks: int, rounds: int, missing: int = 0) -> tupl
     _check(load().dobfs_debug_grid_barrier(int(blocks), int(rounds), int(missing), ctypes.byref(p),
                                            ctypes.byref(sc), ctypes.byref(to)))
     return p.value, sc.value, bool(to.value)
+
+
+def dobfs_debug_random_access(array_bytes: int, accesses: int, width: int, write: bool = False) -> tuple[float, int]:
+    """(milliseconds, accesses made) of one launch of scattered accesses (see the header)."""
+    ms, made = ctypes.c_float(), ctypes.c_int64()
+    _check(load().dobfs_debug_random_access(int(array_bytes), int(accesses), int(width), int(bool(write)),
+                                            ctypes.byref(ms), ctypes.byref(made)))
+    return ms.value, made.value
 
 
 def dobfs_graph_wait(g: int, timeout_ms: int = -1) -> bool:

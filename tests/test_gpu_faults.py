@@ -272,3 +272,16 @@ def test_grid_barrier_completes_and_times_out(d):
     g.run(r, lv)
     np.testing.assert_array_equal(lv, oracle.bfs(og, r)[0])
     g.close()
+
+
+def test_random_access_probe(d):
+    """The scattered-access measurement aid runs and checks its arguments."""
+    for width, write in ((4, False), (8, False), (16, False), (8, True)):
+        ms, made = d.dobfs_debug_random_access(1 << 26, 1 << 20, width, write)
+        assert ms > 0 and made >= 1 << 20
+    for bad in (dict(array_bytes=3 << 20), dict(array_bytes=1 << 10), dict(width=12), dict(accesses=0)):
+        kw = dict(array_bytes=1 << 26, accesses=1 << 20, width=8)
+        kw.update(bad)
+        with pytest.raises(d.DobfsError) as e:
+            d.dobfs_debug_random_access(kw["array_bytes"], kw["accesses"], kw["width"])
+        assert e.value.status == d.DOBFS_ERR_INVALID
