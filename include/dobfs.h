@@ -214,7 +214,9 @@ int dobfs_graph_load(const char* path, uint32_t flags, void* stream, dobfs_graph
 #define DOBFS_RUN_LEVEL_GRAPH 0x8u      /* run the level loop as the CUDA graph also for a small
                                            graph (by default a graph with at most 2^20 vertices
                                            that have edges and 2^26 stored entries runs all its
-                                           levels in one cooperative kernel; same results) */
+                                           levels in one cooperative kernel; same results; where
+                                           the device refuses that launch, the graph uses the
+                                           level graph from then on) */
 
 typedef struct {
   int32_t direction;        /* DOBFS_DIR_* */

@@ -1494,21 +1494,26 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   if (g->last_stream && g->last_stream != s) DOBFS_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
   const BlockCfg bc = block_cfg(o);
   // small graphs (and default block sizes): one cooperative launch for all levels
-  const int fused_grid = (!host_loop_mode && !(o.flags & DOBFS_RUN_LEVEL_GRAPH) && bc.bu == kThreads &&
-                          bc.td == kThreads)
+  const int fused_grid = (!host_loop_mode && !(o.flags & DOBFS_RUN_LEVEL_GRAPH) && !g->fused_off &&
+                          bc.bu == kThreads && bc.td == kThreads)
                              ? fused_grid_for<OffT>(g)
                              : 0;
-  const bool fused = fused_grid > 0;
-  if (!host_loop_mode && !fused && g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
-    // another block configuration: the level graph is rebuilt for it (after
-    // the previous run, which may still use the old one)
-    DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
-    cudaGraphExecDestroy(g->cg_exec);
-    cudaGraphDestroy(g->cg);
-    g->cg_exec = nullptr;
-    g->cg = nullptr;
-  }
-  if (!host_loop_mode && !fused && !g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
+  bool fused = fused_grid > 0;
+  // the level graph for this run's block sizes
+  auto ensure_level_graph = [&]() -> int {
+    if (g->cg_exec && (g->cg_bu != bc.bu || g->cg_td != bc.td)) {
+      // another block configuration: the level graph is rebuilt for it
+      // (after the previous run, which may still use the old one)
+      DOBFS_CUDA_TRY(cudaEventSynchronize(g->ev_done));
+      cudaGraphExecDestroy(g->cg_exec);
+      cudaGraphDestroy(g->cg);
+      g->cg_exec = nullptr;
+      g->cg = nullptr;
+    }
+    if (!g->cg_exec) DOBFS_TRY(build_level_graph<OffT>(g, bc));
+    return DOBFS_OK;
+  };
+  if (!host_loop_mode && !fused) DOBFS_TRY(ensure_level_graph());
   const BfsArgs<OffT> A = make_args<OffT>(g);
   int32_t* lv = level_out;
   int32_t* pa = parent_out;
@@ -1534,9 +1539,21 @@ int run_impl(dobfs_graph* g, int32_t root, int32_t* level_out, int32_t* parent_o
   if (fused) {
     // the whole level loop, status init included, in one cooperative launch
     void* args[] = {(void*)&A, (void*)&P};
-    DOBFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bfs_fused<OffT>, dim3(fused_grid), dim3(kThreads), args,
-                                               0, s));
-  } else {
+    const cudaError_t e =
+        cudaLaunchCooperativeKernel((const void*)k_bfs_fused<OffT>, dim3(fused_grid), dim3(kThreads), args, 0, s);
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
+      // this context cannot hold the grid at once (a partitioned or shared
+      // device, say): nothing was launched; the level graph runs this BFS
+      // and the graph's later ones
+      cudaGetLastError();
+      g->fused_off = true;
+      fused = false;
+      DOBFS_TRY(ensure_level_graph());
+    } else {
+      DOBFS_CUDA_TRY(e);
+    }
+  }
+  if (!fused) {
     DOBFS_CUDA_TRY(cudaMemsetAsync(g->visited.ptr, 0, sizeof(uint32_t) * (size_t)g->words, s));
     k_init<OffT><<<1, 32, 0, s>>>(A, P);
     DOBFS_CUDA_TRY(cudaGetLastError());

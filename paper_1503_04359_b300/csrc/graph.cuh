@@ -118,6 +118,7 @@ struct dobfs_graph {
   cudaGraph_t cg = nullptr;
   cudaGraphExec_t cg_exec = nullptr;
   int cg_bu = 0, cg_td = 0;           // block sizes the level graph was built with
+  bool fused_off = false;             // a cooperative launch was refused here: level graph only
   cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool last_host_loop = false;
