@@ -212,8 +212,8 @@ int dobfs_graph_load(const char* path, uint32_t flags, void* stream, dobfs_graph
                                            (diagnostics; adds one host round trip per level) */
 #define DOBFS_RUN_SYNC_STATS 0x4u       /* wait for completion and fill *stats */
 #define DOBFS_RUN_LEVEL_GRAPH 0x8u      /* run the level loop as the CUDA graph also for a small
-                                           graph (by default a graph with at most 2^20 vertices
-                                           that have edges and 2^26 stored entries runs all its
+                                           graph (by default a graph with at most 2^21 vertices
+                                           that have edges and 2^27 stored entries runs all its
                                            levels in one cooperative kernel; same results; where
                                            the device refuses that launch, the graph uses the
                                            level graph from then on) */

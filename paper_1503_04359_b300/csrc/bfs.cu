@@ -1013,8 +1013,8 @@ __global__ void k_firstdeg(const OffT* __restrict__ off, const int32_t* __restri
 // timed-out flag and ends that block's loop; the others then run out at
 // their next barrier. The output kernel that follows every run reports the
 // flag in the control block and resets the barrier.
-constexpr int64_t kFusedMaxNonisolated = int64_t(1) << 20;  // graphs this size or smaller use the fused loop
-constexpr int64_t kFusedMaxNnz = int64_t(1) << 26;          // ... with at most this many stored entries
+constexpr int64_t kFusedMaxNonisolated = int64_t(1) << 21;  // graphs this size or smaller use the fused loop
+constexpr int64_t kFusedMaxNnz = int64_t(1) << 27;          // ... with at most this many stored entries
 constexpr unsigned long long kGridBarrierNs = 2000000000ull;  // longest wait at a barrier (2 s)
 constexpr size_t kGridBarBytes = 16;                          // after the control block
 

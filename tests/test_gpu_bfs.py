@@ -351,6 +351,27 @@ def test_fused_loop_matches_level_graph(d, s16, name, mode, seed):
         g.close()
 
 
+def test_fused_loop_at_its_size_bound(d):
+    """R-MAT scale 21 (1.24 M vertices with edges, below the fused loop's
+    bound of 2^21, 64 M stored entries): the fused loop's largest graphs.
+    Levels bit-exact against the oracle, parents valid, and the same
+    schedule and counters as the level graph."""
+    spec = inputs.rmat(21)
+    og = oracle.csr_from_rmat_par(spec)
+    assert (og.degrees() > 0).sum() <= 1 << 21 and og.nnz <= 1 << 27
+    g = d.rmat_graph(spec, flags=d.DOBFS_GRAPH_REINDEX)
+    roots = inputs.sample_roots(inputs.root_seed(spec.seed), og.n, 2, og.degrees() > 0)
+    for r in roots:
+        ref = oracle.bfs(og, int(r), want_parent=False)[0]
+        traces = []
+        for rf in (0, d.DOBFS_RUN_LEVEL_GRAPH):
+            lv, pa, st = _run(d, g, int(r), flags=rf)
+            _check_run(og, int(r), lv, pa, ref)
+            traces.append([(t.direction, t.n_frontier, t.m_frontier, t.n_next) for t in g.trace()])
+        assert traces[0] == traces[1]
+    g.close()
+
+
 def _pairs_graph(d, n, pairs, flags=0):
     src = np.array([p[0] for p in pairs], dtype=np.int32)
     dst = np.array([p[1] for p in pairs], dtype=np.int32)
