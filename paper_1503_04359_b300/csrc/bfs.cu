@@ -1042,13 +1042,15 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint3
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();  // the block's writes, before its arrival
-    if (atomicAdd(bar, 1u) == nblocks - 1) {
-      __threadfence();
+    uint32_t old;
+    // arrival: releases the block's writes (ordered before it by the block
+    // barrier) and, in the last block, acquires every other block's
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    if (old == nblocks - 1) {
       last();
       atomicExch(bar, 0u);  // the count starts over for the next barrier
-      __threadfence();
-      atomicExch(bar + 1, gen + 1u);
+      // releases the hook's writes and the reset with the new generation
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1u) : "memory");
     } else {
       const unsigned long long t0 = globaltimer_ns();
       for (uint32_t k = 1; ld_acquire_gpu(bar + 1) == gen; ++k) {
@@ -1059,8 +1061,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint3
         }
       }
     }
-    __threadfence();
-    gen += 1u;
+    gen += 1u;  // the waiting blocks' acquire loads order their later reads
     s_ok = ok;
   }
   __syncthreads();
